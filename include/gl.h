@@ -1,0 +1,155 @@
+/*
+ * gl.h - C ABI of libgl, a B300 (sm_103a) library that evaluates the
+ * log-posterior of a strong gravitational lens model, and its gradient, for
+ * a batch of parameter vectors per call.
+ *
+ * The model is the one the GIGA-Lens pipeline samples (Sec. 3 of the paper:
+ * an elliptical power-law (EPL) mass with external shear, elliptical Sersic
+ * lens light, elliptical Sersic source light, intensities as free parameters
+ * ("forward" modelling), a supersampled pixel grid; the priors of Eq.
+ * sim-dist, Sec. 4.2). Every multi-start MAP step, SVI draw and HMC leapfrog
+ * of the pipeline (Sec. 3, Sec. 3.1) reduces to the calls below.
+ *
+ * Model definition (the paper defers the forward model to its predecessor;
+ * these are the readings this library implements):
+ *   grid      pixel (i, j) centre x = (j - (nx-1)/2) D, y = (i - (ny-1)/2) D
+ *             (D = pixel_scale, arcsec); sub-pixel (k, l) of supersampling s
+ *             at ((l + 1/2)/s - 1/2) D, ((k + 1/2)/s - 1/2) D from it.
+ *   ellipticity (e1, e2) -> axis ratio q = (1-|e|)/(1+|e|), position angle
+ *             atan2(e2, e1)/2 (major axis along +x for e1 > 0).
+ *   EPL       deflection by the Tessore & Metcalf (2015) hypergeometric
+ *             series, theta_E in the intermediate-axis convention
+ *             (b = theta_E sqrt(q)); convergence (2-t)/2 (b/R)^t, t = gamma-1,
+ *             R = sqrt(q^2 x'^2 + y'^2).
+ *   shear     alpha = (g1 x + g2 y, g2 x - g1 y), centred on the origin.
+ *   Sersic    I_e exp(-b_n ((R/R_e)^(1/n) - 1)), b_n = 1.9992 n - 0.3271,
+ *             R = sqrt(q x'^2 + y'^2/q).  Radii are clamped below at 1e-6".
+ *   source    evaluated at beta = theta - alpha_EPL - alpha_shear.
+ *   image     m = PSF (*) [D^2 x mean of the s x s sub-pixel brightnesses],
+ *             true convolution, "same" size, zero padding, PSF renormalised
+ *             to unit sum.
+ *   log p     -1/2 sum ((d - m)/sigma)^2 + log prior (normalised 1-D
+ *             densities; |e| < emax discs restrict the support only).
+ *
+ * Parameter vector (row-major theta[B][P], P = 8 + 7 (n_lens_light +
+ * n_source)), in the order of Eq. sim-dist:
+ *   [theta_E, gamma, e1, e2, x, y]_EPL, [gamma1, gamma2]_shear,
+ *   per lens-light component [R_e, n, e1, e2, x, y, I_e],
+ *   per source component     [R_e, n, e1, e2, x, y, I_e].
+ *
+ * Domain. A row outside the model's domain (theta_E <= 0, gamma outside
+ * (1, 3), any |e| >= 0.8, R_e <= 0, n < 0.2) or outside the prior's support
+ * gets logp = -inf and a zero gradient. A row holding a NaN gets NaN for
+ * logp and every gradient entry. Neither is an error: the call returns GL_OK.
+ *
+ * Conventions for every call:
+ *   - Pointers documented "device" are CUDA device (or managed) pointers on
+ *     the current device; "host" are ordinary host pointers.
+ *   - Calls that take a stream enqueue work on it (a cudaStream_t passed as
+ *     void*, NULL = the legacy default stream) and return without waiting.
+ *   - The caller owns theta and every output buffer; the library never frees
+ *     or keeps them. The library owns gl_system and gl_surrogate objects and
+ *     their device copies.
+ *   - Every call returns a status and never aborts. GL_EINVAL = rejected
+ *     arguments (nothing was enqueued), GL_ENOMEM = a device allocation
+ *     failed, GL_ECUDA = a CUDA call failed. gl_last_error() describes the
+ *     last failure on the calling host thread.
+ *   - One gl_system must not be used by two host threads at once, nor by two
+ *     streams whose work overlaps (it owns one scratch arena).
+ */
+#ifndef GL_H
+#define GL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GL_OK = 0,
+  GL_EINVAL = 1,
+  GL_ENOMEM = 2,
+  GL_ECUDA = 3,
+  GL_ENOSURROGATE = 4,
+  GL_ETIMEOUT = 5
+} gl_status;
+
+/* Which deflection the EPL uses: the exact series or the learned surrogate. */
+typedef enum { GL_DEFL_SERIES = 0, GL_DEFL_SURROGATE = 1 } gl_deflection;
+
+/* Prior kinds (Eq. sim-dist, Sec. 4.2). */
+typedef enum {
+  GL_PRIOR_FLAT = 0,      /* no density; support [lo, hi] (may be infinite) */
+  GL_PRIOR_UNIFORM = 1,   /* U(lo, hi), lo < hi finite                       */
+  GL_PRIOR_NORMAL = 2,    /* N(a, b), b > 0                                  */
+  GL_PRIOR_TRUNCNORM = 3, /* N(a, b) truncated to [lo, hi], renormalised     */
+  GL_PRIOR_LOGNORMAL = 4  /* log x ~ N(a, b), x > 0                          */
+} gl_prior_kind;
+
+typedef struct {
+  int kind; /* gl_prior_kind */
+  float a, b, lo, hi;
+} gl_prior;
+
+/* Description of one lens system. All arrays are copied by gl_system_create
+ * and may be freed by the caller afterwards. */
+typedef struct {
+  int ny, nx;          /* image size in pixels, 1..2048 each                 */
+  float pixel_scale;   /* arcsec per pixel, > 0                              */
+  int supersample;     /* s, 1..8                                            */
+  const float* data;   /* observed image d [ny*nx], row-major (y = row)      */
+  const float* sigma;  /* noise map [ny*nx], > 0 (+inf masks a pixel)       */
+  const float* psf;    /* PSF [psf_ny*psf_nx], positive sum                  */
+  int psf_ny, psf_nx;  /* odd, 1..21                                         */
+  int n_lens_light;    /* Sersic lens-light components, 0..2                 */
+  int n_source;        /* Sersic source components, 1..3                     */
+  const gl_prior* prior; /* host [P]                                         */
+  const float* emax;   /* host [1 + n_lens_light + n_source]: |e| < emax per
+                          component (EPL first), 0 = no constraint; may be NULL */
+  int inputs_on_device; /* nonzero: data, sigma and psf are device pointers  */
+} gl_system_desc;
+
+typedef struct gl_system gl_system;
+typedef struct gl_surrogate gl_surrogate;
+
+/* Creates a system: validates desc, copies data, sigma^-2 and the normalised
+ * PSF to the current device. Synchronous. On error *out is NULL. */
+gl_status gl_system_create(const gl_system_desc* desc, gl_system** out);
+
+/* Frees a system and its device memory (waits for the device first). NULL is
+ * accepted. */
+gl_status gl_system_destroy(gl_system* sys);
+
+/* P = 8 + 7 (n_lens_light + n_source); -1 for NULL. */
+int gl_system_num_params(const gl_system* sys);
+
+/* log p(theta_b | d) for b < B (Sec. 3: the quantity every MAP, SVI and HMC
+ * step evaluates). theta: device [B][P]; logp: device [B]. B = 0 is a no-op.
+ * GL_ENOSURROGATE if defl = GL_DEFL_SURROGATE and no surrogate is attached. */
+gl_status gl_logp(gl_system* sys, const float* theta, int B, float* logp, gl_deflection defl,
+                  void* stream);
+
+/* log p and its gradient d log p / d theta (the autodiff call of Sec. 3).
+ * grad: device [B][P]. */
+gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, float* grad,
+                       gl_deflection defl, void* stream);
+
+/* The same with HOST buffers: copies theta in through the system's pinned
+ * staging buffers, evaluates, copies logp and grad (grad may be NULL) back and
+ * waits for the stream. Grows the system's staging buffers on first use. */
+gl_status gl_logp_grad_host(gl_system* sys, const float* theta_host, int B, float* logp_host,
+                            float* grad_host, gl_deflection defl, void* stream);
+
+/* Model image m (binned, PSF-convolved) for each row: img device [B][ny][nx].
+ * Rows outside the model's domain or holding a NaN give NaN images; the prior
+ * is not checked. */
+gl_status gl_model_image(gl_system* sys, const float* theta, int B, float* img,
+                         gl_deflection defl, void* stream);
+
+/* Last failure message on this host thread ("" if none). */
+const char* gl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GL_H */

@@ -1,0 +1,239 @@
+"""Python binding of libgl, the B300 strong-lens log-posterior library.
+
+Argument marshalling only: every step of the computation runs in libgl's CUDA
+kernels behind the C ABI declared in include/gl.h. Torch tensors provide the
+device memory and the stream. If libgl.so is missing, or no CUDA device is
+present, the calls raise: there is no CPU fallback.
+
+    sys = System(ny, nx, pixel_scale, supersample, data, sigma, psf,
+                 n_lens_light, n_source, prior_spec)
+    logp = sys.logp(theta)                # theta: cuda float32 [B, P]
+    logp, grad = sys.logp_grad(theta)
+    img = sys.model_image(theta)
+    logp = LogPosterior.apply(theta, sys)   # autograd through the adjoint
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgl.so")
+
+GL_OK, GL_EINVAL, GL_ENOMEM, GL_ECUDA, GL_ENOSURROGATE, GL_ETIMEOUT = range(6)
+GL_DEFL_SERIES, GL_DEFL_SURROGATE = 0, 1
+PRIOR_KIND = {"flat": 0, "uniform": 1, "normal": 2, "truncnorm": 3, "lognormal": 4}
+
+_STATUS_NAMES = {0: "GL_OK", 1: "GL_EINVAL", 2: "GL_ENOMEM", 3: "GL_ECUDA",
+                 4: "GL_ENOSURROGATE", 5: "GL_ETIMEOUT"}
+
+
+class GLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class gl_prior(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_float), ("b", ctypes.c_float),
+                ("lo", ctypes.c_float), ("hi", ctypes.c_float)]
+
+
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+class gl_system_desc(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int), ("nx", ctypes.c_int), ("pixel_scale", ctypes.c_float),
+                ("supersample", ctypes.c_int), ("data", _fp), ("sigma", _fp), ("psf", _fp),
+                ("psf_ny", ctypes.c_int), ("psf_nx", ctypes.c_int),
+                ("n_lens_light", ctypes.c_int), ("n_source", ctypes.c_int),
+                ("prior", ctypes.POINTER(gl_prior)), ("emax", _fp),
+                ("inputs_on_device", ctypes.c_int)]
+
+
+# (name, restype, argtypes) of every entry point in include/gl.h
+_VP = ctypes.c_void_p
+SIGNATURES = {
+    "gl_system_create": (ctypes.c_int, [ctypes.POINTER(gl_system_desc), ctypes.POINTER(_VP)]),
+    "gl_system_destroy": (ctypes.c_int, [_VP]),
+    "gl_system_num_params": (ctypes.c_int, [_VP]),
+    "gl_logp": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP]),
+    "gl_logp_grad": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]),
+    "gl_logp_grad_host": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]),
+    "gl_model_image": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP]),
+    "gl_last_error": (ctypes.c_char_p, []),
+}
+
+_LIB: Optional[ctypes.CDLL] = None
+
+
+def load() -> ctypes.CDLL:
+    """Loads libgl.so (built by paper_2606_30633_b300/build.py)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_2606_30633_b300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def last_error() -> str:
+    return load().gl_last_error().decode()
+
+
+def _check(status: int):
+    if status != GL_OK:
+        raise GLError(status, last_error())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+def prior_array(prior_spec) -> ctypes.Array:
+    arr = (gl_prior * len(prior_spec.params))()
+    for k, p in enumerate(prior_spec.params):
+        arr[k] = gl_prior(PRIOR_KIND[p.kind], p.a, p.b, p.lo, p.hi)
+    return arr
+
+
+class System:
+    """One lens system resident on the current CUDA device."""
+
+    def __init__(self, ny: int, nx: int, pixel_scale: float, supersample: int, data, sigma, psf,
+                 n_lens_light: int, n_source: int, prior_spec):
+        lib = load()
+        self._lib = lib
+        data = np.ascontiguousarray(np.asarray(data, dtype=np.float32).reshape(ny, nx))
+        sigma = np.ascontiguousarray(np.asarray(sigma, dtype=np.float32).reshape(ny, nx))
+        psf = np.ascontiguousarray(np.asarray(psf, dtype=np.float32))
+        self._prior = prior_array(prior_spec)
+        emax = np.ascontiguousarray(np.asarray(prior_spec.emax, dtype=np.float32))
+        desc = gl_system_desc(ny, nx, pixel_scale, supersample,
+                              data.ctypes.data_as(_fp), sigma.ctypes.data_as(_fp),
+                              psf.ctypes.data_as(_fp), psf.shape[0], psf.shape[1],
+                              n_lens_light, n_source, self._prior, emax.ctypes.data_as(_fp), 0)
+        h = _VP()
+        _check(lib.gl_system_create(ctypes.byref(desc), ctypes.byref(h)))
+        self._h = h
+        self.ny, self.nx, self.P = ny, nx, int(lib.gl_system_num_params(h))
+        self.n_lens_light, self.n_source = n_lens_light, n_source
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gl_system_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _theta(self, theta):
+        torch = _torch()
+        if not (isinstance(theta, torch.Tensor) and theta.is_cuda and theta.dtype == torch.float32):
+            raise TypeError("theta must be a CUDA float32 tensor")
+        theta = theta.contiguous()
+        if theta.dim() != 2 or theta.shape[1] != self.P:
+            raise ValueError(f"theta must be [B, {self.P}]")
+        return theta
+
+    def logp(self, theta, defl: int = GL_DEFL_SERIES, out=None, stream=None):
+        torch = _torch()
+        theta = self._theta(theta)
+        B = theta.shape[0]
+        out = torch.empty(B, device=theta.device, dtype=torch.float32) if out is None else out
+        _check(self._lib.gl_logp(self._h, _ptr(theta), B, _ptr(out), defl, _stream_ptr(stream)))
+        return out
+
+    def logp_grad(self, theta, defl: int = GL_DEFL_SERIES, out=None, grad=None, stream=None):
+        torch = _torch()
+        theta = self._theta(theta)
+        B = theta.shape[0]
+        out = torch.empty(B, device=theta.device, dtype=torch.float32) if out is None else out
+        grad = torch.empty_like(theta) if grad is None else grad
+        _check(self._lib.gl_logp_grad(self._h, _ptr(theta), B, _ptr(out), _ptr(grad), defl,
+                                      _stream_ptr(stream)))
+        return out, grad
+
+    def logp_grad_host(self, theta: np.ndarray, defl: int = GL_DEFL_SERIES, want_grad=True,
+                       stream=None):
+        """Host arrays in and out (the copies happen inside the call)."""
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+        B = th.shape[0]
+        lp = np.empty(B, dtype=np.float32)
+        g = np.empty_like(th) if want_grad else None
+        _check(self._lib.gl_logp_grad_host(self._h, th.ctypes.data, B, lp.ctypes.data,
+                                           None if g is None else g.ctypes.data, defl,
+                                           _stream_ptr(stream)))
+        return lp, g
+
+    def model_image(self, theta, defl: int = GL_DEFL_SERIES, out=None, stream=None):
+        torch = _torch()
+        theta = self._theta(theta)
+        B = theta.shape[0]
+        out = (torch.empty((B, self.ny, self.nx), device=theta.device, dtype=torch.float32)
+               if out is None else out)
+        _check(self._lib.gl_model_image(self._h, _ptr(theta), B, _ptr(out), defl,
+                                        _stream_ptr(stream)))
+        return out
+
+
+def system_from_workload(W, data, sigma) -> System:
+    """System for a synth.Workload with the given data and noise map."""
+    return System(W.ny, W.nx, W.pixel_scale, W.supersample, data, sigma, W.psf,
+                  W.n_lens_light, W.n_source, W.prior())
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class LogPosterior(torch.autograd.Function):
+        """log p(theta) per row with its gradient from the fused adjoint kernel."""
+
+        @staticmethod
+        def forward(ctx, theta, system: System, defl: int = GL_DEFL_SERIES):
+            lp, g = system.logp_grad(theta.detach().float(), defl)
+            ctx.save_for_backward(g)
+            return lp
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g,) = ctx.saved_tensors
+            return grad_out[:, None] * g, None, None
+
+    return LogPosterior
+
+
+def __getattr__(name):
+    if name == "LogPosterior":
+        fn = _autograd_function()
+        globals()["LogPosterior"] = fn
+        return fn
+    raise AttributeError(name)

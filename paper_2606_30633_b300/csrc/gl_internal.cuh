@@ -1,0 +1,59 @@
+// Internal types of libgl shared by the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace gl {
+
+constexpr int MAX_K = 21;      // largest PSF side
+constexpr int MAX_S = 8;       // largest supersampling factor
+constexpr int MAX_LIGHT = 2;   // lens-light components
+constexpr int MAX_SRC = 3;     // source components
+constexpr int MAX_COMP = MAX_LIGHT + MAX_SRC;
+constexpr int MAX_P = 8 + 7 * MAX_COMP;
+constexpr int N_MAX = 128;     // EPL series terms for |e| < 0.8 at FP32 tolerance
+constexpr int THREADS = 256;   // threads per CTA of the fused kernels
+constexpr int NWARPS = THREADS / 32;
+constexpr int ROWS_STRIP = 8;  // output rows per thread in the unrolled convolution
+
+// One prior entry as the kernels see it; cnst is the log normalisation
+// constant, computed once at system creation.
+struct PriorDev {
+  int kind;
+  float a, b, lo, hi;
+  double cnst;
+};
+
+// Kernel parameter block of one system (passed by value: the PSF taps live in
+// the constant bank, so the unrolled convolution reads them as FFMA operands).
+struct SysParams {
+  int ny, nx, s, P, nL, nS;
+  int ky, kx, cy, cx;      // PSF size and centre
+  int Hp, Wp;              // padded buffer size (rows, row pitch in floats)
+  int bufA_smem, bufB_smem;  // buffer placement: 1 = dynamic shared memory
+  size_t slot_floats;      // global scratch floats per CTA
+  float D;                 // pixel scale (arcsec)
+  float scale;             // D^2 / s^2
+  float xg0, yg0;          // -(nx-1)/2, -(ny-1)/2
+  float off[MAX_S];        // sub-pixel offsets (l + 1/2)/s - 1/2 (pixel units)
+  const float* data;       // [ny*nx]
+  const float* w;          // sigma^-2 [ny*nx]
+  const PriorDev* prior;   // [P]
+  const float* emax;       // [1 + nL + nS]
+  float* scratch;          // global scratch base (CTA b uses slot b)
+  float kconv[MAX_K * MAX_K];  // flipped PSF: m = correlate(b_pad, kconv)
+  float kcorr[MAX_K * MAX_K];  // PSF: adjoint = correlate(g_pad, kcorr)
+};
+
+// Launch entry points (defined in the kernel translation units).
+// img != nullptr: write the model image instead of reducing chi^2.
+cudaError_t launch_forward(const SysParams& sp, const float* theta, int B, float* logp,
+                           float* img, size_t dyn_smem, cudaStream_t st);
+cudaError_t launch_grad(const SysParams& sp, const float* theta, int B, float* logp, float* grad,
+                        size_t dyn_smem, cudaStream_t st);
+cudaError_t set_smem_limits_fwd(size_t bytes);
+cudaError_t set_smem_limits_grad(size_t bytes);
+
+}  // namespace gl

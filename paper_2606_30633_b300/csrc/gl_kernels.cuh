@@ -1,0 +1,385 @@
+// Fused per-sample kernels of the lens log-posterior: one CTA per parameter
+// vector. Phases (all in one launch, per CTA):
+//   1  sub-pixel ray-shoot (EPL series + shear), lens and source Sersic light,
+//      binned to pixels (each thread owns whole pixels: no atomics);
+//   2  PSF convolution of the binned image, chi^2 against the data
+//      (Kahan-compensated FP32 per thread, FP64 across threads);
+//   3  (gradient only) g = sigma^-2 (d - m) correlated with the PSF (the
+//      convolution's adjoint), times D^2/s^2;
+//   4  (gradient only) sub-pixel adjoint: recompute the forward chain and
+//      accumulate the native gradient sums in registers; block reduction; the
+//      per-sample chain rule to the Eq. sim-dist parameters plus the prior.
+// The binned image and g live in zero-padded buffers (dynamic shared memory
+// when they fit, else a per-CTA slot of global scratch).
+#pragma once
+
+#include "gl_model.cuh"
+
+namespace gl {
+
+// ---------------------------------------------------------------- conv ----
+// Correlation of a zero-padded buffer: out(i, j) = sum_{u,v} k[u][v] in(i+u, j+v).
+// Each thread computes ROWS_STRIP outputs of one column; lanes own adjacent
+// columns (conflict-free loads); taps are compile-time indices into the
+// kernel's parameter block.
+template <int K, bool CONV, class Epi>
+__device__ __forceinline__ void correlate_fixed(const SysParams& sp, const float* in, Epi epi) {
+  constexpr int RS = ROWS_STRIP;
+  const int ny = sp.ny, nx = sp.nx, Wp = sp.Wp;
+  const int nrb = (ny + RS - 1) / RS;
+  const int total = nrb * nx;
+  for (int s = threadIdx.x; s < total; s += THREADS) {
+    const int rb = s / nx;
+    const int j = s - rb * nx;
+    const int i0 = rb * RS;
+    float acc[RS];
+#pragma unroll
+    for (int r = 0; r < RS; ++r) acc[r] = 0.f;
+    const float* base = in + (size_t)i0 * Wp + j;
+#pragma unroll
+    for (int v = 0; v < K; ++v) {
+      float col[RS + K - 1];
+#pragma unroll
+      for (int m = 0; m < RS + K - 1; ++m) col[m] = base[m * Wp + v];
+#pragma unroll
+      for (int u = 0; u < K; ++u) {
+        const float kv = CONV ? sp.kconv[u * K + v] : sp.kcorr[u * K + v];
+#pragma unroll
+        for (int r = 0; r < RS; ++r) acc[r] = fmaf(kv, col[u + r], acc[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RS; ++r)
+      if (i0 + r < ny) epi(i0 + r, j, acc[r]);
+  }
+}
+
+template <bool CONV, class Epi>
+__device__ __forceinline__ void correlate_generic(const SysParams& sp, const float* in, Epi epi) {
+  const int ny = sp.ny, nx = sp.nx, Wp = sp.Wp, ky = sp.ky, kx = sp.kx;
+  for (int s = threadIdx.x; s < ny * nx; s += THREADS) {
+    const int i = s / nx;
+    const int j = s - i * nx;
+    float acc = 0.f;
+    for (int u = 0; u < ky; ++u)
+      for (int v = 0; v < kx; ++v)
+        acc = fmaf(CONV ? sp.kconv[u * kx + v] : sp.kcorr[u * kx + v],
+                   in[(size_t)(i + u) * Wp + j + v], acc);
+    epi(i, j, acc);
+  }
+}
+
+template <bool CONV, class Epi>
+__device__ __forceinline__ void correlate(const SysParams& sp, const float* in, Epi epi) {
+  if (sp.ky == 11 && sp.kx == 11)
+    correlate_fixed<11, CONV>(sp, in, epi);
+  else if (sp.ky == 21 && sp.kx == 21)
+    correlate_fixed<21, CONV>(sp, in, epi);
+  else
+    correlate_generic<CONV>(sp, in, epi);
+}
+
+// Zero the halo of a padded buffer (the interior is written by a phase).
+__device__ __forceinline__ void zero_halo(const SysParams& sp, float* buf) {
+  const int Hp = sp.Hp, Wp = sp.Wp;
+  for (int idx = threadIdx.x; idx < Hp * Wp; idx += THREADS) {
+    const int r = idx / Wp, c = idx - r * Wp;
+    const bool inside = r >= sp.cy && r < sp.cy + sp.ny && c >= sp.cx && c < sp.cx + sp.nx;
+    if (!inside) buf[idx] = 0.f;
+  }
+}
+
+// ---------------------------------------------------------- reductions ----
+__device__ __forceinline__ double block_sum_double(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NWARPS; ++k) s += red[k];
+  return s;  // valid on thread 0
+}
+
+// ------------------------------------------------------- sub-pixel work ----
+template <int NL, int NS>
+__device__ __forceinline__ float surface_brightness(const SampleC& sc, const EplC& e,
+                                                    const LightC* L, float x, float y) {
+  float ax, ay;
+  epl_alpha(e, sc.cE, sc.nq, x, y, ax, ay);
+  const float bx = x - ax - fmaf(sc.g1, x, sc.g2 * y);
+  const float by = y - ay - fmaf(sc.g2, x, -sc.g1 * y);
+  float sb = 0.f;
+#pragma unroll
+  for (int c = 0; c < NL; ++c) sb += sersic_fwd(L[c], x, y);
+#pragma unroll
+  for (int c = 0; c < NS; ++c) sb += sersic_fwd(L[NL + c], bx, by);
+  return sb;
+}
+
+// Adds u x d SB / d(native parameters) at one sub-pixel to acc (see
+// epl_finish / sersic_finish for the accumulator meanings).
+template <int NL, int NS>
+__device__ __forceinline__ void subpixel_adjoint(const SampleC& sc, const EplC& e, const LightC* L,
+                                                 float x, float y, float u, float* acc) {
+  const float dx = x - e.xc, dy = y - e.yc;
+  const float xp = fmaf(e.cs, dx, e.sn * dy);
+  const float yp = fmaf(e.cs, dy, -e.sn * dx);
+  const float R2 = fmaxf(fmaf(e.q2 * xp, xp, yp * yp), R_MIN2);
+  const float ir = rsq(R2);
+  const float iR2 = ir * ir;
+  const float cph = e.q * xp * ir, sph = yp * ir;
+  const float wr = fmaf(cph, cph, -sph * sph), wi = 2.f * cph * sph;
+  float Er, Ei, Tr, Ti;
+  horner2(sc.cE, sc.cT, sc.nq, wr, wi, Er, Ei, Tr, Ti);
+  const float zr = -e.f * wr, zi = -e.f * wi;
+  const float Fr = 1.f + fmaf(zr, Er, -zi * Ei);
+  const float Fi = fmaf(zr, Ei, zi * Er);
+  const float Lm = lg2(R2);
+  const float A = e.CA * ex2(e.ht * Lm);
+  const float Qr = A * cph, Qi = A * sph;  // A e^{i vphi}
+  const float aLr = fmaf(Qr, Fr, -Qi * Fi);
+  const float aLi = fmaf(Qr, Fi, Qi * Fr);
+  const float ax = fmaf(e.cs, aLr, -e.sn * aLi);
+  const float ay = fmaf(e.sn, aLr, e.cs * aLi);
+  const float bx = x - ax - fmaf(sc.g1, x, sc.g2 * y);
+  const float by = y - ay - fmaf(sc.g2, x, -sc.g1 * y);
+
+  float gX = 0.f, gY = 0.f;
+#pragma unroll
+  for (int c = 0; c < NL; ++c) sersic_adj<false>(L[c], x, y, u, acc + 8 + 7 * c, gX, gY);
+#pragma unroll
+  for (int c = 0; c < NS; ++c)
+    sersic_adj<true>(L[NL + c], bx, by, u, acc + 8 + 7 * (NL + c), gX, gY);
+  // adjoint of the deflection: v = d logp / d alpha = -u grad_beta S
+  const float vx = -u * gX, vy = -u * gY;
+  acc[6] = fmaf(vx, x, fmaf(-vy, y, acc[6]));
+  acc[7] = fmaf(vx, y, fmaf(vy, x, acc[7]));
+  // lens frame
+  const float vLx = fmaf(e.cs, vx, e.sn * vy);
+  const float vLy = fmaf(e.cs, vy, -e.sn * vx);
+  const float s1 = fmaf(vLx, aLr, vLy * aLi);    // v . alpha
+  const float s1i = fmaf(vLy, aLr, -vLx * aLi);  // v . (i alpha)
+  // dF/dt = z (Tr + i Ti)
+  const float TFr = fmaf(zr, Tr, -zi * Ti), TFi = fmaf(zr, Ti, zi * Tr);
+  const float QTr = fmaf(Qr, TFr, -Qi * TFi), QTi = fmaf(Qr, TFi, Qi * TFr);
+  const float sT = fmaf(vLx, QTr, vLy * QTi);
+  // F'(z) = [t F - (2-t) E] / (2 (1 - z))
+  const float nr = fmaf(e.t, Fr, -e.tmt * Er), ni = fmaf(e.t, Fi, -e.tmt * Ei);
+  const float ozr = 1.f - zr, ozi = -zi;
+  const float inv = 0.5f * rcp(fmaf(ozr, ozr, ozi * ozi));
+  const float Fpr = fmaf(nr, ozr, ni * ozi) * inv;
+  const float Fpi = fmaf(ni, ozr, -nr * ozi) * inv;
+  const float P2r = fmaf(Qr, Fpr, -Qi * Fpi), P2i = fmaf(Qr, Fpi, Qi * Fpr);
+  const float P3r = fmaf(P2r, wr, -P2i * wi), P3i = fmaf(P2r, wi, P2i * wr);
+  const float s3 = fmaf(vLx, P3r, vLy * P3i);
+  const float s3i = fmaf(vLy, P3r, -vLx * P3i);
+  const float lnR = 0.34657359027997264f * Lm;  // ln(2)/2 log2(R^2)
+  const float S13 = fmaf(-2.f * e.f, s3i, s1i);
+  const float dphq = -xp * yp * iR2;
+  acc[0] += s1;
+  acc[1] = fmaf(s1, e.lnb - lnR, acc[1] + sT);
+  acc[2] = fmaf(s1, fmaf(e.omt * e.q * xp * xp, iR2, e.a0), fmaf(S13, dphq, fmaf(-e.dfdq, s3, acc[2])));
+  const float kap = e.Kk * A * ir;
+  acc[3] = fmaf(e.tmt, s1i, fmaf(-2.f * kap, fmaf(xp, vLy, -yp * vLx), acc[3]));
+  acc[4] = fmaf(iR2, fmaf(e.omt * e.q2 * xp, s1, -e.q * yp * S13), acc[4]);
+  acc[5] = fmaf(iR2, fmaf(e.omt * yp, s1, e.q * xp * S13), acc[5]);
+}
+
+// ---------------------------------------------------------------- kernels ----
+struct SmemStatic {
+  SampleC sc;
+  double red[NWARPS];
+  float redP[NWARPS][MAX_P];
+  double gsum[MAX_P];
+};
+
+__device__ __forceinline__ void buffers(const SysParams& sp, float* dsm, bool two, float*& A,
+                                        float*& Bf) {
+  const size_t nbuf = ((size_t)sp.Hp * sp.Wp + 3) & ~(size_t)3;
+  float* slot = sp.scratch ? sp.scratch + (size_t)blockIdx.x * sp.slot_floats : nullptr;
+  size_t soff = 0, goff = 0;
+  if (sp.bufA_smem) { A = dsm; soff += nbuf; } else { A = slot; goff += nbuf; }
+  Bf = nullptr;
+  if (two) {
+    if (sp.bufB_smem) Bf = dsm + soff; else Bf = slot + goff;
+  }
+}
+
+// Forward: log p per row, or (img != nullptr) the model image per row.
+template <int NL, int NS>
+__global__ void __launch_bounds__(THREADS, 2)
+k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta, int B,
+          float* __restrict__ logp, float* __restrict__ img) {
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ SmemStatic st;
+  SampleC& sc = st.sc;
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const bool want_img = img != nullptr;
+  if (threadIdx.x == 0) stage_sample(sp, theta + (size_t)b * sp.P, sc, !want_img);
+  float *A, *Bf;
+  buffers(sp, dsm, false, A, Bf);
+  zero_halo(sp, A);
+  __syncthreads();
+  const int npix = sp.ny * sp.nx;
+  if (sc.status != 0) {
+    if (want_img) {
+      for (int p = threadIdx.x; p < npix; p += THREADS) img[(size_t)b * npix + p] = __int_as_float(0x7fc00000);
+    } else if (threadIdx.x == 0) {
+      logp[b] = sc.status == 2 ? __int_as_float(0x7fc00000) : -__int_as_float(0x7f800000);
+    }
+    return;
+  }
+  const EplC e = sc.epl;
+  LightC L[NL + NS];
+#pragma unroll
+  for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
+  const int s = sp.s;
+  const float D = sp.D;
+  for (int p = threadIdx.x; p < npix; p += THREADS) {
+    const int i = p / sp.nx, j = p - i * sp.nx;
+    const float xj = (float)j + sp.xg0, yi = (float)i + sp.yg0;
+    float acc = 0.f;
+    for (int k = 0; k < s; ++k) {
+      const float y = (yi + sp.off[k]) * D;
+      for (int l = 0; l < s; ++l) {
+        const float x = (xj + sp.off[l]) * D;
+        acc += surface_brightness<NL, NS>(sc, e, L, x, y);
+      }
+    }
+    A[(size_t)(i + sp.cy) * sp.Wp + j + sp.cx] = acc * sp.scale;
+  }
+  __syncthreads();
+  float csum = 0.f, ccomp = 0.f;
+  float* out = want_img ? img + (size_t)b * npix : nullptr;
+  correlate<true>(sp, A, [&](int i, int j, float m) {
+    const int idx = i * sp.nx + j;
+    if (want_img) {
+      out[idx] = m;
+    } else {
+      const float r = sp.data[idx] - m;
+      const float y = fmaf(sp.w[idx] * r, r, -ccomp);
+      const float t = csum + y;
+      ccomp = (t - csum) - y;
+      csum = t;
+    }
+  });
+  if (want_img) return;
+  const double chi2 = block_sum_double((double)csum - (double)ccomp, st.red);
+  if (threadIdx.x == 0) logp[b] = (float)(-0.5 * chi2 + sc.logprior);
+}
+
+// Forward + adjoint: log p and d log p / d theta per row.
+template <int NL, int NS>
+__global__ void __launch_bounds__(THREADS, 2)
+k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, int B,
+       float* __restrict__ logp, float* __restrict__ grad) {
+  constexpr int P = 8 + 7 * (NL + NS);
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ SmemStatic st;
+  SampleC& sc = st.sc;
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const float* th = theta + (size_t)b * P;
+  if (threadIdx.x == 0) stage_sample(sp, th, sc, true);
+  float *A, *Bf;
+  buffers(sp, dsm, true, A, Bf);
+  zero_halo(sp, A);
+  zero_halo(sp, Bf);
+  __syncthreads();
+  const int npix = sp.ny * sp.nx;
+  if (sc.status != 0) {
+    const float lv = sc.status == 2 ? __int_as_float(0x7fc00000) : -__int_as_float(0x7f800000);
+    const float gv = sc.status == 2 ? __int_as_float(0x7fc00000) : 0.f;
+    if (threadIdx.x == 0) logp[b] = lv;
+    if (threadIdx.x < P) grad[(size_t)b * P + threadIdx.x] = gv;
+    return;
+  }
+  const EplC e = sc.epl;
+  LightC L[NL + NS];
+#pragma unroll
+  for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
+  const int s = sp.s;
+  const float D = sp.D;
+  const int Wp = sp.Wp, cy = sp.cy, cx = sp.cx, nx = sp.nx;
+  // phase 1
+  for (int p = threadIdx.x; p < npix; p += THREADS) {
+    const int i = p / nx, j = p - i * nx;
+    const float xj = (float)j + sp.xg0, yi = (float)i + sp.yg0;
+    float acc = 0.f;
+    for (int k = 0; k < s; ++k) {
+      const float y = (yi + sp.off[k]) * D;
+      for (int l = 0; l < s; ++l) {
+        const float x = (xj + sp.off[l]) * D;
+        acc += surface_brightness<NL, NS>(sc, e, L, x, y);
+      }
+    }
+    A[(size_t)(i + cy) * Wp + j + cx] = acc * sp.scale;
+  }
+  __syncthreads();
+  // phase 2
+  float csum = 0.f, ccomp = 0.f;
+  correlate<true>(sp, A, [&](int i, int j, float m) {
+    const int idx = i * nx + j;
+    const float r = sp.data[idx] - m;
+    const float wr = sp.w[idx] * r;
+    const float y = fmaf(wr, r, -ccomp);
+    const float t = csum + y;
+    ccomp = (t - csum) - y;
+    csum = t;
+    Bf[(size_t)(i + cy) * Wp + j + cx] = wr;
+  });
+  const double chi2 = block_sum_double((double)csum - (double)ccomp, st.red);
+  // (block_sum_double synchronised the block: phase 2 is complete)
+  // phase 3
+  const float scale = sp.scale;
+  correlate<false>(sp, Bf, [&](int i, int j, float g) {
+    A[(size_t)(i + cy) * Wp + j + cx] = g * scale;
+  });
+  __syncthreads();
+  // phase 4
+  float acc[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) acc[k] = 0.f;
+  for (int p = threadIdx.x; p < npix; p += THREADS) {
+    const int i = p / nx, j = p - i * nx;
+    const float u = A[(size_t)(i + cy) * Wp + j + cx];
+    const float xj = (float)j + sp.xg0, yi = (float)i + sp.yg0;
+    for (int k = 0; k < s; ++k) {
+      const float y = (yi + sp.off[k]) * D;
+      for (int l = 0; l < s; ++l) {
+        const float x = (xj + sp.off[l]) * D;
+        subpixel_adjoint<NL, NS>(sc, e, L, x, y, u, acc);
+      }
+    }
+  }
+  // reduction
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    float v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) st.redP[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < P) {
+    double v = 0.0;
+    for (int w = 0; w < NWARPS; ++w) v += (double)st.redP[w][threadIdx.x];
+    st.gsum[threadIdx.x] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v[P], g[P];
+    for (int k = 0; k < P; ++k) v[k] = (double)th[k];
+    epl_finish(v, st.gsum, g);
+#pragma unroll
+    for (int c = 0; c < NL + NS; ++c) sersic_finish(v + 8 + 7 * c, st.gsum + 8 + 7 * c, g + 8 + 7 * c);
+    for (int k = 0; k < P; ++k) grad[(size_t)b * P + k] = (float)(g[k] + (double)sc.dprior[k]);
+    logp[b] = (float)(-0.5 * chi2 + sc.logprior);
+  }
+}
+
+}  // namespace gl
