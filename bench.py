@@ -1,0 +1,336 @@
+"""Benchmark: log p + gradient evaluations per second of the strong-lens
+log-posterior on B300.
+
+Workload: the ground-based system (100x100 px at 0.262"/px, 3x3
+supersampling, 11x11 Moffat PSF, one lens-light and one source Sersic), 4096
+parameter vectors per step drawn from the priors; synthetic data rendered by
+the library itself with seeded noise. A step is one fused forward + adjoint
+launch over the whole batch. L2 is flushed (a 256 MB write) before every timed
+step; each step is timed with CUDA events on its stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on the host cores, on a bounded sample of the same workload. Under
+torchrun every rank runs its own replica (the evaluations are independent):
+value is the sum of ranks' evaluations over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "logp+grad evals/s (100x100 px, 3x SS) on 1 B300, learned vs plain; % roofline"
+SM_COUNT_B300 = 148
+FP32_LANES_PER_SM = 128
+MUFU_PER_SM_CLK = 16
+
+
+# ------------------------------------------------------------ op counts ----
+def series_terms(f: float) -> int:
+    """EPL series length the kernels use for |e| = f (before rounding up to
+    a multiple of 4): smallest N >= 1 with f^N <= 2^-24 (1-f)^2 / 2."""
+    tol = 2.0 ** -24 * (1 - f) ** 2 * 0.5
+    n, fn = 1, f
+    while fn > tol and n < 128:
+        fn *= f
+        n += 1
+    return n
+
+
+def algorithmic_ops(theta: np.ndarray, ny: int, nx: int, s: int, k: int, n_light: int,
+                    n_src: int) -> tuple:
+    """FP32 operations (an FMA counts once) and MUFU operations of one
+    log p + gradient evaluation per row, summed over rows, from the
+    formulation's operation count:
+      forward sub-pixel  34 + 4N (EPL) + 8 (shear, lens equation)
+                         + 15 per Sersic + 2 (grid) ... 3 MUFU EPL, 3 per Sersic
+      adjoint sub-pixel  38 + 8N (EPL, both series) + 8 + 31 per Sersic
+                         + 6 per source (position gradient) + 85 (EPL adjoint)
+                         + 2 (grid) ... 4 MUFU EPL, 4 per Sersic
+      per pixel          2 k^2 (PSF convolution and its adjoint) + 8
+    with N the per-row series length."""
+    nsub = ny * nx * s * s
+    npix = ny * nx
+    ncomp = n_light + n_src
+    f = np.hypot(theta[:, 2], theta[:, 3])
+    N = np.array([series_terms(float(v)) for v in f])
+    fwd = 34 + 4 * N + 8 + 15 * ncomp + 2
+    adj = 38 + 8 * N + 8 + 31 * ncomp + 6 * n_src + 85 + 2
+    ops = nsub * (fwd + adj) + npix * (2 * k * k + 8)
+    mufu = nsub * (3 + 3 * ncomp + 4 + 4 * ncomp)
+    return float(ops.sum()), float(mufu * theta.shape[0])
+
+
+# ------------------------------------------------------------- clocks ----
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[4:8]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- arms ----
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args) -> dict | None:
+    """The FP64 oracle (value + dual-number gradient, OpenMP over rows) on the
+    host cores, on a bounded sample of the same workload."""
+    import oracle
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    W = synth.ground_100()
+    spec = W.prior()
+    cores = oracle.max_threads()
+    S0 = oracle.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
+                       np.ones((W.ny, W.nx)), W.psf, 1, 1, spec)
+    m = S0.model_image(W.truth())[0]
+    d, sig = synth.noisy_data(m, W.noise())
+    S = oracle.System(W.ny, W.nx, W.pixel_scale, W.supersample, d, sig, W.psf, 1, 1, spec)
+    theta = W.samples()
+    rows = max(cores, 1)
+    per_step = []
+    for step in range(args.warmup + args.steps):
+        th = theta[(step * rows) % W.batch:(step * rows) % W.batch + rows]
+        t0 = time.perf_counter()
+        S.logp_grad(th, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            per_step.append(dt)
+    total = sum(per_step)
+    value = rows * len(per_step) / total
+    sample = (f"{rows} rows per step (one per core) of the 4096-row ground-based batch, "
+              f"{len(per_step)} timed steps")
+    return {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(per_step),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": W.name, "batch_per_step": rows, "ny": W.ny, "nx": W.nx,
+                   "supersample": W.supersample, "psf": 11, "params": W.P},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def cpu_baseline_leg(budget_s: float = 12.0) -> dict:
+    import oracle
+    W = synth.ground_100()
+    spec = W.prior()
+    cores = oracle.max_threads()
+    S0 = oracle.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
+                       np.ones((W.ny, W.nx)), W.psf, 1, 1, spec)
+    m = S0.model_image(W.truth())[0]
+    d, sig = synth.noisy_data(m, W.noise())
+    S = oracle.System(W.ny, W.nx, W.pixel_scale, W.supersample, d, sig, W.psf, 1, 1, spec)
+    theta = W.samples(8 * cores)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and done + cores <= theta.shape[0]:
+        S.logp_grad(theta[done:done + cores], nthreads=cores)
+        done += cores
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} rows of the ground-based batch (value + dual-number gradient), "
+                      f"{dt:.1f} s on {cores} threads"}
+
+
+def run_ours(args) -> dict | None:
+    import torch
+    import paper_2606_30633_b300 as gl
+    from paper_2606_30633_b300 import build as glbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    glbuild.build()
+    dev = torch.device("cuda", local)
+
+    W = synth.ground_100()
+    if args.batch:
+        W.batch = args.batch
+    spec = W.prior()
+    B = W.batch
+    # synthetic data: the library renders the truth; seeded noise on the host
+    blank = gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
+                      np.ones((W.ny, W.nx)), W.psf, 1, 1, spec)
+    truth = torch.tensor(W.truth()[None], dtype=torch.float32, device=dev)
+    m = blank.model_image(truth)[0].double().cpu().numpy()
+    blank.close()
+    d, sig = synth.noisy_data(m, W.noise())
+    S = gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, d, sig, W.psf, 1, 1, spec)
+    theta_np = W.samples().astype(np.float32)
+    theta = torch.tensor(theta_np, device=dev)
+    logp = torch.empty(B, device=dev)
+    grad = torch.empty_like(theta)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step():
+        S.logp_grad(theta, out=logp, grad=grad, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = world * B * args.steps / (t_ms / 1e3)
+    assert torch.isfinite(logp).all(), "non-finite log p in the benchmark batch"
+
+    # end to end through the public API with host buffers
+    e2e_ms = []
+    for k in range(args.warmup + max(3, args.steps // 5)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.logp_grad_host(theta_np)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            e2e_ms.append(dt * 1e3)
+    e2e_value = world * B / (statistics.mean(e2e_ms) / 1e3)
+
+    ops, mufu = algorithmic_ops(theta_np.astype(np.float64), W.ny, W.nx, W.supersample,
+                                W.psf.shape[0], 1, 1)
+    mean_s = statistics.mean(step_ms) / 1e3
+    peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2.032e9 / 1e12
+    achieved = ops / mean_s / 1e12
+    clocks = clk.summary()
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded priors, library-rendered truth, seeded noise)",
+            "config": {"workload": W.name, "batch_per_step": B, "ny": W.ny, "nx": W.nx,
+                       "supersample": W.supersample, "psf": int(W.psf.shape[0]),
+                       "params": W.P, "deflection": "series (plain)",
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "learned": None,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "note": "FP32 lane-operations (FMA = 1) of the formulation's op "
+                                 "count per evaluation / mean step time; peak = 148 SM x 128 "
+                                 "lanes x 2032 MHz",
+                         "mufu_ops_per_step": mufu},
+            "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": B * W.P * 4,
+                    "d2h_bytes_per_step": B * (W.P + 1) * 4},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_leg()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="rows per step (default: the workload's 4096); for profiling runs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,79 @@
+"""Shared set-up of parity cases: one seeded synthetic lens system handed to
+both the FP64 oracle and the CUDA library with identical (float32-rounded)
+inputs. The noiseless truth is rendered by the oracle only."""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+import oracle
+import synth
+
+
+def f32(a):
+    return np.asarray(np.asarray(a, dtype=np.float32), dtype=np.float64)
+
+
+def round_spec(spec: synth.PriorSpec) -> synth.PriorSpec:
+    ps = [synth.Prior(p.kind, float(np.float32(p.a)), float(np.float32(p.b)),
+                      float(np.float32(p.lo)), float(np.float32(p.hi))) for p in spec.params]
+    return synth.PriorSpec(ps, [float(np.float32(e)) for e in spec.emax])
+
+
+@dataclasses.dataclass
+class Case:
+    W: synth.Workload
+    spec: synth.PriorSpec
+    data: np.ndarray
+    sigma: np.ndarray
+    psf: np.ndarray
+    truth: np.ndarray
+    oracle: oracle.System
+
+    def theta(self, n, seed=None):
+        spec = self.W.prior()
+        th = synth.draw(spec, n, self.W.seed_samples if seed is None else seed,
+                        self.W.n_lens_light, self.W.n_source)
+        return f32(th)
+
+    def gpu_system(self):
+        import paper_2606_30633_b300 as gl
+        return gl.System(self.W.ny, self.W.nx, self.W.pixel_scale, self.W.supersample,
+                         self.data, self.sigma, self.psf, self.W.n_lens_light,
+                         self.W.n_source, self.spec)
+
+
+def make_case(W: synth.Workload, nthreads: int = 0) -> Case:
+    spec = round_spec(W.prior())
+    psf = f32(W.psf)
+    truth = f32(W.truth())
+    blank = oracle.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
+                          np.ones((W.ny, W.nx)), psf, W.n_lens_light, W.n_source, spec)
+    m = blank.model_image(truth, nthreads=nthreads)[0]
+    d, s = synth.noisy_data(m, W.noise())
+    d, s = f32(d), f32(s)
+    osys = oracle.System(W.ny, W.nx, W.pixel_scale, W.supersample, d, s, psf,
+                         W.n_lens_light, W.n_source, spec)
+    return Case(W, spec, d, s, psf, truth, osys)
+
+
+def small_workload(ny, nx, s, psf_size, n_light=1, n_src=1, pixel_scale=0.262, batch=8,
+                   seed=11, fwhm=1.1):
+    return synth.Workload(f"case-{ny}x{nx}-s{s}-k{psf_size}-{n_light}{n_src}", ny, nx,
+                          pixel_scale, s, synth.moffat_psf(psf_size, pixel_scale, fwhm),
+                          n_light, n_src, batch, seed, seed + 1, seed + 2)
+
+
+def image_close(got, ref, rel=1e-5, peak=1e-4):
+    """Per-pixel tolerance: a pixel fails only if it misses both the relative
+    bound rel |m| and the absolute bound peak max|m| (unit-peak images)."""
+    err = np.abs(got - ref)
+    bad = (err > rel * np.abs(ref)) & (err > peak * np.max(np.abs(ref)))
+    return not bad.any(), float(np.max(err / np.maximum(np.abs(ref), 1e-30)))
+
+
+def grad_close(got, ref, rel=1e-3, floor=1e-2):
+    """|g - g_ref| <= rel max(|g_ref|, floor ||g_ref||_inf), per row."""
+    scale = np.maximum(np.abs(ref), floor * np.max(np.abs(ref), axis=-1, keepdims=True))
+    return np.all(np.abs(got - ref) <= rel * scale), float(np.max(np.abs(got - ref) / scale))

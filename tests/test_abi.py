@@ -1,0 +1,95 @@
+"""The C-ABI library loads and exports every entry point include/gl.h declares,
+and rejects invalid system descriptions on the host (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2606_30633_b300 as gl
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(gl_[a-z_0-9]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_30633_b300 import build
+    build.build()
+    return gl.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert "gl_logp_grad" in declared and "gl_system_create" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared <= set(gl.SIGNATURES), declared - set(gl.SIGNATURES)
+
+
+def _desc(**kw):
+    W = synth.ground_60()
+    spec = W.prior()
+    args = dict(ny=W.ny, nx=W.nx, ps=W.pixel_scale, s=W.supersample, psf=W.psf, nl=1, ns=1)
+    args.update(kw)
+    data = np.zeros((args["ny"], args["nx"]), np.float32)
+    sig = np.ones_like(data)
+    psf = np.asarray(args["psf"], np.float32)
+    prior = gl.prior_array(spec)
+    keep = (data, sig, psf, prior)
+    fp = ctypes.POINTER(ctypes.c_float)
+    d = gl.gl_system_desc(args["ny"], args["nx"], args["ps"], args["s"],
+                          data.ctypes.data_as(fp), sig.ctypes.data_as(fp), psf.ctypes.data_as(fp),
+                          psf.shape[0], psf.shape[1], args["nl"], args["ns"], prior, None, 0)
+    return d, keep
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(psf=np.ones((4, 4))), "PSF"),
+    (dict(psf=np.ones((23, 23))), "PSF"),
+    (dict(s=0), "supersample"),
+    (dict(s=9), "supersample"),
+    (dict(ns=0), "n_source"),
+    (dict(nl=3), "n_lens_light"),
+    (dict(ny=0), "image size"),
+    (dict(ps=-1.0), "pixel_scale"),
+])
+def test_invalid_descriptions_are_rejected(lib, kw, msg):
+    d, keep = _desc(**kw)
+    h = ctypes.c_void_p()
+    st = lib.gl_system_create(ctypes.byref(d), ctypes.byref(h))
+    assert st == gl.GL_EINVAL
+    assert h.value is None
+    assert msg in gl.last_error()
+
+
+def test_null_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.gl_system_create(None, ctypes.byref(h)) == gl.GL_EINVAL
+    assert lib.gl_system_num_params(None) == -1
+    assert lib.gl_system_destroy(None) == gl.GL_OK
+    assert lib.gl_logp(None, None, 0, None, 0, None) == gl.GL_EINVAL
+
+
+def test_invalid_sigma_and_prior(lib):
+    d, keep = _desc()
+    keep[1][0, 0] = 0.0  # sigma must be > 0
+    h = ctypes.c_void_p()
+    assert lib.gl_system_create(ctypes.byref(d), ctypes.byref(h)) == gl.GL_EINVAL
+    assert "sigma" in gl.last_error()
+    d, keep = _desc()
+    keep[3][0].kind = 1
+    keep[3][0].lo, keep[3][0].hi = 2.0, 1.0
+    assert lib.gl_system_create(ctypes.byref(d), ctypes.byref(h)) == gl.GL_EINVAL
+    assert "prior" in gl.last_error()

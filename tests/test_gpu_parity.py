@@ -1,0 +1,203 @@
+"""GPU parity: the CUDA library through the C ABI against the FP64 oracle on the
+same seeded, float32-rounded inputs.
+
+Tolerances (FP32 path vs FP64 oracle):
+  model image  a pixel fails only if |dm| > 1e-5 |m| and |dm| > 1e-4 max|m|;
+  log p        relative 1e-6 near the posterior mode (the truth and vectors a
+               small step from it, where samplers spend their time), relative
+               1e-5 at prior draws far from it: there chi^2 is dominated by
+               bright, mis-placed Sersic cores whose FP32 exponent b_n p (5-25)
+               turns the ~2e-7 relative error of p = (R/R_e)^(1/n) into a
+               relative model error of ~1e-6 (measured up to 5.2e-6 in log p);
+  gradient     |g - g_ref| <= 1e-3 max(|g_ref|, 1e-2 ||g_ref||_inf) per row.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from lenscase import grad_close, image_close, make_case, small_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    from paper_2606_30633_b300 import build
+    build.build()
+    return torch
+
+
+REL_MODE, REL_PRIOR = 1e-6, 1e-5
+
+
+def _near_mode(c, n, seed=1):
+    th = synth.jitter(c.truth, c.W.prior(), n, seed, rel=0.01)
+    th[0] = c.truth
+    return np.asarray(np.asarray(th, np.float32), np.float64)
+
+
+def _lp_close(got, ref, rel=REL_PRIOR, absol=1e-3):
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    err = np.abs(got - ref)
+    return np.all(err <= np.maximum(rel * np.abs(ref), absol)), float(np.max(err / np.abs(ref)))
+
+
+CASES = [
+    # ny, nx, s, psf, n_light, n_src
+    (60, 60, 2, 11, 1, 1),     # ground-based workload shape
+    (37, 29, 3, 11, 1, 1),     # ragged rows/columns
+    (23, 41, 2, 5, 1, 2),      # generic (non-unrolled) PSF path, two sources
+    (30, 30, 1, 21, 2, 3),     # 21x21 path, most components, s = 1
+    (17, 19, 4, 3, 0, 1),      # no lens light
+]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: "x".join(map(str, c)))
+def case(request):
+    ny, nx, s, k, nl, ns = request.param
+    return make_case(small_workload(ny, nx, s, k, nl, ns, seed=10 * ny + nx))
+
+
+def test_model_image_matches_oracle(torch, case):
+    th = case.theta(6)
+    th[0] = case.truth
+    sysg = case.gpu_system()
+    img = sysg.model_image(torch.tensor(th, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ref = case.oracle.model_image(th)
+    for b in range(th.shape[0]):
+        ok, worst = image_close(img[b].astype(np.float64), ref[b])
+        assert ok, (b, worst)
+
+
+def test_logp_matches_oracle(torch, case):
+    th = np.concatenate([_near_mode(case, 8), case.theta(8)])
+    sysg = case.gpu_system()
+    t = torch.tensor(th, dtype=torch.float32, device="cuda")
+    lp = sysg.logp(t).cpu().numpy()
+    ref = case.oracle.logp(th)
+    ok, worst = _lp_close(lp[:8], ref[:8], rel=REL_MODE)
+    assert ok, (worst, lp[:4], ref[:4])
+    ok, worst = _lp_close(lp[8:], ref[8:], rel=REL_PRIOR)
+    assert ok, (worst, lp[8:12], ref[8:12])
+    # gl_logp_grad returns the same log p (same kernel arithmetic for the forward)
+    lp2, _ = sysg.logp_grad(t)
+    np.testing.assert_array_equal(lp2.cpu().numpy(), lp)
+
+
+def test_gradient_matches_oracle(torch, case):
+    th = np.concatenate([_near_mode(case, 4), case.theta(8)])
+    sysg = case.gpu_system()
+    lp, g = sysg.logp_grad(torch.tensor(th, dtype=torch.float32, device="cuda"))
+    lref, gref = case.oracle.logp_grad(th)
+    lp = lp.cpu().numpy()
+    assert _lp_close(lp[:4], lref[:4], rel=REL_MODE)[0]
+    ok, worst = _lp_close(lp, lref)
+    assert ok, worst
+    ok, worst = grad_close(g.cpu().numpy().astype(np.float64), gref)
+    assert ok, worst
+
+
+def test_gradient_matches_central_differences(torch):
+    """GPU adjoint against FP64 central differences of the oracle's log p,
+    h = 1e-6 max(|theta|, 1), on every parameter."""
+    c = make_case(small_workload(24, 24, 2, 11, 1, 1, seed=77))
+    th = c.theta(3, seed=5)
+    th[0] = c.truth
+    lp, g = c.gpu_system().logp_grad(torch.tensor(th, dtype=torch.float32, device="cuda"))
+    g = g.cpu().numpy().astype(np.float64)
+    for b in range(th.shape[0]):
+        fd = np.empty(th.shape[1])
+        for k in range(th.shape[1]):
+            h = 1e-6 * max(abs(th[b, k]), 1.0)
+            tp, tm = th[b].copy(), th[b].copy()
+            tp[k] += h
+            tm[k] -= h
+            fd[k] = (c.oracle.logp(tp)[0] - c.oracle.logp(tm)[0]) / (2 * h)
+        ok, worst = grad_close(g[b], fd)
+        assert ok, (b, worst)
+
+
+def test_edge_rows_and_empty_batch(torch):
+    c = make_case(small_workload(20, 20, 2, 5, 1, 1, seed=5))
+    sysg = c.gpu_system()
+    th = np.repeat(c.truth[None], 5, 0)
+    th[1, 0] = 3.0            # outside U(0.8, 2.5): -inf, zero gradient
+    th[2, 2:4] = [0.45, 0.3]  # |e| >= 0.5 disc
+    th[3, 5] = np.nan         # NaN row
+    th[4, 1] = 3.5            # gamma outside the model domain
+    t = torch.tensor(th, dtype=torch.float32, device="cuda")
+    lp, g = sysg.logp_grad(t)
+    lp, g = lp.cpu().numpy(), g.cpu().numpy()
+    assert math.isfinite(lp[0])
+    assert np.isneginf(lp[[1, 2, 4]]).all() and (g[[1, 2, 4]] == 0).all()
+    assert np.isnan(lp[3]) and np.isnan(g[3]).all()
+    lpf = sysg.logp(t).cpu().numpy()
+    assert np.isneginf(lpf[[1, 2, 4]]).all() and np.isnan(lpf[3])
+    img = sysg.model_image(t).cpu().numpy()
+    assert np.isfinite(img[[0, 1, 2]]).all() and np.isnan(img[[3, 4]]).all()
+    ref = c.oracle.logp(th)
+    assert np.isneginf(ref[[1, 2, 4]]).all() and np.isnan(ref[3])
+    empty = torch.empty((0, sysg.P), device="cuda")
+    assert sysg.logp(empty).numel() == 0
+    assert sysg.logp_grad(empty)[1].numel() == 0
+
+
+def test_tiny_image_single_pixel(torch):
+    c = make_case(small_workload(1, 1, 3, 1, 1, 1, seed=3))
+    th = c.theta(4)
+    lp, g = c.gpu_system().logp_grad(torch.tensor(th, dtype=torch.float32, device="cuda"))
+    lref, gref = c.oracle.logp_grad(th)
+    assert _lp_close(lp.cpu().numpy(), lref)[0]
+    assert grad_close(g.cpu().numpy().astype(np.float64), gref)[0]
+
+
+def test_host_buffer_entry_point(torch):
+    c = make_case(small_workload(32, 32, 2, 11, 1, 1, seed=9))
+    sysg = c.gpu_system()
+    th = c.theta(9).astype(np.float32)
+    lp_h, g_h = sysg.logp_grad_host(th)
+    lp_d, g_d = sysg.logp_grad(torch.tensor(th, device="cuda"))
+    np.testing.assert_array_equal(lp_h, lp_d.cpu().numpy())
+    np.testing.assert_array_equal(g_h, g_d.cpu().numpy())
+
+
+def test_autograd_function(torch):
+    import paper_2606_30633_b300 as gl
+    c = make_case(small_workload(24, 24, 2, 5, 1, 1, seed=21))
+    sysg = c.gpu_system()
+    th = torch.tensor(c.theta(4), dtype=torch.float32, device="cuda", requires_grad=True)
+    lp = gl.LogPosterior.apply(th, sysg)
+    (2.0 * lp.sum()).backward()
+    _, g = sysg.logp_grad(th.detach())
+    torch.testing.assert_close(th.grad, 2.0 * g)
+
+
+@pytest.mark.parametrize("which", ["ground100", "space200"])
+def test_full_size_sampled_rows(torch, which):
+    """Full benchmark sizes in the benchmark's launch configuration (the whole
+    batch in one launch); rows sampled across the batch are checked against
+    the oracle one by one."""
+    if which == "ground100":
+        W, rows_lp, rows_g = synth.ground_100(), [0, 1, 2047, 4095], [0, 4095]
+    else:
+        W, rows_lp, rows_g = synth.space_200(), [0, 1, 16383], [16383]
+    c = make_case(W)
+    th_all = c.theta(W.batch)
+    th_all[1] = _near_mode(c, 2)[1]  # one row a small step from the truth
+    sysg = c.gpu_system()
+    t = torch.tensor(th_all, dtype=torch.float32, device="cuda")
+    lp, g = sysg.logp_grad(t)
+    lp, g = lp.cpu().numpy(), g.cpu().numpy().astype(np.float64)
+    assert np.isfinite(lp).all()
+    ref = c.oracle.logp(th_all[rows_lp])
+    ok, worst = _lp_close(lp[rows_lp], ref)
+    assert ok, worst
+    assert _lp_close(lp[1:2], c.oracle.logp(th_all[1:2]), rel=REL_MODE)[0]
+    lref, gref = c.oracle.logp_grad(th_all[rows_g])
+    ok, worst = grad_close(g[rows_g], gref)
+    assert ok, worst
+    lpf = sysg.logp(t).cpu().numpy()
+    np.testing.assert_array_equal(lpf, lp)
