@@ -59,6 +59,7 @@ def lib() -> ctypes.CDLL:
         L.or_log_likelihood.restype = ctypes.c_double
         L.or_logp.argtypes = [sp, _dp, ctypes.c_int, _dp, ctypes.c_int]
         L.or_logp_grad.argtypes = [sp, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int]
+        L.or_model_jacobian.argtypes = [sp, _dp, _dp, _dp]
         _LIB = L
     return _LIB
 
@@ -175,6 +176,14 @@ class System:
         out = np.empty((th.shape[0], self.ny, self.nx))
         lib().or_model_image(self.ref, _d(th), th.shape[0], _d(out), nthreads)
         return out
+
+    def model_jacobian(self, theta):
+        """Model image [ny, nx] and d m / d theta [ny, nx, P] (dual numbers)."""
+        th = _f64(theta)
+        m = np.empty((self.ny, self.nx))
+        J = np.empty((self.ny, self.nx, self.P))
+        lib().or_model_jacobian(self.ref, _d(th), _d(m), _d(J))
+        return m, J
 
     def in_support(self, theta) -> bool:
         return bool(lib().or_in_support(self.ref, _d(_f64(theta))))

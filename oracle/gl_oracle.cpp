@@ -448,6 +448,34 @@ void logp_grad_dispatch(const or_system& s, const double* th, double* logp, doub
   }
 }
 
+template <int NP>
+void jacobian_one(const or_system& s, const double* th, double* m, double* J) {
+  const int P = num_params(s.n_lens_light, s.n_source);
+  std::vector<Dual<NP>> x(P);
+  for (int k = 0; k < P; ++k) {
+    x[k] = cst<NP>(th[k]);
+    x[k].d[k] = 1.0;
+  }
+  std::vector<Dual<NP>> img;
+  model_image(s, x.data(), img);
+  for (size_t p = 0; p < img.size(); ++p) {
+    m[p] = img[p].v;
+    for (int k = 0; k < P; ++k) J[p * P + k] = img[p].d[k];
+  }
+}
+
+void jacobian_dispatch(const or_system& s, const double* th, double* m, double* J) {
+  switch (s.n_lens_light + s.n_source) {
+    case 1: jacobian_one<15>(s, th, m, J); break;
+    case 2: jacobian_one<22>(s, th, m, J); break;
+    case 3: jacobian_one<29>(s, th, m, J); break;
+    case 4: jacobian_one<36>(s, th, m, J); break;
+    case 5: jacobian_one<43>(s, th, m, J); break;
+    case 6: jacobian_one<50>(s, th, m, J); break;
+    default: break;
+  }
+}
+
 void set_threads(int nthreads) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -541,6 +569,12 @@ void or_logp_grad(const or_system* s, const double* theta, int B, double* logp, 
 #pragma omp parallel for schedule(dynamic, 1)
   for (int b = 0; b < B; ++b)
     logp_grad_dispatch(*s, theta + (size_t)b * P, logp + b, grad + (size_t)b * P);
+}
+
+// Model image m [ny*nx] and its Jacobian J [ny*nx][P] = d m / d theta (dual
+// numbers) for one parameter vector.
+void or_model_jacobian(const or_system* s, const double* theta, double* m, double* J) {
+  jacobian_dispatch(*s, theta, m, J);
 }
 
 int or_max_threads(void) {

@@ -80,14 +80,40 @@ __device__ __forceinline__ void correlate(const SysParams& sp, const float* in, 
 }
 
 // Zero the halo of a padded buffer (the interior is written by a phase).
-__device__ __forceinline__ void zero_halo(const SysParams& sp, float* buf) {
+// first_thread: the threads taking part start at this index (warp 0 may be busy).
+__device__ __forceinline__ void zero_halo(const SysParams& sp, float* buf, int first_thread) {
   const int Hp = sp.Hp, Wp = sp.Wp;
-  for (int idx = threadIdx.x; idx < Hp * Wp; idx += THREADS) {
-    const int r = idx / Wp, c = idx - r * Wp;
-    const bool inside = r >= sp.cy && r < sp.cy + sp.ny && c >= sp.cx && c < sp.cx + sp.nx;
-    if (!inside) buf[idx] = 0.f;
+  const int t0 = (int)threadIdx.x - first_thread, nt = THREADS - first_thread;
+  if (t0 < 0) return;
+  const int top = sp.cy * Wp;                        // rows [0, cy)
+  const int bot0 = (sp.cy + sp.ny) * Wp, bot = Hp * Wp - bot0;  // rows [cy+ny, Hp)
+  for (int k = t0; k < top; k += nt) buf[k] = 0.f;
+  for (int k = t0; k < bot; k += nt) buf[bot0 + k] = 0.f;
+  const int side = Wp - sp.nx;                       // halo columns per interior row
+  if (side > 0) {
+    for (int k = t0; k < sp.ny * side; k += nt) {
+      const int r = k / side, c = k - r * side;
+      const int col = c < sp.cx ? c : c + sp.nx;
+      buf[(size_t)(r + sp.cy) * Wp + col] = 0.f;
+    }
   }
 }
+
+// Pixel (i, j) walk for p = threadIdx.x + it * THREADS without a division per step.
+struct PixelWalk {
+  int i, j, di, dj, nx;
+  __device__ __forceinline__ PixelWalk(int nx_) : nx(nx_) {
+    i = (int)threadIdx.x / nx_;
+    j = (int)threadIdx.x - i * nx_;
+    di = THREADS / nx_;
+    dj = THREADS - di * nx_;
+  }
+  __device__ __forceinline__ void next() {
+    i += di;
+    j += dj;
+    if (j >= nx) { j -= nx; ++i; }
+  }
+};
 
 // ---------------------------------------------------------- reductions ----
 __device__ __forceinline__ double block_sum_double(double v, double* red) {
@@ -190,6 +216,7 @@ __device__ __forceinline__ void subpixel_adjoint(const SampleC& sc, const EplC& 
 // ---------------------------------------------------------------- kernels ----
 struct SmemStatic {
   SampleC sc;
+  FinishC fin[MAX_COMP + 1];
   double red[NWARPS];
   float redP[NWARPS][MAX_P];
   double gsum[MAX_P];
@@ -218,10 +245,12 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
   const int b = blockIdx.x;
   if (b >= B) return;
   const bool want_img = img != nullptr;
-  if (threadIdx.x == 0) stage_sample(sp, theta + (size_t)b * sp.P, sc, !want_img);
   float *A, *Bf;
   buffers(sp, dsm, false, A, Bf);
-  zero_halo(sp, A);
+  if (threadIdx.x < 32)
+    stage_warp(sp, theta + (size_t)b * sp.P, sc, st.fin, !want_img);
+  else
+    zero_halo(sp, A, 32);
   __syncthreads();
   const int npix = sp.ny * sp.nx;
   if (sc.status != 0) {
@@ -238,9 +267,9 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
   for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
   const int s = sp.s;
   const float D = sp.D;
-  for (int p = threadIdx.x; p < npix; p += THREADS) {
-    const int i = p / sp.nx, j = p - i * sp.nx;
-    const float xj = (float)j + sp.xg0, yi = (float)i + sp.yg0;
+  PixelWalk pw(sp.nx);
+  for (int p = threadIdx.x; p < npix; p += THREADS, pw.next()) {
+    const float xj = (float)pw.j + sp.xg0, yi = (float)pw.i + sp.yg0;
     float acc = 0.f;
     for (int k = 0; k < s; ++k) {
       const float y = (yi + sp.off[k]) * D;
@@ -249,7 +278,7 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
         acc += surface_brightness<NL, NS>(sc, e, L, x, y);
       }
     }
-    A[(size_t)(i + sp.cy) * sp.Wp + j + sp.cx] = acc * sp.scale;
+    A[(size_t)(pw.i + sp.cy) * sp.Wp + pw.j + sp.cx] = acc * sp.scale;
   }
   __syncthreads();
   float csum = 0.f, ccomp = 0.f;
@@ -283,11 +312,15 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
   const int b = blockIdx.x;
   if (b >= B) return;
   const float* th = theta + (size_t)b * P;
-  if (threadIdx.x == 0) stage_sample(sp, th, sc, true);
   float *A, *Bf;
   buffers(sp, dsm, true, A, Bf);
-  zero_halo(sp, A);
-  zero_halo(sp, Bf);
+  if (threadIdx.x < 32) {
+    stage_warp(sp, th, sc, st.fin, true);
+  } else {
+    zero_halo(sp, A, 32);
+    zero_halo(sp, Bf, 32);
+  }
+  for (int k = threadIdx.x; k < NWARPS * MAX_P; k += THREADS) (&st.redP[0][0])[k] = 0.f;
   __syncthreads();
   const int npix = sp.ny * sp.nx;
   if (sc.status != 0) {
@@ -305,18 +338,20 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
   const float D = sp.D;
   const int Wp = sp.Wp, cy = sp.cy, cx = sp.cx, nx = sp.nx;
   // phase 1
-  for (int p = threadIdx.x; p < npix; p += THREADS) {
-    const int i = p / nx, j = p - i * nx;
-    const float xj = (float)j + sp.xg0, yi = (float)i + sp.yg0;
-    float acc = 0.f;
-    for (int k = 0; k < s; ++k) {
-      const float y = (yi + sp.off[k]) * D;
-      for (int l = 0; l < s; ++l) {
-        const float x = (xj + sp.off[l]) * D;
-        acc += surface_brightness<NL, NS>(sc, e, L, x, y);
+  {
+    PixelWalk pw(nx);
+    for (int p = threadIdx.x; p < npix; p += THREADS, pw.next()) {
+      const float xj = (float)pw.j + sp.xg0, yi = (float)pw.i + sp.yg0;
+      float acc = 0.f;
+      for (int k = 0; k < s; ++k) {
+        const float y = (yi + sp.off[k]) * D;
+        for (int l = 0; l < s; ++l) {
+          const float x = (xj + sp.off[l]) * D;
+          acc += surface_brightness<NL, NS>(sc, e, L, x, y);
+        }
       }
+      A[(size_t)(pw.i + cy) * Wp + pw.j + cx] = acc * sp.scale;
     }
-    A[(size_t)(i + cy) * Wp + j + cx] = acc * sp.scale;
   }
   __syncthreads();
   // phase 2
@@ -339,30 +374,39 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
     A[(size_t)(i + cy) * Wp + j + cx] = g * scale;
   });
   __syncthreads();
-  // phase 4
+  // phase 4: per-thread FP32 sums are flushed into per-warp sums every
+  // FLUSH_PIX pixels, which bounds the FP32 accumulation length (the
+  // gradient is a small difference of large sums near the mode)
+  constexpr int FLUSH_PIX = 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float acc[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) acc[k] = 0.f;
-  for (int p = threadIdx.x; p < npix; p += THREADS) {
-    const int i = p / nx, j = p - i * nx;
-    const float u = A[(size_t)(i + cy) * Wp + j + cx];
-    const float xj = (float)j + sp.xg0, yi = (float)i + sp.yg0;
-    for (int k = 0; k < s; ++k) {
-      const float y = (yi + sp.off[k]) * D;
-      for (int l = 0; l < s; ++l) {
-        const float x = (xj + sp.off[l]) * D;
-        subpixel_adjoint<NL, NS>(sc, e, L, x, y, u, acc);
+  const int iters = (npix + THREADS - 1) / THREADS;  // same trip count in every lane
+  PixelWalk pw(nx);
+  for (int it = 0; it < iters; ++it, pw.next()) {
+    const int p = threadIdx.x + it * THREADS;
+    if (p < npix) {
+      const float u = A[(size_t)(pw.i + cy) * Wp + pw.j + cx];
+      const float xj = (float)pw.j + sp.xg0, yi = (float)pw.i + sp.yg0;
+      for (int k = 0; k < s; ++k) {
+        const float y = (yi + sp.off[k]) * D;
+        for (int l = 0; l < s; ++l) {
+          const float x = (xj + sp.off[l]) * D;
+          subpixel_adjoint<NL, NS>(sc, e, L, x, y, u, acc);
+        }
       }
     }
-  }
-  // reduction
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if ((it + 1) % FLUSH_PIX == 0 || it + 1 == iters) {
 #pragma unroll
-  for (int k = 0; k < P; ++k) {
-    float v = acc[k];
+      for (int k = 0; k < P; ++k) {
+        float v = acc[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) st.redP[warp][k] = v;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) st.redP[warp][k] += v;
+        acc[k] = 0.f;
+      }
+    }
   }
   __syncthreads();
   if (threadIdx.x < P) {
@@ -371,15 +415,22 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
     st.gsum[threadIdx.x] = v;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double v[P], g[P];
-    for (int k = 0; k < P; ++k) v[k] = (double)th[k];
-    epl_finish(v, st.gsum, g);
+  // chain rule to the parameters, one lane per component
+  if (threadIdx.x <= NL + NS) {
+    const int c = threadIdx.x;
+    float g[8];
+    if (c == 0) {
+      epl_finish(st.fin[0], st.gsum, g);
 #pragma unroll
-    for (int c = 0; c < NL + NS; ++c) sersic_finish(v + 8 + 7 * c, st.gsum + 8 + 7 * c, g + 8 + 7 * c);
-    for (int k = 0; k < P; ++k) grad[(size_t)b * P + k] = (float)(g[k] + (double)sc.dprior[k]);
-    logp[b] = (float)(-0.5 * chi2 + sc.logprior);
+      for (int k = 0; k < 8; ++k) grad[(size_t)b * P + k] = g[k] + sc.dprior[k];
+    } else {
+      const int o = 8 + 7 * (c - 1);
+      sersic_finish(st.fin[c], st.gsum + o, g);
+#pragma unroll
+      for (int k = 0; k < 7; ++k) grad[(size_t)b * P + o + k] = g[k] + sc.dprior[o + k];
+    }
   }
+  if (threadIdx.x == 0) logp[b] = (float)(-0.5 * chi2 + sc.logprior);
 }
 
 }  // namespace gl

@@ -89,155 +89,182 @@ struct SampleC {
 
 __device__ __forceinline__ int ellip_index(int c) { return c == 0 ? 2 : 8 + 7 * (c - 1) + 2; }
 
-// Stages one sample: checks NaN, domain and prior support, evaluates the log
-// prior (and its gradient), and the per-sample constants of every component.
-// Runs on one thread in double precision. check_prior = false skips the
-// prior (model-image rendering).
-__device__ inline void stage_sample(const SysParams& sp, const float* __restrict__ th,
-                                    SampleC& sc, bool check_prior) {
+// Per-component constants kept for the gradient's chain rule at the end.
+struct FinishC {
+  float e1, e2, c, cs, sn, q;
+  float p0;         // theta_E (EPL) or R_e (Sersic)
+  float n, I, bn;   // Sersic index, intensity, b_n (unused for the EPL)
+  float t;          // EPL t = gamma - 1
+};
+
+// Stages one sample on warp 0 (all 32 lanes call it): NaN, domain and prior
+// support checks, the log prior and its gradient (one lane per parameter),
+// per-component constants (one lane per component) and the EPL series
+// coefficients (a warp prefix product). FP32 with IEEE-accurate library
+// functions; the prior's normalisation constants and the log-prior sum are
+// FP64. Writes sc.status last (0 ok, 1 -inf, 2 NaN).
+__device__ inline void stage_warp(const SysParams& sp, const float* __restrict__ th, SampleC& sc,
+                                  FinishC* fin, bool check_prior) {
+  const int lane = threadIdx.x & 31;
   const int P = sp.P;
   const int nc = sp.nL + sp.nS;
-  double v[MAX_P];
-  for (int k = 0; k < P; ++k) {
-    v[k] = (double)th[k];
-    if (isnan(v[k])) { sc.status = 2; return; }
+  // NaN
+  bool nan = false;
+  for (int k = lane; k < P; k += 32) nan |= isnan(th[k]);
+  if (__any_sync(0xffffffffu, nan)) {
+    if (lane == 0) sc.status = 2;
+    return;
   }
-  sc.status = 1;
-  if (!(v[0] > 0.0)) return;
-  if (!(v[1] > 1.0 && v[1] < 3.0)) return;
-  for (int c = 0; c <= nc; ++c) {
-    const int i1 = ellip_index(c);
-    const double e = sqrt(v[i1] * v[i1] + v[i1 + 1] * v[i1 + 1]);
-    if (!(e < E_DOMAIN)) return;
+  // domain (one lane per component)
+  bool bad = false;
+  if (lane <= nc) {
+    const int i1 = ellip_index(lane);
+    const float e1 = th[i1], e2 = th[i1 + 1];
+    const double e = sqrt((double)e1 * e1 + (double)e2 * e2);
+    if (!(e < E_DOMAIN)) bad = true;
     if (check_prior && sp.emax) {
-      const double em = (double)sp.emax[c];
-      if (em > 0.0 && !(e < em)) return;
+      const double em = (double)sp.emax[lane];
+      if (em > 0.0 && !(e < em)) bad = true;
     }
-    if (c > 0) {
-      if (!(v[i1 - 2] > 0.0)) return;
-      if (!(v[i1 - 1] >= N_SERSIC_MIN)) return;
+    if (lane == 0) {
+      if (!(th[0] > 0.f) || !(th[1] > 1.f && th[1] < 3.f)) bad = true;
+    } else {
+      if (!(th[i1 - 2] > 0.f) || !((double)th[i1 - 1] >= N_SERSIC_MIN)) bad = true;
     }
   }
+  // prior (one lane per parameter)
   double lp = 0.0;
   if (check_prior) {
-    for (int k = 0; k < P; ++k) {
+    for (int k = lane; k < P; k += 32) {
       const PriorDev pr = sp.prior[k];
-      const double x = v[k], a = pr.a, b = pr.b;
-      double d = 0.0;
+      const float x = th[k];
+      float d = 0.f;
       switch (pr.kind) {
         case 0:
-          if (!(x >= (double)pr.lo && x <= (double)pr.hi)) return;
+          if (!(x >= pr.lo && x <= pr.hi)) bad = true;
           break;
         case 1:
-          if (!(x >= (double)pr.lo && x <= (double)pr.hi)) return;
+          if (!(x >= pr.lo && x <= pr.hi)) bad = true;
           lp += pr.cnst;
           break;
         case 2: {
-          const double z = (x - a) / b;
-          lp += -0.5 * z * z + pr.cnst;
-          d = -z / b;
+          const float z = (x - pr.a) / pr.b;
+          lp += (double)(-0.5f * z * z) + pr.cnst;
+          d = -z / pr.b;
           break;
         }
         case 3: {
-          if (!(x >= (double)pr.lo && x <= (double)pr.hi)) return;
-          const double z = (x - a) / b;
-          lp += -0.5 * z * z + pr.cnst;
-          d = -z / b;
+          if (!(x >= pr.lo && x <= pr.hi)) bad = true;
+          const float z = (x - pr.a) / pr.b;
+          lp += (double)(-0.5f * z * z) + pr.cnst;
+          d = -z / pr.b;
           break;
         }
         case 4: {
-          if (!(x > 0.0)) return;
-          const double lx = log(x);
-          const double z = (lx - a) / b;
-          lp += -0.5 * z * z - lx + pr.cnst;
-          d = (-z / b - 1.0) / x;
+          if (!(x > 0.f)) { bad = true; break; }
+          const float lx = logf(x);
+          const float z = (lx - pr.a) / pr.b;
+          lp += (double)(-0.5f * z * z) - (double)lx + pr.cnst;
+          d = (-z / pr.b - 1.f) / x;
           break;
         }
         default: break;
       }
-      sc.dprior[k] = (float)d;
+      sc.dprior[k] = d;
     }
   }
-  sc.logprior = lp;
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) sc.status = 1;
+    return;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
 
-  // EPL
-  {
-    EplC& E = sc.epl;
-    const double e1 = v[2], e2 = v[3];
-    const double c = sqrt(e1 * e1 + e2 * e2);
-    const double q = (1.0 - c) / (1.0 + c);
-    const double phi = 0.5 * atan2(e2, e1);
-    const double t = v[1] - 1.0;
-    const double b = v[0] * sqrt(q);
-    E.xc = (float)v[4];
-    E.yc = (float)v[5];
-    E.cs = (float)cos(phi);
-    E.sn = (float)sin(phi);
-    E.q = (float)q;
-    E.q2 = (float)(q * q);
-    E.f = (float)c;
-    E.ht = (float)(0.5 * (1.0 - t));
-    E.CA = (float)(2.0 * pow(b, t) / (1.0 + q));
-    E.t = (float)t;
-    E.omt = (float)(1.0 - t);
-    E.tmt = (float)(2.0 - t);
-    E.Kk = (float)((2.0 - t) * (1.0 + q) / 4.0);
-    E.a0 = (float)(t / (2.0 * q) - 1.0 / (1.0 + q));
-    E.lnb = (float)log(b);
-    E.dfdq = (float)(-2.0 / ((1.0 + q) * (1.0 + q)));
-    // terms: smallest N >= 1 with f^N <= 2^-24 (1-f)^2 / 2 (tails of E, F and F')
-    const double tol = SERIES_EPS * (1.0 - c) * (1.0 - c) * 0.5;
-    int N = 1;
-    double fn = c;
-    while (fn > tol && N < N_MAX) { fn *= c; ++N; }
-    const int nq = (N + 3) / 4;
-    sc.nq = nq;
-    float* ce = reinterpret_cast<float*>(sc.cE);
-    float* ct = reinterpret_cast<float*>(sc.cT);
-    double cn = 1.0, hn = 0.0, pw = 1.0;
-    for (int n = 1; n <= 4 * nq; ++n) {
-      if (n <= N) {
-        cn *= (2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
-        hn += 1.0 / (2.0 * n - 2.0 + t) + 1.0 / (2.0 * n + 2.0 - t);
-        ce[n - 1] = (float)(cn * pw);
-        ct[n - 1] = (float)(cn * hn * pw);
-        pw *= -c;
-      } else {
-        ce[n - 1] = 0.f;
-        ct[n - 1] = 0.f;
-      }
+  // per-component constants
+  float t_epl = 0.f, f_epl = 0.f;
+  if (lane <= nc) {
+    const int i1 = ellip_index(lane);
+    const float e1 = th[i1], e2 = th[i1 + 1];
+    const float c = sqrtf(e1 * e1 + e2 * e2);
+    const float q = (1.f - c) / (1.f + c);
+    float sn, cs;
+    sincosf(0.5f * atan2f(e2, e1), &sn, &cs);
+    FinishC& F = fin[lane];
+    F.e1 = e1; F.e2 = e2; F.c = c; F.cs = cs; F.sn = sn; F.q = q;
+    if (lane == 0) {
+      EplC& E = sc.epl;
+      const float t = th[1] - 1.f;
+      const float b = th[0] * sqrtf(q);
+      E.xc = th[4]; E.yc = th[5]; E.cs = cs; E.sn = sn;
+      E.q = q; E.q2 = q * q; E.f = c; E.ht = 0.5f * (1.f - t);
+      E.CA = 2.f * powf(b, t) / (1.f + q);
+      E.t = t; E.omt = 1.f - t; E.tmt = 2.f - t;
+      E.Kk = (2.f - t) * (1.f + q) * 0.25f;
+      E.a0 = t / (2.f * q) - 1.f / (1.f + q);
+      E.lnb = logf(b);
+      E.dfdq = -2.f / ((1.f + q) * (1.f + q));
+      F.p0 = th[0]; F.t = t; F.n = 0.f; F.I = 0.f; F.bn = 0.f;
+      t_epl = t;
+      f_epl = c;
+      sc.g1 = th[6];
+      sc.g2 = th[7];
+    } else {
+      LightC& L = sc.light[lane - 1];
+      const float* p = th + 8 + 7 * (lane - 1);
+      const float Re = p[0], n = p[1];
+      const float bn = 1.9992f * n - 0.3271f;
+      L.xc = p[4]; L.yc = p[5]; L.cs = cs; L.sn = sn;
+      L.q = q; L.iq = 1.f / q; L.iq2 = 1.f / (q * q);
+      L.c1 = 0.5f / n;
+      L.c0 = -log2f(Re) / n;
+      L.bl = bn * 1.4426950408889634f;
+      L.Ip = p[6] * expf(bn);
+      const float m = -bn / n;
+      L.kX1 = m * q * cs; L.kX2 = -m * sn / q;
+      L.kY1 = m * q * sn; L.kY2 = m * cs / q;
+      F.p0 = Re; F.n = n; F.I = p[6]; F.bn = bn; F.t = 0.f;
     }
   }
-  sc.g1 = (float)v[6];
-  sc.g2 = (float)v[7];
-  for (int k = 0; k < nc; ++k) {
-    LightC& L = sc.light[k];
-    const double* p = v + 8 + 7 * k;
-    const double e1 = p[2], e2 = p[3];
-    const double c = sqrt(e1 * e1 + e2 * e2);
-    const double q = (1.0 - c) / (1.0 + c);
-    const double phi = 0.5 * atan2(e2, e1);
-    const double n = p[1], Re = p[0];
-    const double bn = 1.9992 * n - 0.3271;
-    const double cs = cos(phi), sn = sin(phi);
-    L.xc = (float)p[4];
-    L.yc = (float)p[5];
-    L.cs = (float)cs;
-    L.sn = (float)sn;
-    L.q = (float)q;
-    L.iq = (float)(1.0 / q);
-    L.iq2 = (float)(1.0 / (q * q));
-    L.c1 = (float)(0.5 / n);
-    L.c0 = (float)(-log2(Re) / n);
-    L.bl = (float)(bn / LN2);
-    L.Ip = (float)(p[6] * exp(bn));
-    const double m = -bn / n;
-    L.kX1 = (float)(m * q * cs);
-    L.kX2 = (float)(-m * sn / q);
-    L.kY1 = (float)(m * q * sn);
-    L.kY2 = (float)(m * cs / q);
+  t_epl = __shfl_sync(0xffffffffu, t_epl, 0);
+  f_epl = __shfl_sync(0xffffffffu, f_epl, 0);
+  // series length: smallest N >= 1 with f^N <= 2^-24 (1-f)^2 / 2
+  int N = 1;
+  {
+    const float tol = (float)SERIES_EPS * (1.f - f_epl) * (1.f - f_epl) * 0.5f;
+    float fn = f_epl;
+    while (fn > tol && N < N_MAX) { fn *= f_epl; ++N; }
   }
-  sc.status = 0;
+  const int nq = (N + 3) >> 2;
+  // coefficients: e_n = c_n (-f)^{n-1} = prod_{k<=n} rho_k, rho_1 = r_1,
+  // rho_k = -f r_k, r_k = (2k-2+t)/(2k+2-t); t_n = e_n h_n, h_n = sum_k
+  // 1/(2k-2+t) + 1/(2k+2-t): inclusive warp scans of products and sums.
+  float* ce = reinterpret_cast<float*>(sc.cE);
+  float* ct = reinterpret_cast<float*>(sc.cT);
+  float carry_e = 1.f, carry_h = 0.f;
+  for (int base = 0; base < 4 * nq; base += 32) {
+    const int n = base + lane + 1;
+    const float a = 2.f * n - 2.f + t_epl, bb = 2.f * n + 2.f - t_epl;
+    float rho = (n == 1 ? 1.f : -f_epl) * (a / bb);
+    float hin = 1.f / a + 1.f / bb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float r2 = __shfl_up_sync(0xffffffffu, rho, o);
+      const float h2 = __shfl_up_sync(0xffffffffu, hin, o);
+      if (lane >= o) { rho *= r2; hin += h2; }
+    }
+    const float en = carry_e * rho, hn = carry_h + hin;
+    if (n <= 4 * nq) {
+      ce[n - 1] = n <= N ? en : 0.f;
+      ct[n - 1] = n <= N ? en * hn : 0.f;
+    }
+    carry_e = __shfl_sync(0xffffffffu, en, 31);
+    carry_h = __shfl_sync(0xffffffffu, hn, 31);
+  }
+  if (lane == 0) {
+    sc.nq = nq;
+    sc.logprior = lp;
+    sc.status = 0;
+  }
 }
 
 // ---- forward pieces ----
@@ -353,55 +380,43 @@ __device__ __forceinline__ float sersic_adj(const LightC& c, float X, float Y, f
   return S;
 }
 
-// Converts a Sersic component's native accumulators to gradients w.r.t.
-// [R_e, n, e1, e2, x, y, I_e] (double precision, once per sample).
-__device__ inline void sersic_finish(const double* p, const double* a, double* g) {
-  const double Re = p[0], n = p[1], e1 = p[2], e2 = p[3], I = p[6];
-  const double c = sqrt(e1 * e1 + e2 * e2);
-  const double q = (1.0 - c) / (1.0 + c);
-  const double phi = 0.5 * atan2(e2, e1);
-  const double cs = cos(phi), sn = sin(phi);
-  const double bn = 1.9992 * n - 0.3271;
-  const double m = -bn / n;
-  const double dI = a[0] / I;
-  const double dRe = bn / (n * Re) * a[1];
-  const double dn = -1.9992 * (a[1] - a[0]) + bn * LN2 / n * a[2];
-  const double dq = 0.5 * m * a[3];
-  const double dphi = m * (q - 1.0 / q) * a[4];
-  const double Sx = m * q * a[5], Sy = m * a[6] / q;  // sum u dS/dx', sum u dS/dy'
-  const double dxc = -(cs * Sx - sn * Sy);
-  const double dyc = -(sn * Sx + cs * Sy);
-  const double cc = c > 1e-30 ? c : 1e-30;
-  const double dqdc = -2.0 / ((1.0 + c) * (1.0 + c));
-  g[0] = dRe;
-  g[1] = dn;
-  g[2] = dq * dqdc * (e1 / cc) - dphi * e2 / (2.0 * cc * cc);
-  g[3] = dq * dqdc * (e2 / cc) + dphi * e1 / (2.0 * cc * cc);
-  g[4] = dxc;
-  g[5] = dyc;
-  g[6] = dI;
+// Converts a Sersic component's native accumulators a[0..6] to gradients
+// w.r.t. [R_e, n, e1, e2, x, y, I_e] (one lane per component).
+__device__ inline void sersic_finish(const FinishC& F, const double* a, float* g) {
+  const float m = -F.bn / F.n;
+  const float A0 = (float)a[0], A1 = (float)a[1], A2 = (float)a[2], A3 = (float)a[3];
+  const float A4 = (float)a[4], A5 = (float)a[5], A6 = (float)a[6];
+  const float dq = 0.5f * m * A3;
+  const float dphi = m * (F.q - 1.f / F.q) * A4;
+  const float Sx = m * F.q * A5, Sy = m * A6 / F.q;  // sum u dS/dx', sum u dS/dy'
+  const float cc = fmaxf(F.c, 1e-30f);
+  const float dqdc = -2.f / ((1.f + F.c) * (1.f + F.c));
+  g[0] = F.bn / (F.n * F.p0) * A1;
+  g[1] = -1.9992f * (A1 - A0) + F.bn * 0.69314718f / F.n * A2;
+  g[2] = dq * dqdc * (F.e1 / cc) - dphi * F.e2 / (2.f * cc * cc);
+  g[3] = dq * dqdc * (F.e2 / cc) + dphi * F.e1 / (2.f * cc * cc);
+  g[4] = -(F.cs * Sx - F.sn * Sy);
+  g[5] = -(F.sn * Sx + F.cs * Sy);
+  g[6] = A0 / F.I;
 }
 
 // EPL + shear native accumulators:
 // [0] sum s1 (theta_E), [1] d/dt, [2] d/dq, [3] d/dphi, [4] sum v.d alpha/dx',
 // [5] sum v.d alpha/dy' (lens frame; the centre gradient is minus these),
 // [6] d/dg1, [7] d/dg2.
-__device__ inline void epl_finish(const double* v, const double* a, double* g) {
-  const double thetaE = v[0], t = v[1] - 1.0, e1 = v[2], e2 = v[3];
-  const double c = sqrt(e1 * e1 + e2 * e2);
-  const double phi = 0.5 * atan2(e2, e1);
-  const double cs = cos(phi), sn = sin(phi);
-  const double gxl = -a[4], gyl = -a[5];
-  const double cc = c > 1e-30 ? c : 1e-30;
-  const double dqdc = -2.0 / ((1.0 + c) * (1.0 + c));
-  g[0] = t / thetaE * a[0];
-  g[1] = a[1];
-  g[2] = a[2] * dqdc * (e1 / cc) - a[3] * e2 / (2.0 * cc * cc);
-  g[3] = a[2] * dqdc * (e2 / cc) + a[3] * e1 / (2.0 * cc * cc);
-  g[4] = cs * gxl - sn * gyl;
-  g[5] = sn * gxl + cs * gyl;
-  g[6] = a[6];
-  g[7] = a[7];
+__device__ inline void epl_finish(const FinishC& F, const double* a, float* g) {
+  const float gxl = -(float)a[4], gyl = -(float)a[5];
+  const float cc = fmaxf(F.c, 1e-30f);
+  const float dqdc = -2.f / ((1.f + F.c) * (1.f + F.c));
+  const float dq = (float)a[2], dphi = (float)a[3];
+  g[0] = F.t / F.p0 * (float)a[0];
+  g[1] = (float)a[1];
+  g[2] = dq * dqdc * (F.e1 / cc) - dphi * F.e2 / (2.f * cc * cc);
+  g[3] = dq * dqdc * (F.e2 / cc) + dphi * F.e1 / (2.f * cc * cc);
+  g[4] = F.cs * gxl - F.sn * gyl;
+  g[5] = F.sn * gxl + F.cs * gyl;
+  g[6] = (float)a[6];
+  g[7] = (float)a[7];
 }
 
 }  // namespace gl

@@ -77,3 +77,29 @@ def grad_close(got, ref, rel=1e-3, floor=1e-2):
     """|g - g_ref| <= rel max(|g_ref|, floor ||g_ref||_inf), per row."""
     scale = np.maximum(np.abs(ref), floor * np.max(np.abs(ref), axis=-1, keepdims=True))
     return np.all(np.abs(got - ref) <= rel * scale), float(np.max(np.abs(got - ref) / scale))
+
+
+EPS_MODEL = 5e-6  # per-pixel relative FP32 model error the bounds allow for
+
+
+def grad_bound(case: "Case", th: np.ndarray, rel=1e-3, eps=EPS_MODEL) -> np.ndarray:
+    """Per-row, per-parameter gradient tolerance: rel |g_ref| plus the
+    first-order gradient change that a per-pixel relative model error eps
+    (in m and in dm/dtheta) can cause,
+        eps sum_p (|m_p| + |d_p - m_p|) |dm_p/dtheta_k| / sigma_p^2,
+    from the oracle's FP64 Jacobian. Near the mode the gradient is a small
+    difference of large sums, so this term, not rel, sets the bound there."""
+    th = np.atleast_2d(th)
+    out = np.empty_like(th)
+    w = 1.0 / case.sigma ** 2
+    _, gref = case.oracle.logp_grad(th)
+    for b in range(th.shape[0]):
+        m, J = case.oracle.model_jacobian(th[b])
+        wt = w * (np.abs(m) + np.abs(case.data - m))
+        out[b] = rel * np.abs(gref[b]) + eps * np.einsum("ij,ijk->k", wt, np.abs(J))
+    return out
+
+
+def grad_close_bound(got, ref, bound):
+    err = np.abs(np.asarray(got, np.float64) - ref)
+    return bool(np.all(err <= bound)), float(np.max(err / bound))

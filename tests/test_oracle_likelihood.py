@@ -96,3 +96,24 @@ def test_dual_gradient_matches_central_differences(which):
     err = np.abs(g - fd)
     assert np.all(err <= 1e-5 * np.maximum(np.abs(fd), 1e-3 * scale)), (g, fd)
     assert lp[0] == pytest.approx(S.logp(th)[0], rel=1e-14)
+
+
+def test_jacobian_is_consistent_with_gradient_and_differences():
+    """d logp/d theta = sum_p (d_p - m_p)/sigma_p^2 dm_p/dtheta + dlog prior, and
+    the Jacobian matches central differences of the model image."""
+    S, th0, spec, m, sig = _small(12, 12, 2)
+    th = synth.draw(spec, 1, 8)[0]
+    mm, J = S.model_jacobian(th)
+    np.testing.assert_allclose(mm, S.model_image(th)[0], rtol=1e-14)
+    lp, g = S.logp_grad(th)
+    gp = np.empty_like(th)
+    for k in range(th.size):  # prior gradient by differences of the log prior
+        h = 1e-6 * max(abs(th[k]), 1.0)
+        tp, tm = th.copy(), th.copy()
+        tp[k] += h
+        tm[k] -= h
+        gp[k] = (S.log_prior(tp) - S.log_prior(tm)) / (2 * h)
+        fd = (S.model_image(tp)[0] - S.model_image(tm)[0]) / (2 * h)
+        np.testing.assert_allclose(J[:, :, k], fd, rtol=1e-5, atol=1e-7 * np.abs(fd).max() + 1e-12)
+    gl = np.einsum("ij,ijk->k", (S.data - mm) / S.sigma ** 2, J)
+    np.testing.assert_allclose(g[0], gl + gp, rtol=1e-6, atol=1e-6 * np.abs(g).max())
