@@ -207,8 +207,13 @@ __device__ __forceinline__ void subpixel_adjoint(const SampleC& sc, const EplC& 
   acc[0] += s1;
   acc[1] = fmaf(s1, e.lnb - lnR, acc[1] + sT);
   acc[2] = fmaf(s1, fmaf(e.omt * e.q * xp * xp, iR2, e.a0), fmaf(S13, dphq, fmaf(-e.dfdq, s3, acc[2])));
+  // rotation: d alpha'/d phi = i X with X = (2-t) alpha' - 2 kappa z' =
+  // -2 kappa f (z' w E + conj(z') F), which is O(f); acc[3] = sum kappa v.(iY)
   const float kap = e.Kk * A * ir;
-  acc[3] = fmaf(e.tmt, s1i, fmaf(-2.f * kap, fmaf(xp, vLy, -yp * vLx), acc[3]));
+  const float zwr = fmaf(xp, wr, -yp * wi), zwi = fmaf(xp, wi, yp * wr);  // z' w
+  const float Yr = fmaf(zwr, Er, fmaf(-zwi, Ei, fmaf(xp, Fr, yp * Fi)));
+  const float Yi = fmaf(zwr, Ei, fmaf(zwi, Er, fmaf(xp, Fi, -yp * Fr)));
+  acc[3] = fmaf(kap, fmaf(vLy, Yr, -vLx * Yi), acc[3]);
   acc[4] = fmaf(iR2, fmaf(e.omt * e.q2 * xp, s1, -e.q * yp * S13), acc[4]);
   acc[5] = fmaf(iR2, fmaf(e.omt * yp, s1, e.q * xp * S13), acc[5]);
 }

@@ -386,33 +386,39 @@ __device__ inline void sersic_finish(const FinishC& F, const double* a, float* g
   const float m = -F.bn / F.n;
   const float A0 = (float)a[0], A1 = (float)a[1], A2 = (float)a[2], A3 = (float)a[3];
   const float A4 = (float)a[4], A5 = (float)a[5], A6 = (float)a[6];
+  // d/dphi = m (q - 1/q) A4 with q - 1/q = -4c/(1-c^2); d phi/d e = (-e2, e1)/(2c^2),
+  // so the rotation part of d/de is 2 m A4 (sin 2phi, -cos 2phi)/(1-c^2) (no 1/c)
   const float dq = 0.5f * m * A3;
-  const float dphi = m * (F.q - 1.f / F.q) * A4;
+  const float rot = 2.f * m * A4 / (1.f - F.c * F.c);
   const float Sx = m * F.q * A5, Sy = m * A6 / F.q;  // sum u dS/dx', sum u dS/dy'
   const float cc = fmaxf(F.c, 1e-30f);
+  const float c2p = F.e1 / cc, s2p = F.e2 / cc;  // cos 2phi, sin 2phi (0 for a round profile)
   const float dqdc = -2.f / ((1.f + F.c) * (1.f + F.c));
   g[0] = F.bn / (F.n * F.p0) * A1;
   g[1] = -1.9992f * (A1 - A0) + F.bn * 0.69314718f / F.n * A2;
-  g[2] = dq * dqdc * (F.e1 / cc) - dphi * F.e2 / (2.f * cc * cc);
-  g[3] = dq * dqdc * (F.e2 / cc) + dphi * F.e1 / (2.f * cc * cc);
+  g[2] = dq * dqdc * c2p + rot * s2p;
+  g[3] = dq * dqdc * s2p - rot * c2p;
   g[4] = -(F.cs * Sx - F.sn * Sy);
   g[5] = -(F.sn * Sx + F.cs * Sy);
   g[6] = A0 / F.I;
 }
 
 // EPL + shear native accumulators:
-// [0] sum s1 (theta_E), [1] d/dt, [2] d/dq, [3] d/dphi, [4] sum v.d alpha/dx',
-// [5] sum v.d alpha/dy' (lens frame; the centre gradient is minus these),
-// [6] d/dg1, [7] d/dg2.
+// [0] sum s1 (theta_E), [1] d/dt, [2] d/dq, [3] sum kappa v.(iY) with
+// d/dphi = -2 f [3], [4] sum v.d alpha/dx', [5] sum v.d alpha/dy' (lens frame;
+// the centre gradient is minus these), [6] d/dg1, [7] d/dg2.
+// With f = |e| and d phi/d e = (-e2, e1)/(2 f^2) the rotation part of d/de is
+// [3] (sin 2phi, -cos 2phi): no division by |e|.
 __device__ inline void epl_finish(const FinishC& F, const double* a, float* g) {
   const float gxl = -(float)a[4], gyl = -(float)a[5];
   const float cc = fmaxf(F.c, 1e-30f);
+  const float c2p = F.e1 / cc, s2p = F.e2 / cc;
   const float dqdc = -2.f / ((1.f + F.c) * (1.f + F.c));
-  const float dq = (float)a[2], dphi = (float)a[3];
+  const float dq = (float)a[2], rot = (float)a[3];
   g[0] = F.t / F.p0 * (float)a[0];
   g[1] = (float)a[1];
-  g[2] = dq * dqdc * (F.e1 / cc) - dphi * F.e2 / (2.f * cc * cc);
-  g[3] = dq * dqdc * (F.e2 / cc) + dphi * F.e1 / (2.f * cc * cc);
+  g[2] = dq * dqdc * c2p + rot * s2p;
+  g[3] = dq * dqdc * s2p - rot * c2p;
   g[4] = F.cs * gxl - F.sn * gyl;
   g[5] = F.sn * gxl + F.cs * gyl;
   g[6] = (float)a[6];

@@ -82,24 +82,50 @@ def grad_close(got, ref, rel=1e-3, floor=1e-2):
 EPS_MODEL = 5e-6  # per-pixel relative FP32 model error the bounds allow for
 
 
-def grad_bound(case: "Case", th: np.ndarray, rel=1e-3, eps=EPS_MODEL) -> np.ndarray:
-    """Per-row, per-parameter gradient tolerance: rel |g_ref| plus the
-    first-order gradient change that a per-pixel relative model error eps
-    (in m and in dm/dtheta) can cause,
+POS_DELTA = 2e-6  # arcsec: FP32 position precision of grid and deflection
+
+
+def centre_indices(n_comp: int):
+    xs = [4] + [8 + 7 * k + 4 for k in range(n_comp)]
+    return xs, [i + 1 for i in xs]
+
+
+def grad_bound(case: "Case", th: np.ndarray, rel=1e-3, eps=EPS_MODEL,
+               pos_delta=POS_DELTA) -> np.ndarray:
+    """Per-row, per-parameter gradient tolerance, the sum of
+      rel |g_ref|;
+      the first-order gradient change that a per-pixel relative model error
+      eps (in m and in dm/dtheta) causes,
         eps sum_p (|m_p| + |d_p - m_p|) |dm_p/dtheta_k| / sigma_p^2,
-    from the oracle's FP64 Jacobian. Near the mode the gradient is a small
-    difference of large sums, so this term, not rel, sets the bound there."""
+      from the oracle's FP64 Jacobian (near the mode the gradient is a small
+      difference of large sums, so this term sets the bound there);
+      the gradient change under a coherent shift of every component centre by
+      pos_delta in x and in y (FP32 grid and deflection positions are good to
+      ~1e-6 arcsec; far from the mode, where a steep deflection or Sersic cusp
+      meets the grid, the gradient moves by up to ~5e-3 per 1e-6 arcsec)."""
     th = np.atleast_2d(th)
     out = np.empty_like(th)
     w = 1.0 / case.sigma ** 2
     _, gref = case.oracle.logp_grad(th)
+    xs, ys = centre_indices(case.W.n_lens_light + case.W.n_source)
+    tx, ty = th.copy(), th.copy()
+    tx[:, xs] += pos_delta
+    ty[:, ys] += pos_delta
+    _, gx = case.oracle.logp_grad(tx)
+    _, gy = case.oracle.logp_grad(ty)
     for b in range(th.shape[0]):
         m, J = case.oracle.model_jacobian(th[b])
         wt = w * (np.abs(m) + np.abs(case.data - m))
-        out[b] = rel * np.abs(gref[b]) + eps * np.einsum("ij,ijk->k", wt, np.abs(J))
+        out[b] = (rel * np.abs(gref[b]) + eps * np.einsum("ij,ijk->k", wt, np.abs(J))
+                  + np.abs(gx[b] - gref[b]) + np.abs(gy[b] - gref[b]))
     return out
 
 
 def grad_close_bound(got, ref, bound):
+    """(ok, worst ratio err/bound and where: (row, parameter index, got, ref))."""
     err = np.abs(np.asarray(got, np.float64) - ref)
-    return bool(np.all(err <= bound)), float(np.max(err / bound))
+    r = np.atleast_2d(err / bound)
+    b, k = np.unravel_index(int(np.argmax(r)), r.shape)
+    g2, r2 = np.atleast_2d(got), np.atleast_2d(ref)
+    return bool(np.all(err <= bound)), (float(r[b, k]), int(b), int(k), float(g2[b, k]),
+                                       float(r2[b, k]))

@@ -17,7 +17,10 @@ Tolerances (FP32 path vs FP64 oracle):
   gradient     |g_k - g_ref,k| <= 1e-3 |g_ref,k| + EPS_MODEL sum_p (|m_p| +
                |d_p - m_p|) |dm_p/dtheta_k| / sigma_p^2 (the gradient change
                that the same per-pixel model error causes, from the oracle's
-               FP64 Jacobian); against central differences the same bound.
+               FP64 Jacobian), plus the oracle gradient's change under a
+               2e-6 arcsec shift of every component centre (FP32 position
+               precision; far from the mode the gradient can move by ~5e-3 per
+               1e-6 arcsec); against central differences the same bound.
 """
 import math
 
