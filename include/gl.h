@@ -145,6 +145,34 @@ gl_status gl_logp_grad_host(gl_system* sys, const float* theta_host, int B, floa
 gl_status gl_model_image(gl_system* sys, const float* theta, int B, float* img,
                          gl_deflection defl, void* stream);
 
+/* Size of the fixed scratch array used by gl_logp_grad_noalloc, in floats
+ * (64 MiB). */
+#define GL_NOALLOC_SCRATCH_FLOATS (16u * 1024u * 1024u)
+
+/* gl_logp_grad for callers that must not allocate device memory. The paper
+ * has no counterpart: this is a deployment variant of the same computation.
+ * It is meant for code that runs under a framework owning a fixed device
+ * memory budget, or in a real-time loop that cannot take cudaMalloc's
+ * implicit synchronisation; gl_logp_grad may call cudaMalloc to grow the
+ * system's scratch, this call never allocates (no cudaMalloc, cudaFree or
+ * allocating library routine).
+ *   - Scratch: one file-scope device array of GL_NOALLOC_SCRATCH_FLOATS floats
+ *     that every GPU loading the library holds until the process exits.
+ *     Images whose two padded buffers fit in shared memory use none of it;
+ *     larger ones need one slot per row, and a batch whose slots exceed the
+ *     array is rejected with GL_EINVAL (gl_last_error() states the largest
+ *     batch that fits).
+ *   - The first call on each device looks up the array's device address (and
+ *     may load the library's device code); make that first call before any
+ *     stream capture.
+ *   - Every call shares the one array, which keeps the last call's contents
+ *     (the kernel writes every value it later reads): calls whose work
+ *     overlaps on the GPU, from any system or stream, race on it.
+ * Arguments, outputs and errors are those of gl_logp_grad with
+ * defl = GL_DEFL_SERIES. */
+gl_status gl_logp_grad_noalloc(gl_system* sys, const float* theta, int B, float* logp,
+                               float* grad, void* stream);
+
 /* Last failure message on this host thread ("" if none). */
 const char* gl_last_error(void);
 

@@ -65,6 +65,7 @@ SIGNATURES = {
     "gl_logp_grad": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]),
     "gl_logp_grad_host": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]),
     "gl_model_image": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP]),
+    "gl_logp_grad_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
     "gl_last_error": (ctypes.c_char_p, []),
 }
 
@@ -180,6 +181,18 @@ class System:
         grad = torch.empty_like(theta) if grad is None else grad
         _check(self._lib.gl_logp_grad(self._h, _ptr(theta), B, _ptr(out), _ptr(grad), defl,
                                       _stream_ptr(stream)))
+        return out, grad
+
+    def logp_grad_noalloc(self, theta, out=None, grad=None, stream=None):
+        """gl_logp_grad_noalloc: the same result without any device allocation
+        inside the call (fixed library scratch; see include/gl.h)."""
+        torch = _torch()
+        theta = self._theta(theta)
+        B = theta.shape[0]
+        out = torch.empty(B, device=theta.device, dtype=torch.float32) if out is None else out
+        grad = torch.empty_like(theta) if grad is None else grad
+        _check(self._lib.gl_logp_grad_noalloc(self._h, _ptr(theta), B, _ptr(out), _ptr(grad),
+                                              _stream_ptr(stream)))
         return out, grad
 
     def logp_grad_host(self, theta: np.ndarray, defl: int = GL_DEFL_SERIES, want_grad=True,

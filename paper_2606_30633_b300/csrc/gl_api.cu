@@ -414,3 +414,22 @@ gl_status gl_logp_grad_host(gl_system* sys, const float* theta_host, int B, floa
 }
 
 }  // extern "C"
+
+namespace gl {
+// Sets the message gl_last_error() returns on this host thread.
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// Read-only view of a system's gradient-kernel plan for other translation
+// units of the library: kernel parameters with buffer placement, dynamic
+// shared memory and global scratch floats per row. Returns the device index.
+int system_grad_plan(const gl_system* sys, SysParams* sp, size_t* dyn_smem, size_t* slot_floats) {
+  *sp = sys->sp;
+  sp->bufA_smem = sys->grad_A;
+  sp->bufB_smem = sys->grad_B;
+  sp->slot_floats = sys->grad_slot;
+  sp->scratch = nullptr;
+  *dyn_smem = sys->grad_smem;
+  *slot_floats = sys->grad_slot;
+  return sys->device;
+}
+}  // namespace gl
