@@ -139,6 +139,22 @@ gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, f
 gl_status gl_logp_grad_host(gl_system* sys, const float* theta_host, int B, float* logp_host,
                             float* grad_host, gl_deflection defl, void* stream);
 
+/* n_steps HMC leapfrog steps for B chains, in place (the integrator of the
+ * pipeline's HMC stage, Sec. 3; Sec. 3.1 runs chains independently). Per step,
+ * with diagonal inverse mass M^-1 and step size eps:
+ *   p += eps/2 grad; theta += eps M^-1 p; (logp, grad) at theta; p += eps/2 grad.
+ * theta, p, grad: device [B][P]; logp: device [B]; inv_mass: device [P].
+ * On entry logp and grad must hold the values at theta (from gl_logp_grad or a
+ * previous block); on return they hold the values at the new theta. A chain
+ * whose log p is not finite is frozen (theta and p left as they are) and keeps
+ * its -inf/NaN log p: divergent trajectories are flagged, not trapped.
+ * The block runs as one CUDA graph launch on the stream: the library captures
+ * it on a private stream the first time and again whenever a pointer, eps,
+ * n_steps or B changes (re-capture costs about a millisecond). Do not call it
+ * while the calling thread is capturing a stream. */
+gl_status gl_leapfrog(gl_system* sys, float* theta, float* p, float* logp, float* grad,
+                      const float* inv_mass, float eps, int n_steps, int B, void* stream);
+
 /* Model image m (binned, PSF-convolved) for each row: img device [B][ny][nx].
  * Rows outside the model's domain or holding a NaN give NaN images; the prior
  * is not checked. */

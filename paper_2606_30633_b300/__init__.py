@@ -65,6 +65,8 @@ SIGNATURES = {
     "gl_logp_grad": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]),
     "gl_logp_grad_host": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]),
     "gl_model_image": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP]),
+    "gl_leapfrog": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_float, ctypes.c_int,
+                                   ctypes.c_int, _VP]),
     "gl_logp_grad_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
     "gl_last_error": (ctypes.c_char_p, []),
 }
@@ -182,6 +184,22 @@ class System:
         _check(self._lib.gl_logp_grad(self._h, _ptr(theta), B, _ptr(out), _ptr(grad), defl,
                                       _stream_ptr(stream)))
         return out, grad
+
+    def leapfrog(self, theta, p, logp, grad, inv_mass, eps: float, n_steps: int, stream=None):
+        """n_steps leapfrog steps in place (one CUDA graph launch; see gl.h).
+        theta, p, grad: CUDA float32 [B, P]; logp [B]; inv_mass [P]."""
+        torch = _torch()
+        for t in (theta, p, logp, grad, inv_mass):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                    and t.is_contiguous()):
+                raise TypeError("leapfrog buffers must be contiguous CUDA float32 tensors")
+        B = theta.shape[0]
+        if theta.shape != (B, self.P) or p.shape != theta.shape or grad.shape != theta.shape \
+                or logp.shape != (B,) or inv_mass.shape != (self.P,):
+            raise ValueError("leapfrog buffer shapes do not match [B, P]")
+        _check(self._lib.gl_leapfrog(self._h, _ptr(theta), _ptr(p), _ptr(logp), _ptr(grad),
+                                     _ptr(inv_mass), float(eps), int(n_steps), B,
+                                     _stream_ptr(stream)))
 
     def logp_grad_noalloc(self, theta, out=None, grad=None, stream=None):
         """gl_logp_grad_noalloc: the same result without any device allocation

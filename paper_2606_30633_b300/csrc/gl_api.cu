@@ -32,6 +32,16 @@ struct gl_system {
   float *h_stage = nullptr, *d_stage = nullptr;
   size_t stage_floats = 0;
   const gl_surrogate* sur = nullptr;
+  // leapfrog block: one instantiated CUDA graph, re-captured when its
+  // arguments (or the scratch it points into) change
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t lf_exec = nullptr;
+  struct LfKey {
+    float *theta, *p, *logp, *grad, *scratch;
+    const float* inv_mass;
+    float eps;
+    int n_steps, B;
+  } lf_key;
 };
 
 namespace {
@@ -304,6 +314,8 @@ gl_status gl_system_create(const gl_system_desc* d, gl_system** out) {
 gl_status gl_system_destroy(gl_system* s) {
   if (!s) return GL_OK;
   cudaDeviceSynchronize();
+  if (s->lf_exec) cudaGraphExecDestroy(s->lf_exec);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   cudaFree(s->d_data);
   cudaFree(s->d_w);
   cudaFree(s->d_prior);
@@ -369,6 +381,64 @@ gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, f
   }
   GL_CUDA(gl::launch_grad(sp, theta, B, logp, grad, sys->grad_smem, (cudaStream_t)stream),
           "gradient launch");
+  return GL_OK;
+}
+
+gl_status gl_leapfrog(gl_system* sys, float* theta, float* p, float* logp, float* grad,
+                      const float* inv_mass, float eps, int n_steps, int B, void* stream) {
+  if (!sys) return fail(GL_EINVAL, "system is NULL");
+  if (B < 0 || n_steps < 0) return fail(GL_EINVAL, "B and n_steps must be >= 0");
+  if (!std::isfinite(eps)) return fail(GL_EINVAL, "eps must be finite");
+  if (B == 0 || n_steps == 0) return GL_OK;
+  if (!theta || !p || !logp || !grad || !inv_mass)
+    return fail(GL_EINVAL, "NULL theta, p, logp, grad or inv_mass");
+  gl_status r = set_device(sys);
+  if (r != GL_OK) return r;
+  SysParams sp = sys->sp;
+  sp.bufA_smem = sys->grad_A;
+  sp.bufB_smem = sys->grad_B;
+  sp.slot_floats = sys->grad_slot;
+  if (sys->grad_slot) {
+    r = ensure_scratch(sys, (size_t)B * sys->grad_slot);
+    if (r != GL_OK) return r;
+    sp.scratch = sys->scratch;
+  }
+  gl_system::LfKey key;
+  std::memset(&key, 0, sizeof key);  // padding takes part in the comparison
+  key.theta = theta;
+  key.p = p;
+  key.logp = logp;
+  key.grad = grad;
+  key.scratch = sp.scratch;
+  key.inv_mass = inv_mass;
+  key.eps = eps;
+  key.n_steps = n_steps;
+  key.B = B;
+  const bool same = sys->lf_exec && std::memcmp(&key, &sys->lf_key, sizeof key) == 0;
+  if (!same) {
+    if (sys->lf_exec) {
+      GL_CUDA(cudaGraphExecDestroy(sys->lf_exec), "graph destroy");
+      sys->lf_exec = nullptr;
+    }
+    if (!sys->cap_stream)
+      GL_CUDA(cudaStreamCreateWithFlags(&sys->cap_stream, cudaStreamNonBlocking), "stream");
+    GL_CUDA(cudaStreamBeginCapture(sys->cap_stream, cudaStreamCaptureModeThreadLocal),
+            "begin capture");
+    cudaError_t e = gl::launch_leapfrog_block(sp, sys->grad_smem, theta, p, logp, grad, inv_mass,
+                                              eps, n_steps, B, sys->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(sys->cap_stream, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "leapfrog capture");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+    e = cudaGraphInstantiate(&sys->lf_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      sys->lf_exec = nullptr;
+      return cuda_fail(e, "graph instantiate");
+    }
+    std::memcpy(&sys->lf_key, &key, sizeof key);
+  }
+  GL_CUDA(cudaGraphLaunch(sys->lf_exec, (cudaStream_t)stream), "graph launch");
   return GL_OK;
 }
 

@@ -53,6 +53,9 @@ cudaError_t launch_forward(const SysParams& sp, const float* theta, int B, float
                            float* img, size_t dyn_smem, cudaStream_t st);
 cudaError_t launch_grad(const SysParams& sp, const float* theta, int B, float* logp, float* grad,
                         size_t dyn_smem, cudaStream_t st);
+cudaError_t launch_leapfrog_block(const SysParams& sp, size_t dyn, float* theta, float* p,
+                                  float* logp, float* grad, const float* inv_mass, float eps,
+                                  int n_steps, int B, cudaStream_t st);
 cudaError_t set_smem_limits_fwd(size_t bytes);
 cudaError_t set_smem_limits_grad(size_t bytes);
 
