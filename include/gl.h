@@ -73,8 +73,17 @@ typedef enum {
   GL_ETIMEOUT = 5
 } gl_status;
 
-/* Which deflection the EPL uses: the exact series or the learned surrogate. */
-typedef enum { GL_DEFL_SERIES = 0, GL_DEFL_SURROGATE = 1 } gl_deflection;
+/* Which deflection the EPL uses:
+ *   GL_DEFL_SERIES     the exact series at every sub-pixel;
+ *   GL_DEFL_SURROGATE  the learned surrogate (gl_system_set_surrogate): per
+ *                      row, F and its derivatives on 128 angles from the
+ *                      network, interpolated (cubic Hermite) at every
+ *                      sub-pixel; rows outside its training domain use the
+ *                      exact series;
+ *   GL_DEFL_TABLE      the same tables filled from the exact series (rows with
+ *                      |e| > 0.5 use the series): differs from GL_DEFL_SERIES by
+ *                      the interpolation error only. */
+typedef enum { GL_DEFL_SERIES = 0, GL_DEFL_SURROGATE = 1, GL_DEFL_TABLE = 2 } gl_deflection;
 
 /* Prior kinds (Eq. sim-dist, Sec. 4.2). */
 typedef enum {
@@ -188,6 +197,73 @@ gl_status gl_model_image(gl_system* sys, const float* theta, int B, float* img,
  * defl = GL_DEFL_SERIES. */
 gl_status gl_logp_grad_noalloc(gl_system* sys, const float* theta, int B, float* logp,
                                float* grad, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned EPL deflection surrogate (a learned replacement of the
+ * hypergeometric series the deflection uses, Sec. 3 mass model).
+ * A 4 -> 64 -> 64 -> 64 -> 64 -> 2 SiLU MLP with inputs (q, gamma,
+ * log(R/theta_E), vphi): q the EPL axis ratio, vphi the angle of q x' + i y'
+ * in [0, 2 pi). It predicts the part of F = 2F1(1, t/2; 2 - t/2; -f e^{2 i vphi})
+ * beyond its first two series terms, times 100:
+ *   F = 1 + c1 z + c2 z^2 + y/100, z = -f e^{2 i vphi}, c1 = t/(4-t),
+ *   c2 = c1 (2+t)/(6-t).
+ * BF16 weights and activations, FP32 accumulation (tensor cores), FP32
+ * master weights. Parameter vector (FP32, gl_surrogate_num_params() floats):
+ * W1[64][4], b1[64], W2[64][64], b2, W3, b3, W4, b4, W5[2][64], b5[2]
+ * (W[out][in], row-major), acting on normalised inputs
+ *   ((q-0.75)/0.25, (gamma-2)/0.3, log(R/theta_E)/2.3, (vphi-pi)/pi).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  long long n_samples;    /* training tuples labelled by the exact series (e.g. 1e7) */
+  int epochs;             /* passes over the tuples                              */
+  int batch;              /* rows per step, a multiple of 128                    */
+  float lr, lr_min;       /* Adam learning rate, cosine-decayed to lr_min        */
+  unsigned long long seed_data, seed_init;
+  float q_lo, q_hi;       /* q ~ U(q_lo, q_hi), 0 < q_lo < q_hi <= 1            */
+  float gamma_lo, gamma_hi;  /* gamma ~ U(gamma_lo, gamma_hi) inside (1, 3)      */
+  float r_lo, r_hi;       /* R/theta_E ~ logU(r_lo, r_hi)                         */
+} gl_surrogate_train_desc;
+
+/* Number of FP32 parameters of the surrogate MLP (12930). */
+int gl_surrogate_num_params(void);
+
+/* Generates the training tuples on the device, trains with Adam (on the
+ * current device; synchronous) and returns the trained surrogate. final_loss
+ * (may be NULL) receives the mean squared error of the last batch in the
+ * scaled output units. The [q_lo, q_hi] x [gamma_lo, gamma_hi] box is the
+ * surrogate's domain: rows outside it use the exact series. */
+gl_status gl_surrogate_train(const gl_surrogate_train_desc* desc, gl_surrogate** out,
+                             float* final_loss);
+
+/* A surrogate from given parameters (host [gl_surrogate_num_params()]) with
+ * the default domain q in [0.5, 1], gamma in [1.7, 2.3]. */
+gl_status gl_surrogate_create(const float* params_host, gl_surrogate** out);
+
+/* Copies the FP32 parameters to host memory. */
+gl_status gl_surrogate_params(const gl_surrogate* sur, float* params_host);
+
+/* F (Re, Im) for N raw inputs x: device [N][4] = (q, gamma, log(R/theta_E),
+ * vphi) -> y: device [N][2]. */
+gl_status gl_surrogate_infer(const gl_surrogate* sur, const float* x, int N, float* y,
+                             void* stream);
+
+/* Mean squared training loss and its gradient w.r.t. the parameters for N
+ * rows (N a multiple of 128): x device [N][4] raw inputs, target device
+ * [N][2] in scaled output units (100 x the series remainder); loss_host and
+ * grad_host [gl_surrogate_num_params()] receive the results. Synchronous. */
+gl_status gl_surrogate_loss_grad(const gl_surrogate* sur, const float* x, const float* target,
+                                 int N, float* loss_host, float* grad_host);
+
+/* Save / load the parameters and domain to / from a flat binary file. */
+gl_status gl_surrogate_save(const gl_surrogate* sur, const char* path);
+gl_status gl_surrogate_load(const char* path, gl_surrogate** out);
+
+/* Frees a surrogate (waits for the device). NULL is accepted. */
+void gl_surrogate_destroy(gl_surrogate* sur);
+
+/* Attaches a surrogate to a system (borrowed: it must outlive the system's
+ * use of GL_DEFL_SURROGATE); NULL detaches. */
+gl_status gl_system_set_surrogate(gl_system* sys, const gl_surrogate* sur);
 
 /* Last failure message on this host thread ("" if none). */
 const char* gl_last_error(void);

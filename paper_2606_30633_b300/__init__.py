@@ -25,7 +25,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgl.so")
 
 GL_OK, GL_EINVAL, GL_ENOMEM, GL_ECUDA, GL_ENOSURROGATE, GL_ETIMEOUT = range(6)
-GL_DEFL_SERIES, GL_DEFL_SURROGATE = 0, 1
+GL_DEFL_SERIES, GL_DEFL_SURROGATE, GL_DEFL_TABLE = 0, 1, 2
 PRIOR_KIND = {"flat": 0, "uniform": 1, "normal": 2, "truncnorm": 3, "lognormal": 4}
 
 _STATUS_NAMES = {0: "GL_OK", 1: "GL_EINVAL", 2: "GL_ENOMEM", 3: "GL_ECUDA",
@@ -69,7 +69,26 @@ SIGNATURES = {
                                    ctypes.c_int, _VP]),
     "gl_logp_grad_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
     "gl_last_error": (ctypes.c_char_p, []),
+    "gl_surrogate_num_params": (ctypes.c_int, []),
+    "gl_surrogate_train": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_float)]),
+    "gl_surrogate_create": (ctypes.c_int, [_VP, ctypes.POINTER(_VP)]),
+    "gl_surrogate_params": (ctypes.c_int, [_VP, _VP]),
+    "gl_surrogate_infer": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP]),
+    "gl_surrogate_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
+    "gl_surrogate_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "gl_surrogate_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_VP)]),
+    "gl_surrogate_destroy": (None, [_VP]),
+    "gl_system_set_surrogate": (ctypes.c_int, [_VP, _VP]),
 }
+
+
+class gl_surrogate_train_desc(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_longlong), ("epochs", ctypes.c_int),
+                ("batch", ctypes.c_int), ("lr", ctypes.c_float), ("lr_min", ctypes.c_float),
+                ("seed_data", ctypes.c_ulonglong), ("seed_init", ctypes.c_ulonglong),
+                ("q_lo", ctypes.c_float), ("q_hi", ctypes.c_float),
+                ("gamma_lo", ctypes.c_float), ("gamma_hi", ctypes.c_float),
+                ("r_lo", ctypes.c_float), ("r_hi", ctypes.c_float)]
 
 _LIB: Optional[ctypes.CDLL] = None
 
@@ -146,6 +165,11 @@ class System:
     @property
     def handle(self):
         return self._h
+
+    def set_surrogate(self, sur: Optional["Surrogate"]):
+        """Attach a surrogate (kept alive by this object) or detach with None."""
+        self._sur = sur
+        _check(self._lib.gl_system_set_surrogate(self._h, None if sur is None else sur._h))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -234,6 +258,84 @@ class System:
         _check(self._lib.gl_model_image(self._h, _ptr(theta), B, _ptr(out), defl,
                                         _stream_ptr(stream)))
         return out
+
+
+class Surrogate:
+    """The learned EPL deflection surrogate (include/gl.h)."""
+
+    def __init__(self, handle):
+        self._lib = load()
+        self._h = handle
+        self.final_loss = float("nan")
+
+    @staticmethod
+    def num_params() -> int:
+        return int(load().gl_surrogate_num_params())
+
+    @classmethod
+    def train(cls, n_samples=10_000_000, epochs=20, batch=16384, lr=2e-3, lr_min=1e-5,
+              seed_data=401, seed_init=402, q=(0.5, 1.0), gamma=(1.7, 2.3), r=(0.05, 5.0)):
+        lib = load()
+        d = gl_surrogate_train_desc(n_samples, epochs, batch, lr, lr_min, seed_data, seed_init,
+                                    q[0], q[1], gamma[0], gamma[1], r[0], r[1])
+        h = _VP()
+        loss = ctypes.c_float()
+        _check(lib.gl_surrogate_train(ctypes.byref(d), ctypes.byref(h), ctypes.byref(loss)))
+        s = cls(h)
+        s.final_loss = loss.value
+        return s
+
+    @classmethod
+    def from_params(cls, params):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        assert p.size == cls.num_params()
+        h = _VP()
+        _check(load().gl_surrogate_create(p.ctypes.data, ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def load_file(cls, path: str):
+        h = _VP()
+        _check(load().gl_surrogate_load(path.encode(), ctypes.byref(h)))
+        return cls(h)
+
+    def save(self, path: str):
+        _check(self._lib.gl_surrogate_save(self._h, path.encode()))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.num_params(), dtype=np.float32)
+        _check(self._lib.gl_surrogate_params(self._h, out.ctypes.data))
+        return out
+
+    def infer(self, x, stream=None):
+        """x: CUDA float32 [N, 4] raw (q, gamma, log R/theta_E, vphi) -> F [N, 2]."""
+        torch = _torch()
+        x = x.contiguous()
+        y = torch.empty((x.shape[0], 2), device=x.device, dtype=torch.float32)
+        _check(self._lib.gl_surrogate_infer(self._h, _ptr(x), x.shape[0], _ptr(y),
+                                            _stream_ptr(stream)))
+        return y
+
+    def loss_grad(self, x, target):
+        """Mean squared loss and its parameter gradient (x [N, 4], target [N, 2]
+        CUDA float32; N a multiple of 128)."""
+        x, target = x.contiguous(), target.contiguous()
+        loss = np.empty(1, dtype=np.float32)
+        grad = np.empty(self.num_params(), dtype=np.float32)
+        _check(self._lib.gl_surrogate_loss_grad(self._h, _ptr(x), _ptr(target), x.shape[0],
+                                                loss.ctypes.data, grad.ctypes.data))
+        return float(loss[0]), grad
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gl_surrogate_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def system_from_workload(W, data, sigma) -> System:

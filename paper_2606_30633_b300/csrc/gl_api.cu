@@ -32,6 +32,8 @@ struct gl_system {
   float *h_stage = nullptr, *d_stage = nullptr;
   size_t stage_floats = 0;
   const gl_surrogate* sur = nullptr;
+  float4* d_table = nullptr;  // surrogate tables, [rows][TABLE_M][2]
+  size_t table_rows = 0;
   // leapfrog block: one instantiated CUDA graph, re-captured when its
   // arguments (or the scratch it points into) change
   cudaStream_t cap_stream = nullptr;
@@ -126,12 +128,30 @@ gl_status ensure_scratch(gl_system* s, size_t floats) {
   return GL_OK;
 }
 
+// Builds the surrogate tables for B rows and points sp at them.
+gl_status prepare_surrogate(gl_system* s, const float* theta, int B, SysParams& sp,
+                            gl_deflection defl, cudaStream_t st) {
+  if ((size_t)B > s->table_rows) {
+    cudaFree(s->d_table);
+    s->d_table = nullptr;
+    s->table_rows = 0;
+    GL_CUDA(cudaMalloc(&s->d_table, (size_t)B * 2 * gl::TABLE_M * sizeof(float4)),
+            "surrogate table allocation");
+    s->table_rows = B;
+  }
+  const gl_surrogate* src = defl == GL_DEFL_TABLE ? nullptr : s->sur;
+  GL_CUDA(gl::launch_table(src, theta, s->sp.P, B, s->d_table, st), "table launch");
+  sp.table = s->d_table;
+  gl::surrogate_domain(src, &sp.sq_lo, &sp.sq_hi, &sp.sg_lo, &sp.sg_hi);
+  return GL_OK;
+}
+
 gl_status check_call(gl_system* sys, const void* theta, int B, const void* out,
                      gl_deflection defl) {
   if (!sys) return fail(GL_EINVAL, "system is NULL");
   if (B < 0) return fail(GL_EINVAL, "B < 0");
   if (B > 0 && (!theta || !out)) return fail(GL_EINVAL, "NULL theta or output");
-  if (defl != GL_DEFL_SERIES && defl != GL_DEFL_SURROGATE)
+  if (defl != GL_DEFL_SERIES && defl != GL_DEFL_SURROGATE && defl != GL_DEFL_TABLE)
     return fail(GL_EINVAL, "unknown deflection kind");
   if (defl == GL_DEFL_SURROGATE && !sys->sur)
     return fail(GL_ENOSURROGATE, "no surrogate attached to this system");
@@ -150,6 +170,12 @@ gl_status set_device(gl_system* sys) {
 extern "C" {
 
 const char* gl_last_error(void) { return g_last_error.c_str(); }
+
+gl_status gl_system_set_surrogate(gl_system* sys, const gl_surrogate* sur) {
+  if (!sys) return fail(GL_EINVAL, "system is NULL");
+  sys->sur = sur;
+  return GL_OK;
+}
 
 int gl_system_num_params(const gl_system* sys) { return sys ? sys->sp.P : -1; }
 
@@ -321,6 +347,7 @@ gl_status gl_system_destroy(gl_system* s) {
   cudaFree(s->d_prior);
   cudaFree(s->d_emax);
   cudaFree(s->scratch);
+  cudaFree(s->d_table);
   cudaFree(s->d_stage);
   cudaFreeHost(s->h_stage);
   delete s;
@@ -328,8 +355,12 @@ gl_status gl_system_destroy(gl_system* s) {
 }
 
 static gl_status run_forward(gl_system* sys, const float* theta, int B, float* logp, float* img,
-                             cudaStream_t st) {
+                             gl_deflection defl, cudaStream_t st) {
   SysParams sp = sys->sp;
+  if (defl != GL_DEFL_SERIES) {
+    gl_status r = prepare_surrogate(sys, theta, B, sp, defl, st);
+    if (r != GL_OK) return r;
+  }
   sp.bufA_smem = sys->fwd_A;
   sp.bufB_smem = 0;
   sp.slot_floats = sys->fwd_slot;
@@ -346,20 +377,18 @@ gl_status gl_logp(gl_system* sys, const float* theta, int B, float* logp, gl_def
                   void* stream) {
   gl_status r = check_call(sys, theta, B, logp, defl);
   if (r != GL_OK) return r;
-  if (defl == GL_DEFL_SURROGATE) return fail(GL_ENOSURROGATE, "surrogate path not available");
   if (B == 0) return GL_OK;
   if ((r = set_device(sys)) != GL_OK) return r;
-  return run_forward(sys, theta, B, logp, nullptr, (cudaStream_t)stream);
+  return run_forward(sys, theta, B, logp, nullptr, defl, (cudaStream_t)stream);
 }
 
 gl_status gl_model_image(gl_system* sys, const float* theta, int B, float* img,
                          gl_deflection defl, void* stream) {
   gl_status r = check_call(sys, theta, B, img, defl);
   if (r != GL_OK) return r;
-  if (defl == GL_DEFL_SURROGATE) return fail(GL_ENOSURROGATE, "surrogate path not available");
   if (B == 0) return GL_OK;
   if ((r = set_device(sys)) != GL_OK) return r;
-  return run_forward(sys, theta, B, nullptr, img, (cudaStream_t)stream);
+  return run_forward(sys, theta, B, nullptr, img, defl, (cudaStream_t)stream);
 }
 
 gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, float* grad,
@@ -367,10 +396,13 @@ gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, f
   gl_status r = check_call(sys, theta, B, logp, defl);
   if (r != GL_OK) return r;
   if (B > 0 && !grad) return fail(GL_EINVAL, "grad is NULL");
-  if (defl == GL_DEFL_SURROGATE) return fail(GL_ENOSURROGATE, "surrogate path not available");
   if (B == 0) return GL_OK;
   if ((r = set_device(sys)) != GL_OK) return r;
   SysParams sp = sys->sp;
+  if (defl != GL_DEFL_SERIES) {
+    r = prepare_surrogate(sys, theta, B, sp, defl, (cudaStream_t)stream);
+    if (r != GL_OK) return r;
+  }
   sp.bufA_smem = sys->grad_A;
   sp.bufB_smem = sys->grad_B;
   sp.slot_floats = sys->grad_slot;

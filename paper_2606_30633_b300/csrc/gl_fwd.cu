@@ -1,20 +1,19 @@
-// Instantiates the forward kernels (log p, model image) for every supported
-// component count and dispatches on the system's counts.
-#include "gl_kernels.cuh"
+// Dispatch of k_forward on the system's component counts and deflection kind
+// (instantiations live in gl_fwd_l*.cu).
+#include "gl_fwd_impl.cuh"
 
 namespace gl {
 
-template <int NL, int NS>
-static cudaError_t launch_fwd_t(const SysParams& sp, const float* theta, int B, float* logp,
-                                float* img, size_t dyn, cudaStream_t st) {
-  k_forward<NL, NS><<<B, THREADS, dyn, st>>>(sp, theta, B, logp, img);
-  return cudaGetLastError();
-}
+GL_FWD_INST(extern, 0)
+GL_FWD_INST(extern, 1)
+GL_FWD_INST(extern, 2)
 
-cudaError_t launch_forward(const SysParams& sp, const float* theta, int B, float* logp,
-                           float* img, size_t dyn, cudaStream_t st) {
-#define GL_CASE(a, b) \
-  if (sp.nL == a && sp.nS == b) return launch_fwd_t<a, b>(sp, theta, B, logp, img, dyn, st);
+cudaError_t launch_forward(const SysParams& sp, const float* theta, int B, float* logp, float* img,
+                        size_t dyn, cudaStream_t st) {
+#define GL_CASE(a, b)                                                         \
+  if (sp.nL == a && sp.nS == b)                                               \
+    return sp.table ? fwd_launch<a, b, true>(sp, theta, B, logp, img, dyn, st) \
+                    : fwd_launch<a, b, false>(sp, theta, B, logp, img, dyn, st);
   GL_CASE(0, 1) GL_CASE(0, 2) GL_CASE(0, 3)
   GL_CASE(1, 1) GL_CASE(1, 2) GL_CASE(1, 3)
   GL_CASE(2, 1) GL_CASE(2, 2) GL_CASE(2, 3)
@@ -24,10 +23,8 @@ cudaError_t launch_forward(const SysParams& sp, const float* theta, int B, float
 
 cudaError_t set_smem_limits_fwd(size_t bytes) {
   cudaError_t e = cudaSuccess;
-#define GL_SET(a, b)                                                                          \
-  if (e == cudaSuccess)                                                                        \
-    e = cudaFuncSetAttribute(k_forward<a, b>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)bytes);
+#define GL_SET(a, b) \
+  if (e == cudaSuccess) e = fwd_smem<a, b>(bytes);
   GL_SET(0, 1) GL_SET(0, 2) GL_SET(0, 3)
   GL_SET(1, 1) GL_SET(1, 2) GL_SET(1, 3)
   GL_SET(2, 1) GL_SET(2, 2) GL_SET(2, 3)

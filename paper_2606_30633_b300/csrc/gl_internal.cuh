@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+struct gl_surrogate;
+
 namespace gl {
 
 constexpr int MAX_K = 21;      // largest PSF side
@@ -17,6 +19,7 @@ constexpr int N_MAX = 128;     // EPL series terms for |e| < 0.8 at FP32 toleran
 constexpr int THREADS = 256;   // threads per CTA of the fused kernels
 constexpr int NWARPS = THREADS / 32;
 constexpr int ROWS_STRIP = 8;  // output rows per thread in the unrolled convolution
+constexpr int TABLE_M = 128;   // surrogate angular table points over [0, pi)
 
 // One prior entry as the kernels see it; cnst is the log normalisation
 // constant, computed once at system creation.
@@ -43,12 +46,15 @@ struct SysParams {
   const PriorDev* prior;   // [P]
   const float* emax;       // [1 + nL + nS]
   float* scratch;          // global scratch base (CTA b uses slot b)
+  const float4* table;     // surrogate tables [B][TABLE_M][2] (null: exact series)
+  float sq_lo, sq_hi, sg_lo, sg_hi;  // surrogate domain in q and gamma
   float kconv[MAX_K * MAX_K];  // flipped PSF: m = correlate(b_pad, kconv)
   float kcorr[MAX_K * MAX_K];  // PSF: adjoint = correlate(g_pad, kcorr)
 };
 
 // Launch entry points (defined in the kernel translation units).
 // img != nullptr: write the model image instead of reducing chi^2.
+// sp.table != nullptr selects the surrogate instantiations.
 cudaError_t launch_forward(const SysParams& sp, const float* theta, int B, float* logp,
                            float* img, size_t dyn_smem, cudaStream_t st);
 cudaError_t launch_grad(const SysParams& sp, const float* theta, int B, float* logp, float* grad,
@@ -56,6 +62,10 @@ cudaError_t launch_grad(const SysParams& sp, const float* theta, int B, float* l
 cudaError_t launch_leapfrog_block(const SysParams& sp, size_t dyn, float* theta, float* p,
                                   float* logp, float* grad, const float* inv_mass, float eps,
                                   int n_steps, int B, cudaStream_t st);
+// Surrogate tables [B][TABLE_M][2] for the rows of theta (gl_surrogate.cu).
+cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B, float4* table,
+                         cudaStream_t st);
+void surrogate_domain(const gl_surrogate* s, float* q_lo, float* q_hi, float* g_lo, float* g_hi);
 cudaError_t set_smem_limits_fwd(size_t bytes);
 cudaError_t set_smem_limits_grad(size_t bytes);
 

@@ -128,12 +128,70 @@ __device__ __forceinline__ double block_sum_double(double v, double* red) {
   return s;  // valid on thread 0
 }
 
+// ------------------------------------------------- surrogate table lookup ----
+// Table of row b: TABLE_M nodes uniform in the pseudo-angle
+//   pa = 1 - cos(vphi) / (|cos(vphi)| + sin(vphi)),  vphi folded into [0, pi)
+// (F has period pi in vphi; pa is monotonic, in [0, 2), with
+// d pa / d vphi = 1 / (|cos| + sin)^2), two float4 per node:
+// (F, dF/dpa) and (dF/dq, dF/dt). Cubic Hermite interpolation in pa for F and
+// its derivative, linear for the rest.
+struct TabF {
+  float Fr, Fi, Pr, Pi, Qr, Qi, Tr, Ti;  // F, dF/dvphi, dF/dq, dF/dt
+};
+template <bool DERIV>
+__device__ __forceinline__ TabF table_eval(const float4* __restrict__ tab, float cph, float sph) {
+  const float fl = sph < 0.f ? -1.f : 1.f;  // fold vphi into [0, pi)
+  const float c = cph * fl, sn = sph * fl;
+  const float rd = rcp(fmaxf(fabsf(c) + sn, 1e-20f));  // 0 only at the clamped centre
+  const float pa = fmaf(-c, rd, 1.f);
+  const float u = pa * (0.5f * TABLE_M);
+  const int i0 = min((int)u, TABLE_M - 1);
+  const float t = u - (float)i0;
+  const int i1 = (i0 + 1) & (TABLE_M - 1);
+  const float4 a0 = tab[2 * i0], a1 = tab[2 * i1];
+  const float h = 2.f / TABLE_M;
+  const float t2 = t * t, omt = 1.f - t;
+  const float h00 = (1.f + 2.f * t) * omt * omt, h10 = t * omt * omt;
+  const float h01 = t2 * (3.f - 2.f * t), h11 = t2 * (t - 1.f);
+  TabF o;
+  o.Fr = h00 * a0.x + h01 * a1.x + h * (h10 * a0.z + h11 * a1.z);
+  o.Fi = h00 * a0.y + h01 * a1.y + h * (h10 * a0.w + h11 * a1.w);
+  if (DERIV) {
+    const float d00 = 6.f * (t2 - t) / h, d10 = 3.f * t2 - 4.f * t + 1.f, d11 = 3.f * t2 - 2.f * t;
+    const float k = rd * rd;  // d pa / d vphi
+    o.Pr = k * (d00 * (a0.x - a1.x) + d10 * a0.z + d11 * a1.z);
+    o.Pi = k * (d00 * (a0.y - a1.y) + d10 * a0.w + d11 * a1.w);
+    const float4 b0 = tab[2 * i0 + 1], b1 = tab[2 * i1 + 1];
+    o.Qr = omt * b0.x + t * b1.x;
+    o.Qi = omt * b0.y + t * b1.y;
+    o.Tr = omt * b0.z + t * b1.z;
+    o.Ti = omt * b0.w + t * b1.w;
+  }
+  return o;
+}
+
 // ------------------------------------------------------- sub-pixel work ----
-template <int NL, int NS>
+template <int NL, int NS, bool TAB>
 __device__ __forceinline__ float surface_brightness(const SampleC& sc, const EplC& e,
-                                                    const LightC* L, float x, float y) {
+                                                    const LightC* L, const float4* tab, float x,
+                                                    float y) {
   float ax, ay;
-  epl_alpha(e, sc.cE, sc.nq, x, y, ax, ay);
+  if (TAB) {
+    const float dx = x - e.xc, dy = y - e.yc;
+    const float xp = fmaf(e.cs, dx, e.sn * dy);
+    const float yp = fmaf(e.cs, dy, -e.sn * dx);
+    const float R2 = fmaxf(fmaf(e.q2 * xp, xp, yp * yp), R_MIN2);
+    const float ir = rsq(R2);
+    const float cph = e.q * xp * ir, sph = yp * ir;
+    const TabF F = table_eval<false>(tab, cph, sph);
+    const float A = e.CA * ex2(e.ht * lg2(R2));
+    const float aLr = A * fmaf(cph, F.Fr, -sph * F.Fi);
+    const float aLi = A * fmaf(cph, F.Fi, sph * F.Fr);
+    ax = fmaf(e.cs, aLr, -e.sn * aLi);
+    ay = fmaf(e.sn, aLr, e.cs * aLi);
+  } else {
+    epl_alpha(e, sc.cE, sc.nq, x, y, ax, ay);
+  }
   const float bx = x - ax - fmaf(sc.g1, x, sc.g2 * y);
   const float by = y - ay - fmaf(sc.g2, x, -sc.g1 * y);
   float sb = 0.f;
@@ -146,9 +204,10 @@ __device__ __forceinline__ float surface_brightness(const SampleC& sc, const Epl
 
 // Adds u x d SB / d(native parameters) at one sub-pixel to acc (see
 // epl_finish / sersic_finish for the accumulator meanings).
-template <int NL, int NS>
+template <int NL, int NS, bool TAB>
 __device__ __forceinline__ void subpixel_adjoint(const SampleC& sc, const EplC& e, const LightC* L,
-                                                 float x, float y, float u, float* acc) {
+                                                 const float4* tab, float x, float y, float u,
+                                                 float* acc) {
   const float dx = x - e.xc, dy = y - e.yc;
   const float xp = fmaf(e.cs, dx, e.sn * dy);
   const float yp = fmaf(e.cs, dy, -e.sn * dx);
@@ -157,11 +216,20 @@ __device__ __forceinline__ void subpixel_adjoint(const SampleC& sc, const EplC& 
   const float iR2 = ir * ir;
   const float cph = e.q * xp * ir, sph = yp * ir;
   const float wr = fmaf(cph, cph, -sph * sph), wi = 2.f * cph * sph;
-  float Er, Ei, Tr, Ti;
-  horner2(sc.cE, sc.cT, sc.nq, wr, wi, Er, Ei, Tr, Ti);
-  const float zr = -e.f * wr, zi = -e.f * wi;
-  const float Fr = 1.f + fmaf(zr, Er, -zi * Ei);
-  const float Fi = fmaf(zr, Ei, zi * Er);
+  float Er, Ei, Tr, Ti, Fr, Fi, zr, zi;
+  TabF tf;
+  if (TAB) {
+    tf = table_eval<true>(tab, cph, sph);
+    Fr = tf.Fr;
+    Fi = tf.Fi;
+    Er = Ei = Tr = Ti = zr = zi = 0.f;
+  } else {
+    horner2(sc.cE, sc.cT, sc.nq, wr, wi, Er, Ei, Tr, Ti);
+    zr = -e.f * wr;
+    zi = -e.f * wi;
+    Fr = 1.f + fmaf(zr, Er, -zi * Ei);
+    Fi = fmaf(zr, Ei, zi * Er);
+  }
   const float Lm = lg2(R2);
   const float A = e.CA * ex2(e.ht * Lm);
   const float Qr = A * cph, Qi = A * sph;  // A e^{i vphi}
@@ -187,6 +255,25 @@ __device__ __forceinline__ void subpixel_adjoint(const SampleC& sc, const EplC& 
   const float vLy = fmaf(e.cs, vy, -e.sn * vx);
   const float s1 = fmaf(vLx, aLr, vLy * aLi);    // v . alpha
   const float s1i = fmaf(vLy, aLr, -vLx * aLi);  // v . (i alpha)
+  const float lnR = 0.34657359027997264f * Lm;  // ln(2)/2 log2(R^2)
+  const float dphq = -xp * yp * iR2;
+  if (TAB) {
+    // table derivatives at fixed (the other) arguments: dF/dvphi, dF/dq, dF/dt
+    const float PFr = fmaf(Qr, tf.Pr, -Qi * tf.Pi), PFi = fmaf(Qr, tf.Pi, Qi * tf.Pr);
+    const float QFr = fmaf(Qr, tf.Qr, -Qi * tf.Qi), QFi = fmaf(Qr, tf.Qi, Qi * tf.Qr);
+    const float TFr = fmaf(Qr, tf.Tr, -Qi * tf.Ti), TFi = fmaf(Qr, tf.Ti, Qi * tf.Tr);
+    const float S13 = s1i + fmaf(vLx, PFr, vLy * PFi);
+    const float sQ = fmaf(vLx, QFr, vLy * QFi), sT = fmaf(vLx, TFr, vLy * TFi);
+    acc[0] += s1;
+    acc[1] = fmaf(s1, e.lnb - lnR, acc[1] + sT);
+    acc[2] = fmaf(s1, fmaf(e.omt * e.q * xp * xp, iR2, e.a0), fmaf(S13, dphq, acc[2] + sQ));
+    const float Dx = iR2 * fmaf(e.omt * e.q2 * xp, s1, -e.q * yp * S13);
+    const float Dy = iR2 * fmaf(e.omt * yp, s1, e.q * xp * S13);
+    acc[3] += fmaf(yp, Dx, fmaf(-xp, Dy, s1i));  // d alpha/d phi (lens rotation)
+    acc[4] += Dx;
+    acc[5] += Dy;
+    return;
+  }
   // dF/dt = z (Tr + i Ti)
   const float TFr = fmaf(zr, Tr, -zi * Ti), TFi = fmaf(zr, Ti, zi * Tr);
   const float QTr = fmaf(Qr, TFr, -Qi * TFi), QTi = fmaf(Qr, TFi, Qi * TFr);
@@ -201,9 +288,7 @@ __device__ __forceinline__ void subpixel_adjoint(const SampleC& sc, const EplC& 
   const float P3r = fmaf(P2r, wr, -P2i * wi), P3i = fmaf(P2r, wi, P2i * wr);
   const float s3 = fmaf(vLx, P3r, vLy * P3i);
   const float s3i = fmaf(vLy, P3r, -vLx * P3i);
-  const float lnR = 0.34657359027997264f * Lm;  // ln(2)/2 log2(R^2)
   const float S13 = fmaf(-2.f * e.f, s3i, s1i);
-  const float dphq = -xp * yp * iR2;
   acc[0] += s1;
   acc[1] = fmaf(s1, e.lnb - lnR, acc[1] + sT);
   acc[2] = fmaf(s1, fmaf(e.omt * e.q * xp * xp, iR2, e.a0), fmaf(S13, dphq, fmaf(-e.dfdq, s3, acc[2])));
@@ -239,13 +324,89 @@ __device__ __forceinline__ void buffers(const SysParams& sp, float* dsm, bool tw
   }
 }
 
+// Phase 1: bin the sub-pixel surface brightness into the padded buffer A.
+template <int NL, int NS, bool TAB>
+__device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& sc, const EplC& e,
+                                           const LightC* L, const float4* tab, float* A) {
+  const int s = sp.s, npix = sp.ny * sp.nx;
+  const float D = sp.D;
+  PixelWalk pw(sp.nx);
+  for (int p = threadIdx.x; p < npix; p += THREADS, pw.next()) {
+    const float xj = (float)pw.j + sp.xg0, yi = (float)pw.i + sp.yg0;
+    float acc = 0.f;
+    for (int k = 0; k < s; ++k) {
+      const float y = (yi + sp.off[k]) * D;
+      for (int l = 0; l < s; ++l) {
+        const float x = (xj + sp.off[l]) * D;
+        acc += surface_brightness<NL, NS, TAB>(sc, e, L, tab, x, y);
+      }
+    }
+    A[(size_t)(pw.i + sp.cy) * sp.Wp + pw.j + sp.cx] = acc * sp.scale;
+  }
+}
+
+// Phase 4: sub-pixel adjoint; per-thread FP32 sums are flushed into the
+// per-warp sums redP every FLUSH_PIX pixels, which bounds the FP32
+// accumulation length (near the mode the gradient is a small difference of
+// large sums).
+template <int NL, int NS, bool TAB>
+__device__ __forceinline__ void adjoint_pixels(const SysParams& sp, const SampleC& sc,
+                                               const EplC& e, const LightC* L, const float4* tab,
+                                               const float* A, float (*redP)[MAX_P]) {
+  constexpr int P = 8 + 7 * (NL + NS);
+  constexpr int FLUSH_PIX = 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = sp.s, npix = sp.ny * sp.nx, Wp = sp.Wp, cy = sp.cy, cx = sp.cx;
+  const float D = sp.D;
+  float acc[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) acc[k] = 0.f;
+  const int iters = (npix + THREADS - 1) / THREADS;  // same trip count in every lane
+  PixelWalk pw(sp.nx);
+  for (int it = 0; it < iters; ++it, pw.next()) {
+    const int p = threadIdx.x + it * THREADS;
+    if (p < npix) {
+      const float u = A[(size_t)(pw.i + cy) * Wp + pw.j + cx];
+      const float xj = (float)pw.j + sp.xg0, yi = (float)pw.i + sp.yg0;
+      for (int k = 0; k < s; ++k) {
+        const float y = (yi + sp.off[k]) * D;
+        for (int l = 0; l < s; ++l) {
+          const float x = (xj + sp.off[l]) * D;
+          subpixel_adjoint<NL, NS, TAB>(sc, e, L, tab, x, y, u, acc);
+        }
+      }
+    }
+    if ((it + 1) % FLUSH_PIX == 0 || it + 1 == iters) {
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        float v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) redP[warp][k] += v;
+        acc[k] = 0.f;
+      }
+    }
+  }
+}
+
+// The row's surrogate table into shared memory (when the row uses it).
+template <bool SURR>
+__device__ __forceinline__ void load_table(const SysParams& sp, const SampleC& sc, float4* tab) {
+  if (SURR && sc.use_table) {
+    const float4* src = sp.table + (size_t)blockIdx.x * 2 * TABLE_M;
+    for (int k = threadIdx.x; k < 2 * TABLE_M; k += THREADS) tab[k] = src[k];
+  }
+  __syncthreads();
+}
+
 // Forward: log p per row, or (img != nullptr) the model image per row.
-template <int NL, int NS>
+template <int NL, int NS, bool SURR>
 __global__ void __launch_bounds__(THREADS, 2)
 k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta, int B,
           float* __restrict__ logp, float* __restrict__ img) {
   extern __shared__ __align__(16) float dsm[];
   __shared__ SmemStatic st;
+  __shared__ float4 tab[SURR ? 2 * TABLE_M : 1];
   SampleC& sc = st.sc;
   const int b = blockIdx.x;
   if (b >= B) return;
@@ -266,25 +427,15 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
     }
     return;
   }
+  load_table<SURR>(sp, sc, tab);
   const EplC e = sc.epl;
   LightC L[NL + NS];
 #pragma unroll
   for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
-  const int s = sp.s;
-  const float D = sp.D;
-  PixelWalk pw(sp.nx);
-  for (int p = threadIdx.x; p < npix; p += THREADS, pw.next()) {
-    const float xj = (float)pw.j + sp.xg0, yi = (float)pw.i + sp.yg0;
-    float acc = 0.f;
-    for (int k = 0; k < s; ++k) {
-      const float y = (yi + sp.off[k]) * D;
-      for (int l = 0; l < s; ++l) {
-        const float x = (xj + sp.off[l]) * D;
-        acc += surface_brightness<NL, NS>(sc, e, L, x, y);
-      }
-    }
-    A[(size_t)(pw.i + sp.cy) * sp.Wp + pw.j + sp.cx] = acc * sp.scale;
-  }
+  if (SURR && sc.use_table)
+    bin_pixels<NL, NS, true>(sp, sc, e, L, tab, A);
+  else
+    bin_pixels<NL, NS, false>(sp, sc, e, L, tab, A);
   __syncthreads();
   float csum = 0.f, ccomp = 0.f;
   float* out = want_img ? img + (size_t)b * npix : nullptr;
@@ -306,13 +457,14 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
 }
 
 // Forward + adjoint: log p and d log p / d theta per row.
-template <int NL, int NS>
+template <int NL, int NS, bool SURR>
 __global__ void __launch_bounds__(THREADS, 2)
 k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, int B,
        float* __restrict__ logp, float* __restrict__ grad) {
   constexpr int P = 8 + 7 * (NL + NS);
   extern __shared__ __align__(16) float dsm[];
   __shared__ SmemStatic st;
+  __shared__ float4 tab[SURR ? 2 * TABLE_M : 1];
   SampleC& sc = st.sc;
   const int b = blockIdx.x;
   if (b >= B) return;
@@ -327,7 +479,6 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
   }
   for (int k = threadIdx.x; k < NWARPS * MAX_P; k += THREADS) (&st.redP[0][0])[k] = 0.f;
   __syncthreads();
-  const int npix = sp.ny * sp.nx;
   if (sc.status != 0) {
     const float lv = sc.status == 2 ? __int_as_float(0x7fc00000) : -__int_as_float(0x7f800000);
     const float gv = sc.status == 2 ? __int_as_float(0x7fc00000) : 0.f;
@@ -335,29 +486,18 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
     if (threadIdx.x < P) grad[(size_t)b * P + threadIdx.x] = gv;
     return;
   }
+  load_table<SURR>(sp, sc, tab);
+  const bool use_tab = SURR && sc.use_table;
   const EplC e = sc.epl;
   LightC L[NL + NS];
 #pragma unroll
   for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
-  const int s = sp.s;
-  const float D = sp.D;
   const int Wp = sp.Wp, cy = sp.cy, cx = sp.cx, nx = sp.nx;
   // phase 1
-  {
-    PixelWalk pw(nx);
-    for (int p = threadIdx.x; p < npix; p += THREADS, pw.next()) {
-      const float xj = (float)pw.j + sp.xg0, yi = (float)pw.i + sp.yg0;
-      float acc = 0.f;
-      for (int k = 0; k < s; ++k) {
-        const float y = (yi + sp.off[k]) * D;
-        for (int l = 0; l < s; ++l) {
-          const float x = (xj + sp.off[l]) * D;
-          acc += surface_brightness<NL, NS>(sc, e, L, x, y);
-        }
-      }
-      A[(size_t)(pw.i + cy) * Wp + pw.j + cx] = acc * sp.scale;
-    }
-  }
+  if (use_tab)
+    bin_pixels<NL, NS, true>(sp, sc, e, L, tab, A);
+  else
+    bin_pixels<NL, NS, false>(sp, sc, e, L, tab, A);
   __syncthreads();
   // phase 2
   float csum = 0.f, ccomp = 0.f;
@@ -379,40 +519,11 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
     A[(size_t)(i + cy) * Wp + j + cx] = g * scale;
   });
   __syncthreads();
-  // phase 4: per-thread FP32 sums are flushed into per-warp sums every
-  // FLUSH_PIX pixels, which bounds the FP32 accumulation length (the
-  // gradient is a small difference of large sums near the mode)
-  constexpr int FLUSH_PIX = 2;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float acc[P];
-#pragma unroll
-  for (int k = 0; k < P; ++k) acc[k] = 0.f;
-  const int iters = (npix + THREADS - 1) / THREADS;  // same trip count in every lane
-  PixelWalk pw(nx);
-  for (int it = 0; it < iters; ++it, pw.next()) {
-    const int p = threadIdx.x + it * THREADS;
-    if (p < npix) {
-      const float u = A[(size_t)(pw.i + cy) * Wp + pw.j + cx];
-      const float xj = (float)pw.j + sp.xg0, yi = (float)pw.i + sp.yg0;
-      for (int k = 0; k < s; ++k) {
-        const float y = (yi + sp.off[k]) * D;
-        for (int l = 0; l < s; ++l) {
-          const float x = (xj + sp.off[l]) * D;
-          subpixel_adjoint<NL, NS>(sc, e, L, x, y, u, acc);
-        }
-      }
-    }
-    if ((it + 1) % FLUSH_PIX == 0 || it + 1 == iters) {
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        float v = acc[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) st.redP[warp][k] += v;
-        acc[k] = 0.f;
-      }
-    }
-  }
+  // phase 4
+  if (use_tab)
+    adjoint_pixels<NL, NS, true>(sp, sc, e, L, tab, A, st.redP);
+  else
+    adjoint_pixels<NL, NS, false>(sp, sc, e, L, tab, A, st.redP);
   __syncthreads();
   if (threadIdx.x < P) {
     double v = 0.0;
@@ -425,7 +536,7 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
     const int c = threadIdx.x;
     float g[8];
     if (c == 0) {
-      epl_finish(st.fin[0], st.gsum, g);
+      epl_finish(st.fin[0], st.gsum, g, use_tab);
 #pragma unroll
       for (int k = 0; k < 8; ++k) grad[(size_t)b * P + k] = g[k] + sc.dprior[k];
     } else {

@@ -83,6 +83,7 @@ struct SampleC {
   float4 cT[N_MAX / 4];    // t-derivative coefficients c_n h_n (-f)^{n-1}
   int nq;                  // number of float4 chunks (N rounded up to a multiple of 4)
   int status;              // 0 ok, 1 outside domain/support (-inf), 2 NaN
+  int use_table;           // surrogate table covers this row
   double logprior;
   float dprior[MAX_P];
 };
@@ -208,6 +209,8 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
       f_epl = c;
       sc.g1 = th[6];
       sc.g2 = th[7];
+      sc.use_table = sp.table != nullptr && q >= sp.sq_lo && q <= sp.sq_hi &&
+                     th[1] >= sp.sg_lo && th[1] <= sp.sg_hi;
     } else {
       LightC& L = sc.light[lane - 1];
       const float* p = th + 8 + 7 * (lane - 1);
@@ -405,11 +408,13 @@ __device__ inline void sersic_finish(const FinishC& F, const double* a, float* g
 
 // EPL + shear native accumulators:
 // [0] sum s1 (theta_E), [1] d/dt, [2] d/dq, [3] sum kappa v.(iY) with
-// d/dphi = -2 f [3], [4] sum v.d alpha/dx', [5] sum v.d alpha/dy' (lens frame;
-// the centre gradient is minus these), [6] d/dg1, [7] d/dg2.
+// d/dphi = -2 f [3] (exact series) or d/dphi itself (surrogate table),
+// [4] sum v.d alpha/dx', [5] sum v.d alpha/dy' (lens frame; the centre
+// gradient is minus these), [6] d/dg1, [7] d/dg2.
 // With f = |e| and d phi/d e = (-e2, e1)/(2 f^2) the rotation part of d/de is
-// [3] (sin 2phi, -cos 2phi): no division by |e|.
-__device__ inline void epl_finish(const FinishC& F, const double* a, float* g) {
+// [3] (sin 2phi, -cos 2phi) for the series: no division by |e|.
+__device__ inline void epl_finish(const FinishC& F, const double* a, float* g,
+                                  bool rot_is_dphi = false) {
   const float gxl = -(float)a[4], gyl = -(float)a[5];
   const float cc = fmaxf(F.c, 1e-30f);
   const float c2p = F.e1 / cc, s2p = F.e2 / cc;
@@ -417,8 +422,14 @@ __device__ inline void epl_finish(const FinishC& F, const double* a, float* g) {
   const float dq = (float)a[2], rot = (float)a[3];
   g[0] = F.t / F.p0 * (float)a[0];
   g[1] = (float)a[1];
-  g[2] = dq * dqdc * c2p + rot * s2p;
-  g[3] = dq * dqdc * s2p - rot * c2p;
+  if (rot_is_dphi) {
+    const float k = rot / (2.f * cc * cc);
+    g[2] = dq * dqdc * c2p - k * F.e2;
+    g[3] = dq * dqdc * s2p + k * F.e1;
+  } else {
+    g[2] = dq * dqdc * c2p + rot * s2p;
+    g[3] = dq * dqdc * s2p - rot * c2p;
+  }
   g[4] = F.cs * gxl - F.sn * gyl;
   g[5] = F.sn * gxl + F.cs * gyl;
   g[6] = (float)a[6];

@@ -1,0 +1,785 @@
+// Learned EPL deflection surrogate: training data from the exact series,
+// training (forward, backward and Adam on BF16 tensor cores with FP32
+// accumulation and FP32 master weights), inference, and the per-sample
+// angular tables the lens kernels interpolate.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/gl.h"
+#include "gl_internal.cuh"
+#include "gl_mlp.cuh"
+
+namespace gl {
+void set_last_error(const std::string& msg);
+}
+
+using namespace gl::mlp;
+
+struct gl_surrogate {
+  int device = 0;
+  float* params = nullptr;        // [NPARAM] FP32 master weights
+  __nv_bfloat16* wb = nullptr;    // [NBF16] packed BF16 operands
+  float final_loss = NAN;
+  float q_lo = 0.5f, q_hi = 1.f, g_lo = 1.7f, g_hi = 2.3f;  // training domain
+};
+
+namespace {
+
+constexpr int TILE = 128;   // rows per training CTA (8 warps x 16)
+constexpr int SROW = 136;   // padded row stride (bf16) of transposed tiles
+constexpr int SPROW = 72;   // padded row stride (bf16) of the SiLU' tiles
+
+gl_status fail(gl_status st, const std::string& msg) {
+  gl::set_last_error(msg);
+  return st;
+}
+
+#define SUR_CUDA(call, what)                                                              \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess)                                                                \
+      return fail(_e == cudaErrorMemoryAllocation ? GL_ENOMEM : GL_ECUDA,                \
+                  std::string(what) + ": " + cudaGetErrorString(_e));                     \
+  } while (0)
+
+// splitmix64 (Steele, Lea & Flood 2014): a counter-based generator
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__host__ __device__ inline double u01(uint64_t seed, uint64_t i, int k) {
+  return (double)(splitmix64(seed ^ (i * 4 + k) * 0xD1B54A32D192ED03ull) >> 11) * 0x1.0p-53;
+}
+
+// Remainder of the series beyond two terms, sum_{n>=3} c_n z^n, by the
+// coefficient recurrence (FP64, until the terms are below 1e-16).
+__device__ inline void series_remainder(double q, double t, double vphi, double& rr, double& ri) {
+  const double f = (1.0 - q) / (1.0 + q);
+  const double zr = -f * cos(2.0 * vphi), zi = -f * sin(2.0 * vphi);
+  double c = 1.0, tr = 1.0, ti = 0.0;  // c_n and z^n
+  rr = 0.0;
+  ri = 0.0;
+  for (int n = 1; n < 400; ++n) {
+    c *= (2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
+    const double nr = tr * zr - ti * zi, ni = tr * zi + ti * zr;
+    tr = nr;
+    ti = ni;
+    if (n >= 3) {
+      rr += c * tr;
+      ri += c * ti;
+      if (fabs(c) * (fabs(tr) + fabs(ti)) < 1e-16) break;
+    }
+  }
+}
+
+// Training tuples (q, gamma, log r/theta_E, vphi) and targets OUT_SCALE x the
+// series remainder, q ~ U(q_lo, q_hi), gamma ~ U, r/theta_E ~ logU(r_lo, r_hi),
+// vphi ~ U(0, 2 pi).
+__global__ void k_gen_data(float4* __restrict__ X, float2* __restrict__ Y, long long n,
+                           uint64_t seed, float q_lo, float q_hi, float g_lo, float g_hi,
+                           float lr_lo, float lr_hi) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double q = q_lo + (q_hi - q_lo) * u01(seed, i, 0);
+    const double g = g_lo + (g_hi - g_lo) * u01(seed, i, 1);
+    const double lr = lr_lo + (lr_hi - lr_lo) * u01(seed, i, 2);
+    const double vp = 2.0 * 3.14159265358979323846 * u01(seed, i, 3);
+    double rr, ri;
+    series_remainder(q, g - 1.0, vp, rr, ri);
+    X[i] = make_float4((float)q, (float)g, (float)lr, (float)vp);
+    Y[i] = make_float2((float)(rr * OUT_SCALE), (float)(ri * OUT_SCALE));
+  }
+}
+
+__global__ void k_init_params(float* __restrict__ p, uint64_t seed) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= NPARAM) return;
+  float fan_in = 0.f;
+  bool bias = false;
+  if (k < OFF_B1) fan_in = NIN;
+  else if (k < OFF_W2) bias = true;
+  else if (k < OFF_B2) fan_in = H;
+  else if (k < OFF_W3) bias = true;
+  else if (k < OFF_B3) fan_in = H;
+  else if (k < OFF_W4) bias = true;
+  else if (k < OFF_B4) fan_in = H;
+  else if (k < OFF_W5) bias = true;
+  else if (k < OFF_B5) fan_in = H;
+  else bias = true;
+  // He-uniform for SiLU layers; zero biases; small output layer
+  float v = 0.f;
+  if (!bias) {
+    const float lim = sqrtf(6.f / fan_in) * (k >= OFF_W5 ? 0.1f : 1.f);
+    v = (float)(2.0 * u01(seed, k, 0) - 1.0) * lim;
+  }
+  p[k] = v;
+}
+
+// FP32 parameters -> BF16 operand layouts (gl_mlp.cuh).
+__global__ void k_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ wb) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= NBF16) return;
+  float v = 0.f;
+  if (k < BOFF_P2) {
+    const int o = (k - BOFF_P1) / 16, i = (k - BOFF_P1) % 16;
+    v = i < NIN ? p[OFF_W1 + o * NIN + i] : 0.f;
+  } else if (k < BOFF_P5) {
+    const int l = (k - BOFF_P2) / (H * H), r = (k - BOFF_P2) % (H * H);
+    const int off = l == 0 ? OFF_W2 : (l == 1 ? OFF_W3 : OFF_W4);
+    v = p[off + r];
+  } else if (k < BOFF_T2) {
+    const int o = (k - BOFF_P5) / H, i = (k - BOFF_P5) % H;
+    v = o < NOUT ? p[OFF_W5 + o * H + i] : 0.f;
+  } else if (k < BOFF_T5) {
+    const int l = (k - BOFF_T2) / (H * H), r = (k - BOFF_T2) % (H * H);
+    const int i = r / H, o = r % H;  // T[in][out] = W[out][in]
+    const int off = l == 0 ? OFF_W2 : (l == 1 ? OFF_W3 : OFF_W4);
+    v = p[off + o * H + i];
+  } else {
+    const int i = (k - BOFF_T5) / 16, o = (k - BOFF_T5) % 16;
+    v = o < NOUT ? p[OFF_W5 + o * H + i] : 0.f;
+  }
+  wb[k] = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// CTA-wide weight-gradient contraction dW[o][i] = sum_rows dZ[row][o] A[row][i]
+// over the 128 rows of the tile, from transposed tiles dZT[o][row], AT[i][row]
+// (row stride SROW). Warp w owns output rows 16 mt.., columns 8 nt.. as listed.
+__device__ __forceinline__ void dw_tile(const __nv_bfloat16* dZT, const __nv_bfloat16* AT, int mt,
+                                        int nt, float (&acc)[4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+  acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
+#pragma unroll
+  for (int kk = 0; kk < TILE / 16; ++kk) {
+    uint32_t a[4];
+    const __nv_bfloat16* za = dZT + (16 * mt + g) * SROW + kk * 16 + 2 * c;
+    a[0] = lds32(za);
+    a[1] = lds32(za + 8 * SROW);
+    a[2] = lds32(za + 8);
+    a[3] = lds32(za + 8 * SROW + 8);
+    const __nv_bfloat16* bb = AT + (8 * nt + g) * SROW + kk * 16 + 2 * c;
+    mma16816(acc, a, lds32(bb), lds32(bb + 8));
+  }
+}
+
+struct TrainSmem {
+  __nv_bfloat16 sp[4][TILE * SPROW];  // SiLU'(z) per hidden layer, [row][col]
+  __nv_bfloat16 AT0[16 * SROW];       // inputs, transposed [col][row]
+  __nv_bfloat16 AT[4][H * SROW];      // hidden activations, transposed
+  __nv_bfloat16 dZT[H * SROW];        // current layer's dZ, transposed
+  float loss[8];
+};
+
+// One training step for a 128-row tile: forward, MSE loss, backward; the
+// tile's loss and gradient go to its own slot (no atomics).
+// grid = batch / 128, block = 256.
+__global__ void __launch_bounds__(256, 1)
+k_train(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
+        const float4* __restrict__ X, const float2* __restrict__ Y, long long n_data,
+        long long row0, long long stride, float inv_batch, float* __restrict__ gpart,
+        float* __restrict__ lpart) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, c = lane & 3;
+  const int r0 = warp * 16;
+  float* gp = gpart + (size_t)blockIdx.x * NPARAM;
+
+  for (int k = tid; k < 16 * SROW; k += 256) S.AT0[k] = __float2bfloat16_rn(0.f);
+  for (int k = tid; k < H * SROW; k += 256) S.dZT[k] = __float2bfloat16_rn(0.f);
+  __syncthreads();
+
+  // rows of this thread: r0+g and r0+g+8 (data index by a strided permutation)
+  long long idx[2];
+  float x[2][4], tgt[2][2];
+  for (int h = 0; h < 2; ++h) {
+    const long long tr = (long long)blockIdx.x * TILE + r0 + g + 8 * h;
+    idx[h] = (row0 + tr * stride) % n_data;
+    const float4 v = X[idx[h]];
+    features(v.x, v.y, v.z, v.w, x[h]);
+    const float2 t = Y[idx[h]];
+    tgt[h][0] = t.x;
+    tgt[h][1] = t.y;
+  }
+  if (c < 2)
+    for (int h = 0; h < 2; ++h) {
+      S.AT0[(2 * c) * SROW + r0 + g + 8 * h] = __float2bfloat16_rn(x[h][2 * c]);
+      S.AT0[(2 * c + 1) * SROW + r0 + g + 8 * h] = __float2bfloat16_rn(x[h][2 * c + 1]);
+    }
+  // forward
+  uint32_t a1[1][4];
+  input_frag(x[0], x[1], a1);
+  float z[8][4];
+  uint32_t a[4][4];
+  layer_mma<1>(a1, wb + BOFF_P1, z);
+  const float* bias[4] = {params + OFF_B1, params + OFF_B2, params + OFF_B3, params + OFF_B4};
+  const __nv_bfloat16* Wl[3] = {wb + BOFF_P2, wb + BOFF_P3, wb + BOFF_P4};
+  for (int l = 0; l < 4; ++l) {
+    if (l > 0) layer_mma<4>(a, Wl[l - 1], z);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int col = nt * 8 + 2 * c + (j & 1), row = r0 + g + 8 * (j >> 1);
+        const float zz = z[nt][j] + bias[l][col];
+        const float s = sigm(zz);
+        const float act = zz * s;
+        z[nt][j] = act;
+        S.sp[l][row * SPROW + col] = __float2bfloat16_rn(s * (1.f + zz * (1.f - s)));
+        S.AT[l][col * SROW + row] = __float2bfloat16_rn(act);
+      }
+    c_to_a(z, a);
+  }
+  float y[4];
+  out_mma(a, wb + BOFF_P5, y);
+  // loss and output gradient (cols 0, 1 live in lanes c == 0)
+  float dz5[4] = {0.f, 0.f, 0.f, 0.f};
+  float lsum = 0.f;
+  if (c == 0) {
+    for (int h = 0; h < 2; ++h)
+      for (int o = 0; o < 2; ++o) {
+        const float e = y[2 * h + o] + params[OFF_B5 + o] - tgt[h][o];
+        lsum += e * e;
+        dz5[2 * h + o] = 2.f * e * inv_batch;
+      }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  if (lane == 0) S.loss[warp] = lsum;
+  // output layer: dZ5^T (rows 0, 1 of dZT)
+  if (c == 0)
+    for (int h = 0; h < 2; ++h)
+      for (int o = 0; o < 2; ++o)
+        S.dZT[o * SROW + r0 + g + 8 * h] = __float2bfloat16_rn(dz5[2 * h + o]);
+  // db5
+  {
+    float s0 = dz5[0] + dz5[2], s1 = dz5[1] + dz5[3];
+    for (int o = 4; o < 32; o <<= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    // per-warp partial: summed over warps below through shared memory
+    __shared__ float db5[8][2];
+    if (lane == 0) {
+      db5[warp][0] = s0;
+      db5[warp][1] = s1;
+    }
+    __syncthreads();
+    if (tid < 2) {
+      float v = 0.f;
+      for (int w = 0; w < 8; ++w) v += db5[w][tid];
+      gp[OFF_B5 + tid] = v;
+    }
+    if (tid == 0) {
+      float v = 0.f;
+      for (int w = 0; w < 8; ++w) v += S.loss[w];
+      lpart[blockIdx.x] = v;
+    }
+  }
+  // dW5 = dZ5^T A4: warp w -> output rows 0..15 (0, 1 real), columns 8w..8w+7
+  {
+    float acc[4];
+    dw_tile(S.dZT, S.AT[3], 0, warp, acc);
+    if (g < NOUT) {
+      gp[OFF_W5 + g * H + warp * 8 + 2 * c] = acc[0];
+      gp[OFF_W5 + g * H + warp * 8 + 2 * c + 1] = acc[1];
+    }
+  }
+  // dA4 = dZ5 W5
+  float dA[8][4];
+  {
+    uint32_t ad[1][4];
+    ad[0][0] = pack_bf16(dz5[0], dz5[1]);
+    ad[0][1] = pack_bf16(dz5[2], dz5[3]);
+    ad[0][2] = 0u;
+    ad[0][3] = 0u;
+    layer_mma<1>(ad, wb + BOFF_T5, dA);
+  }
+  const __nv_bfloat16* Tl[3] = {wb + BOFF_T2, wb + BOFF_T3, wb + BOFF_T4};
+  const int OFF_W[4] = {OFF_W1, OFF_W2, OFF_W3, OFF_W4};
+  const int OFF_B[4] = {OFF_B1, OFF_B2, OFF_B3, OFF_B4};
+  for (int l = 3; l >= 0; --l) {
+    __syncthreads();  // dZT / previous dW reads done
+    // dZ_l = dA_l * SiLU'(z_l)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int col = nt * 8 + 2 * c + (j & 1), row = r0 + g + 8 * (j >> 1);
+        const float v = dA[nt][j] * __bfloat162float(S.sp[l][row * SPROW + col]);
+        dA[nt][j] = v;
+        S.dZT[col * SROW + row] = __float2bfloat16_rn(v);
+      }
+    // db_l (row sums): rows g and g+8, then over g
+    __shared__ float dbw[8][H];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        float s = dA[nt][e] + dA[nt][2 + e];
+        for (int o = 4; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (g == 0) dbw[warp][nt * 8 + 2 * c + e] = s;
+      }
+    __syncthreads();
+    if (tid < H) {
+      float v = 0.f;
+      for (int w = 0; w < 8; ++w) v += dbw[w][tid];
+      gp[OFF_B[l] + tid] = v;
+    }
+    // dW_l = dZ_l^T A_{l-1}
+    if (l > 0) {
+      const int mt = warp >> 1;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int nt = 4 * (warp & 1) + q;
+        float acc[4];
+        dw_tile(S.dZT, S.AT[l - 1], mt, nt, acc);
+        const int o = 16 * mt + g, i = nt * 8 + 2 * c;
+        gp[OFF_W[l] + o * H + i] = acc[0];
+        gp[OFF_W[l] + o * H + i + 1] = acc[1];
+        gp[OFF_W[l] + (o + 8) * H + i] = acc[2];
+        gp[OFF_W[l] + (o + 8) * H + i + 1] = acc[3];
+      }
+      // dA_{l-1} = dZ_l W_l
+      uint32_t ad[4][4];
+      c_to_a(dA, ad);
+      layer_mma<4>(ad, Tl[l - 1], dA);
+    } else if (warp < 4) {
+      // dW1 = dZ1^T X: output rows 16 warp.., input columns 0..7 (0..3 real)
+      float acc[4];
+      dw_tile(S.dZT, S.AT0, warp, 0, acc);
+      const int o = 16 * warp + g;
+      if (c < 2) {
+        gp[OFF_W1 + o * NIN + 2 * c] = acc[0];
+        gp[OFF_W1 + o * NIN + 2 * c + 1] = acc[1];
+        gp[OFF_W1 + (o + 8) * NIN + 2 * c] = acc[2];
+        gp[OFF_W1 + (o + 8) * NIN + 2 * c + 1] = acc[3];
+      }
+    }
+  }
+}
+
+// Sum of the tiles' gradients and Adam (FP32 master weights); writes the
+// gradient itself when out_grad is non-null (tests) and skips the update when
+// lr == 0.
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ gpart, int ntiles, float lr, float b1, float b2,
+                       float eps, float bc1, float bc2, float* __restrict__ out_grad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= NPARAM) return;
+  float gsum = 0.f;
+  for (int t = 0; t < ntiles; ++t) gsum += gpart[(size_t)t * NPARAM + k];
+  if (out_grad) out_grad[k] = gsum;
+  if (lr == 0.f) return;
+  const float mk = b1 * m[k] + (1.f - b1) * gsum;
+  const float vk = b2 * v[k] + (1.f - b2) * gsum * gsum;
+  m[k] = mk;
+  v[k] = vk;
+  p[k] -= lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+}
+
+__global__ void k_sum(const float* __restrict__ x, int n, float* __restrict__ out) {
+  float s = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ float w[32];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += w[k];
+    *out = t;
+  }
+}
+
+// F (Re, Im) for raw tuples (q, gamma, log r/theta_E, vphi): one 16-row tile
+// per warp.
+__global__ void k_infer(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
+                        const float4* __restrict__ X, int n, float2* __restrict__ F) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile * 16 < n;
+       tile += warps) {
+    float x[2][4], t0[4] = {0.f, 0.f, 0.f, 0.f};
+    float4 raw[2];
+    for (int h = 0; h < 2; ++h) {
+      const int r = min(tile * 16 + g + 8 * h, n - 1);
+      raw[h] = X[r];
+      features(raw[h].x, raw[h].y, raw[h].z, raw[h].w, x[h]);
+    }
+    float y[4], dy[4];
+    forward_jvp(wb, params, x[0], x[1], t0, t0, y, dy);
+    if (c == 0)
+      for (int h = 0; h < 2; ++h) {
+        const int r = tile * 16 + g + 8 * h;
+        if (r >= n) continue;
+        const Base b = base_terms(raw[h].x, raw[h].y - 1.f, raw[h].w);
+        F[r] = make_float2(b.Fr + y[2 * h] / OUT_SCALE, b.Fi + y[2 * h + 1] / OUT_SCALE);
+      }
+  }
+}
+
+}  // namespace
+
+namespace gl {
+
+// Node j of a table: pseudo-angle pa_j = 2j/TABLE_M and its angle vphi_j in
+// [0, pi) (inverse of pa = 1 - cos/(|cos| + sin)), with d vphi/d pa = (|cos| + sin)^2.
+__device__ __forceinline__ void table_node(int j, float& vphi, float& dvdpa) {
+  const float pa = 2.f * j / TABLE_M;
+  vphi = pa <= 1.f ? atan2f(pa, 1.f - pa) : PI_F - atan2f(2.f - pa, pa - 1.f);
+  float s, c;
+  sincosf(vphi, &s, &c);
+  const float d = fabsf(c) + s;
+  dvdpa = d * d;
+}
+
+// Per-sample tables for the lens kernels from the network: for row b with EPL
+// axis ratio q and slope gamma, node j holds (F, dF/dpa, dF/dq, dF/dt) as 4
+// complex numbers, from the network at R = theta_E with forward-mode
+// derivatives. One CTA (8 warps x 16 nodes) per row; rows outside the
+// training domain are skipped (the lens kernels use the exact series there).
+__global__ void k_table(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
+                        const float* __restrict__ theta, int P, int B, float q_lo, float q_hi,
+                        float g_lo, float g_hi, float4* __restrict__ table) {
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const float* th = theta + (size_t)b * P;
+  const float e1 = th[2], e2 = th[3];
+  const float cc = sqrtf(e1 * e1 + e2 * e2);
+  const float q = (1.f - cc) / (1.f + cc), gamma = th[1];
+  if (!(q >= q_lo && q <= q_hi && gamma >= g_lo && gamma <= g_hi)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+  float x[2][4], vp[2], dv[2];
+  for (int h = 0; h < 2; ++h) {
+    table_node(warp * 16 + g + 8 * h, vp[h], dv[h]);
+    features(q, gamma, 0.f, vp[h], x[h]);
+  }
+  // tangents of the normalised inputs: d/dvphi, d/dq, d/dgamma (= d/dt)
+  const float seeds[3][4] = {{0.f, 0.f, 0.f, 1.f / PI_F}, {4.f, 0.f, 0.f, 0.f},
+                             {0.f, 1.f / 0.3f, 0.f, 0.f}};
+  float y[4], dy[3][4];
+  for (int s = 0; s < 3; ++s) forward_jvp(wb, params, x[0], x[1], seeds[s], seeds[s], y, dy[s]);
+  if (c == 0)
+    for (int h = 0; h < 2; ++h) {
+      const int j = warp * 16 + g + 8 * h;
+      const Base bt = base_terms(q, gamma - 1.f, vp[h]);
+      const float k = 1.f / OUT_SCALE;
+      float4* out = table + ((size_t)b * TABLE_M + j) * 2;
+      out[0] = make_float4(bt.Fr + k * y[2 * h], bt.Fi + k * y[2 * h + 1],
+                           dv[h] * (bt.Pr + k * dy[0][2 * h]), dv[h] * (bt.Pi + k * dy[0][2 * h + 1]));
+      out[1] = make_float4(bt.Qr + k * dy[1][2 * h], bt.Qi + k * dy[1][2 * h + 1],
+                           bt.Tr + k * dy[2][2 * h], bt.Ti + k * dy[2][2 * h + 1]);
+    }
+}
+
+// The same tables from the exact series (FP64 per node): F, dF/dvphi =
+// F'(z) 2iz, dF/dq = -F'(z) e^{2i vphi} df/dq, dF/dt = sum c_n h_n z^n, with
+// F'(z) = [t F - (2-t) E]/(2(1-z)) and F = 1 + zE. Rows with |e| above 0.5
+// (q < 1/3) are skipped: the lens kernels use the series there.
+__global__ void k_table_exact(const float* __restrict__ theta, int P, int B, float q_lo,
+                              float4* __restrict__ table) {
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const float* th = theta + (size_t)b * P;
+  const float e1 = th[2], e2 = th[3];
+  const float cc = sqrtf(e1 * e1 + e2 * e2);
+  const float qf = (1.f - cc) / (1.f + cc);
+  if (!(qf >= q_lo) || !(th[1] > 1.f && th[1] < 3.f)) return;
+  const double q = qf, t = (double)th[1] - 1.0, f = (1.0 - q) / (1.0 + q);
+  for (int j = threadIdx.x; j < TABLE_M; j += blockDim.x) {
+    float vpf, dv;
+    table_node(j, vpf, dv);
+    const double vp = vpf;
+    const double wr = cos(2.0 * vp), wi = sin(2.0 * vp);
+    const double zr = -f * wr, zi = -f * wi;
+    // E = sum_{n>=1} c_n z^{n-1}, T = sum_{n>=1} c_n h_n z^n
+    double cn = 1.0, hn = 0.0, pr = 1.0, pi = 0.0, Er = 0.0, Ei = 0.0, Tr = 0.0, Ti = 0.0;
+    for (int n = 1; n < 2000; ++n) {
+      cn *= (2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
+      hn += 1.0 / (2.0 * n - 2.0 + t) + 1.0 / (2.0 * n + 2.0 - t);
+      Er += cn * pr;  // p = z^{n-1}
+      Ei += cn * pi;
+      const double nr = pr * zr - pi * zi, ni = pr * zi + pi * zr;
+      pr = nr;
+      pi = ni;  // now z^n
+      Tr += cn * hn * pr;
+      Ti += cn * hn * pi;
+      if (fabs(cn) * (fabs(pr) + fabs(pi)) * (1.0 + hn) < 1e-18) break;
+    }
+    const double Fr = 1.0 + zr * Er - zi * Ei, Fi = zr * Ei + zi * Er;
+    const double nr = t * Fr - (2.0 - t) * Er, ni = t * Fi - (2.0 - t) * Ei;
+    const double or_ = 1.0 - zr, oi = -zi, den = 2.0 * (or_ * or_ + oi * oi);
+    const double Dr = (nr * or_ + ni * oi) / den, Di = (ni * or_ - nr * oi) / den;  // F'(z)
+    const double Pr = -2.0 * (Dr * zi + Di * zr), Pi = 2.0 * (Dr * zr - Di * zi);  // F' 2iz
+    const double dfdq = -2.0 / ((1.0 + q) * (1.0 + q));
+    const double Qr = -(Dr * wr - Di * wi) * dfdq, Qi = -(Dr * wi + Di * wr) * dfdq;
+    float4* out = table + ((size_t)b * TABLE_M + j) * 2;
+    out[0] = make_float4((float)Fr, (float)Fi, (float)(dv * Pr), (float)(dv * Pi));
+    out[1] = make_float4((float)Qr, (float)Qi, (float)Tr, (float)Ti);
+  }
+}
+
+cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B, float4* table,
+                         cudaStream_t st) {
+  if (s)
+    k_table<<<B, 256, 0, st>>>(s->wb, s->params, theta, P, B, s->q_lo, s->q_hi, s->g_lo, s->g_hi,
+                               table);
+  else
+    k_table_exact<<<B, TABLE_M, 0, st>>>(theta, P, B, 1.f / 3.f, table);
+  return cudaGetLastError();
+}
+
+void surrogate_domain(const gl_surrogate* s, float* q_lo, float* q_hi, float* g_lo, float* g_hi) {
+  if (!s) {  // tabulated exact series: |e| <= 0.5, the model's gamma range
+    *q_lo = 1.f / 3.f;
+    *q_hi = 1.f;
+    *g_lo = 1.f;
+    *g_hi = 3.f;
+    return;
+  }
+  *q_lo = s->q_lo;
+  *q_hi = s->q_hi;
+  *g_lo = s->g_lo;
+  *g_hi = s->g_hi;
+}
+
+}  // namespace gl
+
+// ------------------------------------------------------------------ C ABI --
+namespace {
+
+gl_status sur_alloc(gl_surrogate** out) {
+  gl_surrogate* s = new gl_surrogate();
+  cudaGetDevice(&s->device);
+  if (cudaMalloc(&s->params, NPARAM * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&s->wb, NBF16 * sizeof(__nv_bfloat16)) != cudaSuccess) {
+    cudaFree(s->params);
+    cudaFree(s->wb);
+    delete s;
+    return fail(GL_ENOMEM, "surrogate allocation failed");
+  }
+  *out = s;
+  return GL_OK;
+}
+
+struct TrainBuffers {
+  float4* X = nullptr;
+  float2* Y = nullptr;
+  float *m = nullptr, *v = nullptr, *gpart = nullptr, *lpart = nullptr, *loss = nullptr;
+  ~TrainBuffers() {
+    cudaFree(X);
+    cudaFree(Y);
+    cudaFree(m);
+    cudaFree(v);
+    cudaFree(gpart);
+    cudaFree(lpart);
+    cudaFree(loss);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int gl_surrogate_num_params(void) { return NPARAM; }
+
+gl_status gl_surrogate_create(const float* params_host, gl_surrogate** out) {
+  if (!out || !params_host) return fail(GL_EINVAL, "NULL argument");
+  *out = nullptr;
+  for (int k = 0; k < NPARAM; ++k)
+    if (!std::isfinite(params_host[k])) return fail(GL_EINVAL, "non-finite surrogate parameter");
+  gl_surrogate* s = nullptr;
+  gl_status r = sur_alloc(&s);
+  if (r != GL_OK) return r;
+  cudaError_t e = cudaMemcpy(s->params, params_host, NPARAM * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_pack<<<(NBF16 + 255) / 256, 256>>>(s->params, s->wb);
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    gl_surrogate_destroy(s);
+    return fail(GL_ECUDA, std::string("surrogate upload: ") + cudaGetErrorString(e));
+  }
+  *out = s;
+  return GL_OK;
+}
+
+gl_status gl_surrogate_params(const gl_surrogate* s, float* params_host) {
+  if (!s || !params_host) return fail(GL_EINVAL, "NULL argument");
+  SUR_CUDA(cudaMemcpy(params_host, s->params, NPARAM * sizeof(float), cudaMemcpyDeviceToHost),
+           "copy parameters");
+  return GL_OK;
+}
+
+void gl_surrogate_destroy(gl_surrogate* s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  cudaFree(s->params);
+  cudaFree(s->wb);
+  delete s;
+}
+
+gl_status gl_surrogate_infer(const gl_surrogate* s, const float* x, int N, float* y, void* stream) {
+  if (!s) return fail(GL_EINVAL, "surrogate is NULL");
+  if (N < 0 || (N > 0 && (!x || !y))) return fail(GL_EINVAL, "bad x, y or N");
+  if (N == 0) return GL_OK;
+  const int tiles = (N + 15) / 16;
+  k_infer<<<(tiles + 7) / 8, 256, 0, (cudaStream_t)stream>>>(
+      s->wb, s->params, reinterpret_cast<const float4*>(x), N, reinterpret_cast<float2*>(y));
+  SUR_CUDA(cudaGetLastError(), "surrogate inference launch");
+  return GL_OK;
+}
+
+gl_status gl_surrogate_loss_grad(const gl_surrogate* s, const float* x, const float* target, int N,
+                                 float* loss_host, float* grad_host) {
+  if (!s || !x || !target || !loss_host || !grad_host) return fail(GL_EINVAL, "NULL argument");
+  if (N <= 0 || N % TILE != 0) return fail(GL_EINVAL, "N must be a positive multiple of 128");
+  const int ntiles = N / TILE;
+  TrainBuffers tb;
+  SUR_CUDA(cudaMalloc(&tb.gpart, (size_t)ntiles * NPARAM * sizeof(float)), "alloc");
+  SUR_CUDA(cudaMalloc(&tb.lpart, ntiles * sizeof(float)), "alloc");
+  SUR_CUDA(cudaMalloc(&tb.loss, NPARAM * sizeof(float) + sizeof(float)), "alloc");
+  SUR_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(TrainSmem)),
+           "smem limit");
+  k_train<<<ntiles, 256, sizeof(TrainSmem)>>>(s->wb, s->params, reinterpret_cast<const float4*>(x),
+                                              reinterpret_cast<const float2*>(target), N, 0, 1,
+                                              1.f / N, tb.gpart, tb.lpart);
+  k_adam<<<(NPARAM + 255) / 256, 256>>>(nullptr, nullptr, nullptr, tb.gpart, ntiles, 0.f, 0.f, 0.f,
+                                       0.f, 1.f, 1.f, tb.loss);
+  k_sum<<<1, 256>>>(tb.lpart, ntiles, tb.loss + NPARAM);
+  SUR_CUDA(cudaGetLastError(), "loss/gradient launch");
+  SUR_CUDA(cudaMemcpy(grad_host, tb.loss, NPARAM * sizeof(float), cudaMemcpyDeviceToHost), "copy");
+  float lsum = 0.f;
+  SUR_CUDA(cudaMemcpy(&lsum, tb.loss + NPARAM, sizeof(float), cudaMemcpyDeviceToHost), "copy");
+  *loss_host = lsum / N;
+  return GL_OK;
+}
+
+gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** out,
+                             float* final_loss) {
+  if (!d || !out) return fail(GL_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (d->n_samples < TILE || d->batch < TILE || d->batch % TILE != 0 || d->epochs < 1)
+    return fail(GL_EINVAL, "need n_samples >= 128, batch a positive multiple of 128, epochs >= 1");
+  if (!(d->q_lo > 0.f && d->q_lo < d->q_hi && d->q_hi <= 1.f && d->gamma_lo > 1.f &&
+        d->gamma_lo < d->gamma_hi && d->gamma_hi < 3.f && d->r_lo > 0.f && d->r_lo < d->r_hi &&
+        d->lr > 0.f && d->lr_min >= 0.f))
+    return fail(GL_EINVAL, "invalid training ranges or learning rate");
+  gl_surrogate* s = nullptr;
+  gl_status r = sur_alloc(&s);
+  if (r != GL_OK) return r;
+  s->q_lo = d->q_lo;
+  s->q_hi = d->q_hi;
+  s->g_lo = d->gamma_lo;
+  s->g_hi = d->gamma_hi;
+  auto bail = [&](gl_status st) {
+    gl_surrogate_destroy(s);
+    return st;
+  };
+  const long long n = d->n_samples;
+  const int ntiles = d->batch / TILE;
+  TrainBuffers tb;
+  if (cudaMalloc(&tb.X, n * sizeof(float4)) != cudaSuccess ||
+      cudaMalloc(&tb.Y, n * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&tb.m, NPARAM * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&tb.v, NPARAM * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&tb.gpart, (size_t)ntiles * NPARAM * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&tb.lpart, ntiles * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&tb.loss, sizeof(float)) != cudaSuccess)
+    return bail(fail(GL_ENOMEM, "training buffers"));
+  cudaMemset(tb.m, 0, NPARAM * sizeof(float));
+  cudaMemset(tb.v, 0, NPARAM * sizeof(float));
+  k_gen_data<<<1184, 256>>>(tb.X, tb.Y, n, d->seed_data, d->q_lo, d->q_hi, d->gamma_lo,
+                            d->gamma_hi, logf(d->r_lo), logf(d->r_hi));
+  k_init_params<<<(NPARAM + 255) / 256, 256>>>(s->params, d->seed_init);
+  if (cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(TrainSmem)) != cudaSuccess)
+    return bail(fail(GL_ECUDA, "training kernel shared-memory limit"));
+  const long long steps_per_epoch = (n + d->batch - 1) / d->batch;
+  const long long total = steps_per_epoch * d->epochs;
+  const float b1 = 0.9f, b2 = 0.999f;
+  double bc1 = 1.0, bc2 = 1.0;
+  // a large odd stride co-prime with n visits the data in a scrambled order
+  long long stride = (long long)(0.6180339887 * n) | 1;
+  while (std::gcd(stride, n) != 1) stride += 2;
+  for (long long it = 0; it < total; ++it) {
+    const double frac = (double)it / (double)total;
+    const float lr = (float)(d->lr_min + 0.5 * (d->lr - d->lr_min) * (1.0 + cos(3.14159265358979323846 * frac)));
+    bc1 *= b1;
+    bc2 *= b2;
+    k_pack<<<(NBF16 + 255) / 256, 256>>>(s->params, s->wb);
+    const long long row0 = (it * (long long)d->batch) % n;
+    k_train<<<ntiles, 256, sizeof(TrainSmem)>>>(s->wb, s->params, tb.X, tb.Y, n, row0, stride,
+                                                1.f / d->batch, tb.gpart, tb.lpart);
+    k_adam<<<(NPARAM + 255) / 256, 256>>>(s->params, tb.m, tb.v, tb.gpart, ntiles, lr, b1, b2,
+                                         1e-8f, (float)(1.0 - bc1), (float)(1.0 - bc2), nullptr);
+    if ((it & 255) == 0) {
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return bail(fail(GL_ECUDA, std::string("training: ") + cudaGetErrorString(e)));
+    }
+  }
+  k_pack<<<(NBF16 + 255) / 256, 256>>>(s->params, s->wb);
+  // final loss over the last batch's tiles
+  k_sum<<<1, 256>>>(tb.lpart, ntiles, tb.loss);
+  float lsum = 0.f;
+  cudaError_t e = cudaMemcpy(&lsum, tb.loss, sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bail(fail(GL_ECUDA, std::string("training: ") + cudaGetErrorString(e)));
+  s->final_loss = lsum / d->batch;
+  if (final_loss) *final_loss = s->final_loss;
+  *out = s;
+  return GL_OK;
+}
+
+gl_status gl_surrogate_save(const gl_surrogate* s, const char* path) {
+  if (!s || !path) return fail(GL_EINVAL, "NULL argument");
+  std::vector<float> p(NPARAM);
+  SUR_CUDA(cudaMemcpy(p.data(), s->params, NPARAM * sizeof(float), cudaMemcpyDeviceToHost), "copy");
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(GL_EINVAL, std::string("cannot open ") + path);
+  const char magic[8] = {'G', 'L', 'S', 'U', 'R', '0', '1', '\0'};
+  const int32_t np = NPARAM;
+  const float dom[4] = {s->q_lo, s->q_hi, s->g_lo, s->g_hi};
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(&np, 4, 1, f) == 1 &&
+            std::fwrite(dom, 4, 4, f) == 4 && std::fwrite(p.data(), 4, NPARAM, f) == (size_t)NPARAM;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(GL_EINVAL, std::string("write failed: ") + path);
+  return GL_OK;
+}
+
+gl_status gl_surrogate_load(const char* path, gl_surrogate** out) {
+  if (!path || !out) return fail(GL_EINVAL, "NULL argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(GL_EINVAL, std::string("cannot open ") + path);
+  char magic[8];
+  int32_t np = 0;
+  float dom[4];
+  std::vector<float> p(NPARAM);
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "GLSUR01", 8) == 0 &&
+            std::fread(&np, 4, 1, f) == 1 && np == NPARAM && std::fread(dom, 4, 4, f) == 4 &&
+            std::fread(p.data(), 4, NPARAM, f) == (size_t)NPARAM;
+  std::fclose(f);
+  if (!ok) return fail(GL_EINVAL, std::string("not a surrogate file: ") + path);
+  gl_status r = gl_surrogate_create(p.data(), out);
+  if (r != GL_OK) return r;
+  (*out)->q_lo = dom[0];
+  (*out)->q_hi = dom[1];
+  (*out)->g_lo = dom[2];
+  (*out)->g_hi = dom[3];
+  return GL_OK;
+}
+
+}  // extern "C"
