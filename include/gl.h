@@ -148,6 +148,37 @@ gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, f
 gl_status gl_logp_grad_host(gl_system* sys, const float* theta_host, int B, float* logp_host,
                             float* grad_host, gl_deflection defl, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Uneven multi-system batches: many systems (different image sizes,
+ * supersampling, component counts), each with its own rows, per call. One
+ * persistent launch per (n_lens_light, n_source) group evaluates all rows of
+ * the group; rows are taken heaviest system first from a device work queue.
+ * ------------------------------------------------------------------------- */
+typedef struct gl_multi gl_multi;
+
+/* Shared-memory policies for the image buffers of a multi-system launch:
+ *   0  all buffers in global scratch (occupancy set by registers alone);
+ *   1  shared memory while two CTAs fit per SM, the rest in global scratch;
+ *   2  shared memory up to one CTA per SM.
+ * Which is fastest depends on the size mix; the package's autotuner times them. */
+enum { GL_MULTI_SMEM_GLOBAL = 0, GL_MULTI_SMEM_TWO_CTAS = 1, GL_MULTI_SMEM_ONE_CTA = 2 };
+
+/* Plans a batch over n_sys systems (borrowed: they must outlive the plan and
+ * live on the current device) with rows_per_sys[k] rows each. Allocates the
+ * work lists and the per-CTA scratch. */
+gl_status gl_multi_create(gl_system* const* systems, int n_sys, const int* rows_per_sys,
+                          int smem_policy, gl_multi** out);
+
+/* log p and gradient of every row of every system: theta[k] device
+ * [rows_k][P_k], logp[k] device [rows_k], grad[k] device [rows_k][P_k] (host
+ * arrays of device pointers). Results equal gl_logp_grad per system with the
+ * same deflection. The work lists are re-uploaded when a pointer changes. */
+gl_status gl_multi_logp_grad(gl_multi* multi, const float* const* theta, float* const* logp,
+                             float* const* grad, gl_deflection defl, void* stream);
+
+/* Frees a plan (waits for the device). NULL is accepted. */
+gl_status gl_multi_destroy(gl_multi* multi);
+
 /* n_steps HMC leapfrog steps for B chains, in place (the integrator of the
  * pipeline's HMC stage, Sec. 3; Sec. 3.1 runs chains independently). Per step,
  * with diagonal inverse mass M^-1 and step size eps:

@@ -79,7 +79,12 @@ SIGNATURES = {
     "gl_surrogate_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_VP)]),
     "gl_surrogate_destroy": (None, [_VP]),
     "gl_system_set_surrogate": (ctypes.c_int, [_VP, _VP]),
+    "gl_multi_create": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "gl_multi_logp_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
+    "gl_multi_destroy": (ctypes.c_int, [_VP]),
 }
+
+GL_MULTI_SMEM_GLOBAL, GL_MULTI_SMEM_TWO_CTAS, GL_MULTI_SMEM_ONE_CTA = 0, 1, 2
 
 
 class gl_surrogate_train_desc(ctypes.Structure):
@@ -258,6 +263,48 @@ class System:
         _check(self._lib.gl_model_image(self._h, _ptr(theta), B, _ptr(out), defl,
                                         _stream_ptr(stream)))
         return out
+
+
+class Multi:
+    """An uneven multi-system batch plan (gl_multi_create / gl_multi_logp_grad)."""
+
+    def __init__(self, systems, rows, smem_policy: int = GL_MULTI_SMEM_TWO_CTAS):
+        self._lib = load()
+        self.systems = list(systems)
+        self.rows = [int(r) for r in rows]
+        hs = (_VP * len(self.systems))(*[s.handle for s in self.systems])
+        rs = (ctypes.c_int * len(self.rows))(*self.rows)
+        h = _VP()
+        _check(self._lib.gl_multi_create(hs, len(self.systems), rs, int(smem_policy),
+                                         ctypes.byref(h)))
+        self._h = h
+        self.smem_policy = smem_policy
+
+    def logp_grad(self, thetas, logps=None, grads=None, defl: int = GL_DEFL_SERIES, stream=None):
+        """thetas: list of CUDA float32 [rows_k, P_k]; returns lists of logp, grad."""
+        torch = _torch()
+        n = len(self.systems)
+        thetas = [t.contiguous() for t in thetas]
+        if logps is None:
+            logps = [torch.empty(t.shape[0], device=t.device, dtype=torch.float32) for t in thetas]
+        if grads is None:
+            grads = [torch.empty_like(t) for t in thetas]
+        tp = (_VP * n)(*[_ptr(t) for t in thetas])
+        lp = (_VP * n)(*[_ptr(t) for t in logps])
+        gp = (_VP * n)(*[_ptr(t) for t in grads])
+        _check(self._lib.gl_multi_logp_grad(self._h, tp, lp, gp, int(defl), _stream_ptr(stream)))
+        return logps, grads
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gl_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Surrogate:

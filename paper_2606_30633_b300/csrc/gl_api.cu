@@ -11,40 +11,12 @@
 
 #include "../../include/gl.h"
 #include "gl_internal.cuh"
+#include "gl_system.h"
 
 using gl::PriorDev;
 using gl::SysParams;
 
-struct gl_system {
-  int device = 0;
-  SysParams sp;
-  float* d_data = nullptr;
-  float* d_w = nullptr;
-  PriorDev* d_prior = nullptr;
-  float* d_emax = nullptr;
-  // buffer plans (dynamic shared memory bytes and placement) per kernel kind
-  size_t fwd_smem = 0, grad_smem = 0;
-  int fwd_A = 1, grad_A = 1, grad_B = 1;
-  size_t fwd_slot = 0, grad_slot = 0;  // global scratch floats per CTA
-  float* scratch = nullptr;
-  size_t scratch_floats = 0;
-  // host-buffer entry point staging
-  float *h_stage = nullptr, *d_stage = nullptr;
-  size_t stage_floats = 0;
-  const gl_surrogate* sur = nullptr;
-  float4* d_table = nullptr;  // surrogate tables, [rows][TABLE_M][2]
-  size_t table_rows = 0;
-  // leapfrog block: one instantiated CUDA graph, re-captured when its
-  // arguments (or the scratch it points into) change
-  cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t lf_exec = nullptr;
-  struct LfKey {
-    float *theta, *p, *logp, *grad, *scratch;
-    const float* inv_mass;
-    float eps;
-    int n_steps, B;
-  } lf_key;
-};
+
 
 namespace {
 
@@ -96,9 +68,13 @@ __global__ void k_weights(const float* sigma, float* w, int n) {
 
 size_t align4(size_t n) { return (n + 3) & ~(size_t)3; }
 
-// Chooses buffer placement for a kernel needing nbufs padded images.
-// Shared memory when the CTA still fits twice per SM, else global scratch.
-void plan(size_t buf_floats, int nbufs, size_t smem_budget, size_t* dyn, int* a_smem, int* b_smem,
+}  // namespace
+
+namespace gl {
+// Chooses buffer placement for a kernel needing nbufs padded images: all in
+// shared memory when they fit the budget, else the first one when it fits,
+// else global scratch.
+void plan_buffers(size_t buf_floats, int nbufs, size_t smem_budget, size_t* dyn, int* a_smem, int* b_smem,
           size_t* slot) {
   const size_t bb = buf_floats * sizeof(float);
   *a_smem = 0;
@@ -117,6 +93,9 @@ void plan(size_t buf_floats, int nbufs, size_t smem_budget, size_t* dyn, int* a_
     *slot = nbufs * buf_floats;
   }
 }
+}  // namespace gl
+
+namespace {
 
 gl_status ensure_scratch(gl_system* s, size_t floats) {
   if (floats <= s->scratch_floats) return GL_OK;
@@ -327,10 +306,16 @@ gl_status gl_system_create(const gl_system_desc* d, gl_system** out) {
   if (budget + 4096 > (size_t)smem_blk) budget = (size_t)smem_blk > 4096 ? smem_blk - 4096 : 0;
   const size_t nbuf = align4((size_t)sp.Hp * sp.Wp);
   int bdummy = 0;
-  plan(nbuf, 1, budget, &s->fwd_smem, &s->fwd_A, &bdummy, &s->fwd_slot);
-  plan(nbuf, 2, budget, &s->grad_smem, &s->grad_A, &s->grad_B, &s->grad_slot);
-  e = gl::set_smem_limits_fwd(s->fwd_smem > 48 * 1024 ? s->fwd_smem : 48 * 1024);
-  if (e == cudaSuccess) e = gl::set_smem_limits_grad(s->grad_smem > 48 * 1024 ? s->grad_smem : 48 * 1024);
+  gl::plan_buffers(nbuf, 1, budget, &s->fwd_smem, &s->fwd_A, &bdummy, &s->fwd_slot);
+  gl::plan_buffers(nbuf, 2, budget, &s->grad_smem, &s->grad_A, &s->grad_B, &s->grad_slot);
+  // the attribute is per kernel and process-wide: always the device maximum,
+  // so that no system or plan lowers another's limit (it does not change
+  // occupancy, which follows each launch's own size)
+  // (the limit counts dynamic memory only: leave room for the kernels' static
+  // shared memory, at most 8 KB)
+  const size_t dyn_max = (size_t)smem_blk > 8192 ? (size_t)smem_blk - 8192 : 0;
+  e = gl::set_smem_limits_fwd(dyn_max);
+  if (e == cudaSuccess) e = gl::set_smem_limits_grad(dyn_max);
   if (e != cudaSuccess) return bail(cuda_fail(e, "kernel shared-memory limit"));
   g_last_error.clear();
   *out = s;

@@ -1,0 +1,7 @@
+// k_grad / k_grad_multi instantiations with 0 lens-light component(s),
+// table (surrogate or exact-table) deflection.
+#include "gl_grad_impl.cuh"
+
+namespace gl {
+GL_GRAD_INST_S(, 0, true)
+}  // namespace gl

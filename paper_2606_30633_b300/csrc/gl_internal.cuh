@@ -52,6 +52,15 @@ struct SysParams {
   float kcorr[MAX_K * MAX_K];  // PSF: adjoint = correlate(g_pad, kcorr)
 };
 
+// One work item (row) of an uneven multi-system batch.
+struct MultiItem {
+  int sys;              // index into the system table
+  const float* theta;   // the row
+  float* logp;
+  float* grad;
+  const float4* table;  // the row's surrogate/exact table (or null)
+};
+
 // Launch entry points (defined in the kernel translation units).
 // img != nullptr: write the model image instead of reducing chi^2.
 // sp.table != nullptr selects the surrogate instantiations.
@@ -62,6 +71,10 @@ cudaError_t launch_grad(const SysParams& sp, const float* theta, int B, float* l
 cudaError_t launch_leapfrog_block(const SysParams& sp, size_t dyn, float* theta, float* p,
                                   float* logp, float* grad, const float* inv_mass, float eps,
                                   int n_steps, int B, cudaStream_t st);
+// Persistent forward + adjoint over multi-system work items (MultiItem array).
+cudaError_t launch_grad_multi(int nL, int nS, bool surr, const SysParams* systems,
+                              const void* items, int n_items, int* counter, int grid, size_t dyn,
+                              cudaStream_t st);
 // Surrogate tables [B][TABLE_M][2] for the rows of theta (gl_surrogate.cu).
 cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B, float4* table,
                          cudaStream_t st);

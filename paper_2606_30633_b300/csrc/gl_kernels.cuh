@@ -313,9 +313,9 @@ struct SmemStatic {
 };
 
 __device__ __forceinline__ void buffers(const SysParams& sp, float* dsm, bool two, float*& A,
-                                        float*& Bf) {
+                                        float*& Bf, int slot_index) {
   const size_t nbuf = ((size_t)sp.Hp * sp.Wp + 3) & ~(size_t)3;
-  float* slot = sp.scratch ? sp.scratch + (size_t)blockIdx.x * sp.slot_floats : nullptr;
+  float* slot = sp.scratch ? sp.scratch + (size_t)slot_index * sp.slot_floats : nullptr;
   size_t soff = 0, goff = 0;
   if (sp.bufA_smem) { A = dsm; soff += nbuf; } else { A = slot; goff += nbuf; }
   Bf = nullptr;
@@ -391,9 +391,8 @@ __device__ __forceinline__ void adjoint_pixels(const SysParams& sp, const Sample
 
 // The row's surrogate table into shared memory (when the row uses it).
 template <bool SURR>
-__device__ __forceinline__ void load_table(const SysParams& sp, const SampleC& sc, float4* tab) {
+__device__ __forceinline__ void load_table(const float4* src, const SampleC& sc, float4* tab) {
   if (SURR && sc.use_table) {
-    const float4* src = sp.table + (size_t)blockIdx.x * 2 * TABLE_M;
     for (int k = threadIdx.x; k < 2 * TABLE_M; k += THREADS) tab[k] = src[k];
   }
   __syncthreads();
@@ -412,7 +411,7 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
   if (b >= B) return;
   const bool want_img = img != nullptr;
   float *A, *Bf;
-  buffers(sp, dsm, false, A, Bf);
+  buffers(sp, dsm, false, A, Bf, blockIdx.x);
   if (threadIdx.x < 32)
     stage_warp(sp, theta + (size_t)b * sp.P, sc, st.fin, !want_img);
   else
@@ -427,7 +426,7 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
     }
     return;
   }
-  load_table<SURR>(sp, sc, tab);
+  load_table<SURR>(sp.table + (size_t)blockIdx.x * 2 * TABLE_M, sc, tab);
   const EplC e = sc.epl;
   LightC L[NL + NS];
 #pragma unroll
@@ -456,21 +455,20 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
   if (threadIdx.x == 0) logp[b] = (float)(-0.5 * chi2 + sc.logprior);
 }
 
-// Forward + adjoint: log p and d log p / d theta per row.
+// Forward + adjoint of one row (all threads of the CTA): log p and
+// d log p / d theta of theta row th into *logp_out and grad_out[0..P).
+// slot_index picks the CTA's global-scratch slot, table_row the row's table.
+// Ends with a block barrier, so a persistent CTA can start its next row.
 template <int NL, int NS, bool SURR>
-__global__ void __launch_bounds__(THREADS, 2)
-k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, int B,
-       float* __restrict__ logp, float* __restrict__ grad) {
+__device__ __forceinline__ void grad_row(const SysParams& sp, const float* __restrict__ th,
+                                         float* __restrict__ logp_out,
+                                         float* __restrict__ grad_out,
+                                         const float4* __restrict__ table_row, int slot_index,
+                                         float* dsm, SmemStatic& st, float4* tab) {
   constexpr int P = 8 + 7 * (NL + NS);
-  extern __shared__ __align__(16) float dsm[];
-  __shared__ SmemStatic st;
-  __shared__ float4 tab[SURR ? 2 * TABLE_M : 1];
   SampleC& sc = st.sc;
-  const int b = blockIdx.x;
-  if (b >= B) return;
-  const float* th = theta + (size_t)b * P;
   float *A, *Bf;
-  buffers(sp, dsm, true, A, Bf);
+  buffers(sp, dsm, true, A, Bf, slot_index);
   if (threadIdx.x < 32) {
     stage_warp(sp, th, sc, st.fin, true);
   } else {
@@ -482,11 +480,12 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
   if (sc.status != 0) {
     const float lv = sc.status == 2 ? __int_as_float(0x7fc00000) : -__int_as_float(0x7f800000);
     const float gv = sc.status == 2 ? __int_as_float(0x7fc00000) : 0.f;
-    if (threadIdx.x == 0) logp[b] = lv;
-    if (threadIdx.x < P) grad[(size_t)b * P + threadIdx.x] = gv;
+    if (threadIdx.x == 0) *logp_out = lv;
+    if (threadIdx.x < P) grad_out[threadIdx.x] = gv;
+    __syncthreads();
     return;
   }
-  load_table<SURR>(sp, sc, tab);
+  load_table<SURR>(table_row, sc, tab);
   const bool use_tab = SURR && sc.use_table;
   const EplC e = sc.epl;
   LightC L[NL + NS];
@@ -538,15 +537,54 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
     if (c == 0) {
       epl_finish(st.fin[0], st.gsum, g, use_tab);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) grad[(size_t)b * P + k] = g[k] + sc.dprior[k];
+      for (int k = 0; k < 8; ++k) grad_out[k] = g[k] + sc.dprior[k];
     } else {
       const int o = 8 + 7 * (c - 1);
       sersic_finish(st.fin[c], st.gsum + o, g);
 #pragma unroll
-      for (int k = 0; k < 7; ++k) grad[(size_t)b * P + o + k] = g[k] + sc.dprior[o + k];
+      for (int k = 0; k < 7; ++k) grad_out[o + k] = g[k] + sc.dprior[o + k];
     }
   }
-  if (threadIdx.x == 0) logp[b] = (float)(-0.5 * chi2 + sc.logprior);
+  if (threadIdx.x == 0) *logp_out = (float)(-0.5 * chi2 + sc.logprior);
+  __syncthreads();
+}
+
+// Forward + adjoint: log p and d log p / d theta per row (one CTA per row).
+template <int NL, int NS, bool SURR>
+__global__ void __launch_bounds__(THREADS, 2)
+k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, int B,
+       float* __restrict__ logp, float* __restrict__ grad) {
+  constexpr int P = 8 + 7 * (NL + NS);
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ SmemStatic st;
+  __shared__ float4 tab[SURR ? 2 * TABLE_M : 1];
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  grad_row<NL, NS, SURR>(sp, theta + (size_t)b * P, logp + b, grad + (size_t)b * P,
+                         SURR ? sp.table + (size_t)b * 2 * TABLE_M : nullptr, b, dsm, st, tab);
+}
+
+// Persistent forward + adjoint over uneven multi-system batches: each CTA
+// takes items from a global counter, heaviest first (the host sorts them by
+// cost), and uses its own global-scratch slot. counter must be 0 at launch.
+template <int NL, int NS, bool SURR>
+__global__ void __launch_bounds__(THREADS, 1)
+k_grad_multi(const SysParams* __restrict__ systems, const MultiItem* __restrict__ items,
+             int n_items, int* __restrict__ counter) {
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ SmemStatic st;
+  __shared__ float4 tab[SURR ? 2 * TABLE_M : 1];
+  __shared__ int next;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = next;
+    __syncthreads();
+    if (it >= n_items) break;
+    const MultiItem m = items[it];
+    grad_row<NL, NS, SURR>(systems[m.sys], m.theta, m.logp, m.grad, m.table, blockIdx.x, dsm, st,
+                           tab);
+  }
 }
 
 }  // namespace gl
