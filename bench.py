@@ -488,6 +488,95 @@ def run_leapfrog(args) -> dict | None:
     return out
 
 
+def run_uneven(args) -> dict | None:
+    """Uneven-batch persistent run: 100 synthetic systems (sides 40-200 px,
+    s = 2-5, 1-3 source components, 0.262"/px, 11x11 Moffat), 256 rows each,
+    all evaluated per step by gl_multi_logp_grad (one persistent launch per
+    component-count group); the shared-memory policy is picked by the
+    autotuner; the exact series and the learned surrogate side by side."""
+    import torch
+    import paper_2606_30633_b300 as gl
+    from paper_2606_30633_b300 import autotune
+    from paper_2606_30633_b300 import build as glbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    glbuild.build()
+    dev = torch.device("cuda", local)
+    Ws = synth.uneven_systems()
+    systems, thetas, rows = [], [], []
+    for W in Ws:
+        spec = W.prior()
+        blank = gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
+                          np.ones((W.ny, W.nx)), W.psf, W.n_lens_light, W.n_source, spec)
+        m = blank.model_image(torch.tensor(W.truth()[None], dtype=torch.float32, device=dev))[0]
+        m = m.double().cpu().numpy()
+        blank.close()
+        d, sig = synth.noisy_data(m, W.noise())
+        systems.append(gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, d, sig, W.psf,
+                                 W.n_lens_light, W.n_source, spec))
+        thetas.append(torch.tensor(W.samples().astype(np.float32), device=dev))
+        rows.append(W.batch)
+    n_rows = sum(rows)
+    plan, tune_ms = autotune.tune_multi(systems, rows, thetas, reps=2)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    logps, grads = plan.logp_grad(thetas)
+    with ClockSampler(local) as clk:
+        ms = timed_steps(lambda: plan.logp_grad(thetas, logps, grads, stream=stream), args.steps,
+                         args.warmup, stream, flush)
+    sur = gl.Surrogate.train(n_samples=10_000_000, epochs=20, batch=16384, lr=2e-3, lr_min=1e-5,
+                             seed_data=401, seed_init=402)
+    for s_ in systems:
+        s_.set_surrogate(sur)
+    lps_s = [t.clone() for t in logps]
+    ms_sur = timed_steps(lambda: plan.logp_grad(thetas, logps, grads, defl=gl.GL_DEFL_SURROGATE,
+                                                stream=stream), args.steps, args.warmup, stream,
+                         flush)
+    dl = torch.cat([(a - b).abs() for a, b in zip(logps, lps_s)]).cpu().numpy()
+    t_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = world * n_rows * args.steps / (t_ms / 1e3)
+    ops = 0.0
+    for W, th in zip(Ws, thetas):
+        o, _ = algorithmic_ops(th.double().cpu().numpy(), W.ny, W.nx, W.supersample,
+                               W.psf.shape[0], W.n_lens_light, W.n_source)
+        ops += o
+    peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2.032e9 / 1e12
+    achieved = ops / (statistics.mean(ms) / 1e3) / 1e12
+    out = None
+    if rank == 0:
+        out = {
+            "metric": "logp+grad evals/s (100 uneven systems: 40-200 px, 2-5x SS, 1-3 sources, "
+                      "256 rows each) on 1 B300",
+            "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded priors, library-rendered truths, seeded noise)",
+            "config": {"workload": "uneven-100-systems", "systems": len(Ws), "rows": n_rows,
+                       "smem_policy": {v: k for k, v in autotune.POLICIES.items()}[plan.smem_policy],
+                       "autotune_ms": tune_ms,
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "learned": {"value": world * n_rows / (statistics.mean(ms_sur) / 1e3), "unit": "evals/s",
+                        "dlogp_abs_median": float(np.median(dl)),
+                        "dlogp_abs_p90": float(np.quantile(dl, 0.9))},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None},
+            "e2e": None,
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk.summary(),
+        }
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -497,7 +586,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=None,
                     help="rows per step (default: the workload's); for profiling runs")
-    ap.add_argument("--workload", choices=["ground100", "space200-leapfrog"],
+    ap.add_argument("--workload", choices=["ground100", "space200-leapfrog", "uneven"],
                     default="ground100")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -506,6 +595,8 @@ def main():
         res = run_reference(args)
     elif args.workload == "space200-leapfrog":
         res = run_leapfrog(args)
+    elif args.workload == "uneven":
+        res = run_uneven(args)
     else:
         res = run_ours(args)
     if res is not None:
