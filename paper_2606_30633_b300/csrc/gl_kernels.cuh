@@ -13,7 +13,7 @@
 // when they fit, else a per-CTA slot of global scratch).
 #pragma once
 
-#include "gl_model.cuh"
+#include "gl_pair.cuh"
 
 namespace gl {
 
@@ -304,13 +304,24 @@ __device__ __forceinline__ void subpixel_adjoint(const SampleC& sc, const EplC& 
 }
 
 // ---------------------------------------------------------------- kernels ----
+struct AdjSums {
+  float redP[NWARPS][MAX_P];
+  double gsum[MAX_P];
+};
+// Static shared memory of the kernels (the host reserves 4 KB for it, and
+// 8 KB with the surrogate table).
 struct SmemStatic {
   SampleC sc;
   FinishC fin[MAX_COMP + 1];
   double red[NWARPS];
-  float redP[NWARPS][MAX_P];
-  double gsum[MAX_P];
+  union {
+    PairC pc;     // phase 1 (exact series)
+    AdjSums adj;  // phase 4 and the chain rule
+  } u;
 };
+static_assert(sizeof(SmemStatic) <= 4096, "static shared memory over its reservation");
+static_assert(sizeof(SmemStatic) + 2 * TABLE_M * sizeof(float4) <= 8192,
+              "static shared memory (with the table) over its reservation");
 
 __device__ __forceinline__ void buffers(const SysParams& sp, float* dsm, bool two, float*& A,
                                         float*& Bf, int slot_index) {
@@ -342,6 +353,73 @@ __device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& s
       }
     }
     A[(size_t)(pw.i + sp.cy) * sp.Wp + pw.j + sp.cx] = acc * sp.scale;
+  }
+}
+
+// Phase 1 on the exact series in the lanes of float2 pairs: four pixels per
+// thread (p, p + T, p + 2T, p + 3T; two interleaved pairs) while all four
+// exist, then pairs, where a missing second pixel repeats the first and is not
+// written. Needs pc filled (fill_pair_consts and a barrier).
+template <int NL, int NS>
+__device__ __forceinline__ void bin_pixels2(const SysParams& sp, const PairC& pc, int nq,
+                                            float* A) {
+  const int s = sp.s, npix = sp.ny * sp.nx, Wp = sp.Wp, cy = sp.cy, cx = sp.cx;
+  const float2 D = f2(sp.D), scale = f2(sp.scale);
+  PixelWalk w0(sp.nx);
+  int p = threadIdx.x;
+  for (; p + 3 * THREADS < npix; p += 4 * THREADS) {
+    PixelWalk w1 = w0;
+    w1.next();
+    PixelWalk w2 = w1;
+    w2.next();
+    PixelWalk w3 = w2;
+    w3.next();
+    const float2 xj0 = make_float2((float)w0.j + sp.xg0, (float)w1.j + sp.xg0);
+    const float2 yi0 = make_float2((float)w0.i + sp.yg0, (float)w1.i + sp.yg0);
+    const float2 xj1 = make_float2((float)w2.j + sp.xg0, (float)w3.j + sp.xg0);
+    const float2 yi1 = make_float2((float)w2.i + sp.yg0, (float)w3.i + sp.yg0);
+    float2 acc0 = f2(0.f), acc1 = f2(0.f);
+    for (int k = 0; k < s; ++k) {
+      const float2 ok = f2(sp.off[k]);
+      const float2 y0 = mul2(add2(yi0, ok), D), y1 = mul2(add2(yi1, ok), D);
+      for (int l = 0; l < s; ++l) {
+        const float2 ol = f2(sp.off[l]);
+        const float2 x0 = mul2(add2(xj0, ol), D), x1 = mul2(add2(xj1, ol), D);
+        float2 sb0, sb1;
+        surface_brightness2x2<NL, NS>(reload(pc), nq, x0, y0, x1, y1, sb0, sb1);
+        acc0 = add2(acc0, sb0);
+        acc1 = add2(acc1, sb1);
+      }
+    }
+    acc0 = mul2(acc0, scale);
+    acc1 = mul2(acc1, scale);
+    A[(size_t)(w0.i + cy) * Wp + w0.j + cx] = acc0.x;
+    A[(size_t)(w1.i + cy) * Wp + w1.j + cx] = acc0.y;
+    A[(size_t)(w2.i + cy) * Wp + w2.j + cx] = acc1.x;
+    A[(size_t)(w3.i + cy) * Wp + w3.j + cx] = acc1.y;
+    w0 = w3;
+    w0.next();
+  }
+  for (; p < npix; p += 2 * THREADS) {
+    PixelWalk w1 = w0;
+    w1.next();
+    const bool v1 = p + THREADS < npix;
+    const int i1 = v1 ? w1.i : w0.i, j1 = v1 ? w1.j : w0.j;
+    const float2 xj = make_float2((float)w0.j + sp.xg0, (float)j1 + sp.xg0);
+    const float2 yi = make_float2((float)w0.i + sp.yg0, (float)i1 + sp.yg0);
+    float2 acc = f2(0.f);
+    for (int k = 0; k < s; ++k) {
+      const float2 y = mul2(add2(yi, f2(sp.off[k])), D);
+      for (int l = 0; l < s; ++l) {
+        const float2 x = mul2(add2(xj, f2(sp.off[l])), D);
+        acc = add2(acc, surface_brightness2<NL, NS>(reload(pc), nq, x, y));
+      }
+    }
+    acc = mul2(acc, scale);
+    A[(size_t)(w0.i + cy) * Wp + w0.j + cx] = acc.x;
+    if (v1) A[(size_t)(w1.i + cy) * Wp + w1.j + cx] = acc.y;
+    w0 = w1;
+    w0.next();
   }
 }
 
@@ -427,14 +505,17 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
     return;
   }
   load_table<SURR>(sp.table + (size_t)blockIdx.x * 2 * TABLE_M, sc, tab);
-  const EplC e = sc.epl;
-  LightC L[NL + NS];
+  if (SURR && sc.use_table) {
+    const EplC e = sc.epl;
+    LightC L[NL + NS];
 #pragma unroll
-  for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
-  if (SURR && sc.use_table)
+    for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
     bin_pixels<NL, NS, true>(sp, sc, e, L, tab, A);
-  else
-    bin_pixels<NL, NS, false>(sp, sc, e, L, tab, A);
+  } else {
+    fill_pair_consts(sc, NL + NS, st.u.pc);
+    __syncthreads();
+    bin_pixels2<NL, NS>(sp, st.u.pc, sc.nq, A);
+  }
   __syncthreads();
   float csum = 0.f, ccomp = 0.f;
   float* out = want_img ? img + (size_t)b * npix : nullptr;
@@ -475,7 +556,6 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
     zero_halo(sp, A, 32);
     zero_halo(sp, Bf, 32);
   }
-  for (int k = threadIdx.x; k < NWARPS * MAX_P; k += THREADS) (&st.redP[0][0])[k] = 0.f;
   __syncthreads();
   if (sc.status != 0) {
     const float lv = sc.status == 2 ? __int_as_float(0x7fc00000) : -__int_as_float(0x7f800000);
@@ -487,17 +567,22 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
   }
   load_table<SURR>(table_row, sc, tab);
   const bool use_tab = SURR && sc.use_table;
-  const EplC e = sc.epl;
-  LightC L[NL + NS];
-#pragma unroll
-  for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
   const int Wp = sp.Wp, cy = sp.cy, cx = sp.cx, nx = sp.nx;
   // phase 1
-  if (use_tab)
+  if (use_tab) {
+    const EplC e = sc.epl;
+    LightC L[NL + NS];
+#pragma unroll
+    for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
     bin_pixels<NL, NS, true>(sp, sc, e, L, tab, A);
-  else
-    bin_pixels<NL, NS, false>(sp, sc, e, L, tab, A);
+  } else {
+    fill_pair_consts(sc, NL + NS, st.u.pc);
+    __syncthreads();
+    bin_pixels2<NL, NS>(sp, st.u.pc, sc.nq, A);
+  }
   __syncthreads();
+  // (the per-warp adjoint sums share memory with the phase-1 constants)
+  for (int k = threadIdx.x; k < NWARPS * MAX_P; k += THREADS) (&st.u.adj.redP[0][0])[k] = 0.f;
   // phase 2
   float csum = 0.f, ccomp = 0.f;
   correlate<true>(sp, A, [&](int i, int j, float m) {
@@ -518,16 +603,20 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
     A[(size_t)(i + cy) * Wp + j + cx] = g * scale;
   });
   __syncthreads();
-  // phase 4
+  // phase 4 (per-sample constants in registers from here on)
+  const EplC e = sc.epl;
+  LightC L[NL + NS];
+#pragma unroll
+  for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
   if (use_tab)
-    adjoint_pixels<NL, NS, true>(sp, sc, e, L, tab, A, st.redP);
+    adjoint_pixels<NL, NS, true>(sp, sc, e, L, tab, A, st.u.adj.redP);
   else
-    adjoint_pixels<NL, NS, false>(sp, sc, e, L, tab, A, st.redP);
+    adjoint_pixels<NL, NS, false>(sp, sc, e, L, tab, A, st.u.adj.redP);
   __syncthreads();
   if (threadIdx.x < P) {
     double v = 0.0;
-    for (int w = 0; w < NWARPS; ++w) v += (double)st.redP[w][threadIdx.x];
-    st.gsum[threadIdx.x] = v;
+    for (int w = 0; w < NWARPS; ++w) v += (double)st.u.adj.redP[w][threadIdx.x];
+    st.u.adj.gsum[threadIdx.x] = v;
   }
   __syncthreads();
   // chain rule to the parameters, one lane per component
@@ -535,12 +624,12 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
     const int c = threadIdx.x;
     float g[8];
     if (c == 0) {
-      epl_finish(st.fin[0], st.gsum, g, use_tab);
+      epl_finish(st.fin[0], st.u.adj.gsum, g, use_tab);
 #pragma unroll
       for (int k = 0; k < 8; ++k) grad_out[k] = g[k] + sc.dprior[k];
     } else {
       const int o = 8 + 7 * (c - 1);
-      sersic_finish(st.fin[c], st.gsum + o, g);
+      sersic_finish(st.fin[c], st.u.adj.gsum + o, g);
 #pragma unroll
       for (int k = 0; k < 7; ++k) grad_out[o + k] = g[k] + sc.dprior[o + k];
     }
