@@ -301,7 +301,7 @@ gl_status gl_system_create(const gl_system_desc* d, gl_system** out) {
   int dev = s->device, smem_sm = 0, smem_blk = 0;
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t static_smem = 4096 + 1024;  // static shared + per-CTA reservation
+  const size_t static_smem = gl::static_smem_bytes() + 1024;  // static + per-CTA reservation
   size_t budget = (size_t)smem_sm / 2 > static_smem ? (size_t)smem_sm / 2 - static_smem : 0;
   if (budget + 4096 > (size_t)smem_blk) budget = (size_t)smem_blk > 4096 ? smem_blk - 4096 : 0;
   const size_t nbuf = align4((size_t)sp.Hp * sp.Wp);
@@ -312,8 +312,9 @@ gl_status gl_system_create(const gl_system_desc* d, gl_system** out) {
   // so that no system or plan lowers another's limit (it does not change
   // occupancy, which follows each launch's own size)
   // (the limit counts dynamic memory only: leave room for the kernels' static
-  // shared memory, at most 8 KB)
-  const size_t dyn_max = (size_t)smem_blk > 8192 ? (size_t)smem_blk - 8192 : 0;
+  // shared memory)
+  const size_t stat = gl::static_smem_bytes();
+  const size_t dyn_max = (size_t)smem_blk > stat ? (size_t)smem_blk - stat : 0;
   e = gl::set_smem_limits_fwd(dyn_max);
   if (e == cudaSuccess) e = gl::set_smem_limits_grad(dyn_max);
   if (e != cudaSuccess) return bail(cuda_fail(e, "kernel shared-memory limit"));

@@ -21,6 +21,11 @@ cudaError_t launch_forward(const SysParams& sp, const float* theta, int B, float
   return cudaErrorInvalidValue;
 }
 
+size_t static_smem_bytes() {
+  // SmemStatic + the table + k_grad_multi's work index, with alignment slack
+  return sizeof(SmemStatic) + 2 * TABLE_M * sizeof(float4) + 256;
+}
+
 cudaError_t set_smem_limits_fwd(size_t bytes) {
   cudaError_t e = cudaSuccess;
 #define GL_SET(a, b) \

@@ -13,7 +13,9 @@
 // when they fit, else a per-CTA slot of global scratch).
 #pragma once
 
-#include "gl_pair.cuh"
+#include <type_traits>
+
+#include "gl_subpixel.cuh"
 
 namespace gl {
 
@@ -128,200 +130,18 @@ __device__ __forceinline__ double block_sum_double(double v, double* red) {
   return s;  // valid on thread 0
 }
 
-// ------------------------------------------------- surrogate table lookup ----
-// Table of row b: TABLE_M nodes uniform in the pseudo-angle
-//   pa = 1 - cos(vphi) / (|cos(vphi)| + sin(vphi)),  vphi folded into [0, pi)
-// (F has period pi in vphi; pa is monotonic, in [0, 2), with
-// d pa / d vphi = 1 / (|cos| + sin)^2), two float4 per node:
-// (F, dF/dpa) and (dF/dq, dF/dt). Cubic Hermite interpolation in pa for F and
-// its derivative, linear for the rest.
-struct TabF {
-  float Fr, Fi, Pr, Pi, Qr, Qi, Tr, Ti;  // F, dF/dvphi, dF/dq, dF/dt
-};
-template <bool DERIV>
-__device__ __forceinline__ TabF table_eval(const float4* __restrict__ tab, float cph, float sph) {
-  const float fl = sph < 0.f ? -1.f : 1.f;  // fold vphi into [0, pi)
-  const float c = cph * fl, sn = sph * fl;
-  const float rd = rcp(fmaxf(fabsf(c) + sn, 1e-20f));  // 0 only at the clamped centre
-  const float pa = fmaf(-c, rd, 1.f);
-  const float u = pa * (0.5f * TABLE_M);
-  const int i0 = min((int)u, TABLE_M - 1);
-  const float t = u - (float)i0;
-  const int i1 = (i0 + 1) & (TABLE_M - 1);
-  const float4 a0 = tab[2 * i0], a1 = tab[2 * i1];
-  const float h = 2.f / TABLE_M;
-  const float t2 = t * t, omt = 1.f - t;
-  const float h00 = (1.f + 2.f * t) * omt * omt, h10 = t * omt * omt;
-  const float h01 = t2 * (3.f - 2.f * t), h11 = t2 * (t - 1.f);
-  TabF o;
-  o.Fr = h00 * a0.x + h01 * a1.x + h * (h10 * a0.z + h11 * a1.z);
-  o.Fi = h00 * a0.y + h01 * a1.y + h * (h10 * a0.w + h11 * a1.w);
-  if (DERIV) {
-    const float d00 = 6.f * (t2 - t) / h, d10 = 3.f * t2 - 4.f * t + 1.f, d11 = 3.f * t2 - 2.f * t;
-    const float k = rd * rd;  // d pa / d vphi
-    o.Pr = k * (d00 * (a0.x - a1.x) + d10 * a0.z + d11 * a1.z);
-    o.Pi = k * (d00 * (a0.y - a1.y) + d10 * a0.w + d11 * a1.w);
-    const float4 b0 = tab[2 * i0 + 1], b1 = tab[2 * i1 + 1];
-    o.Qr = omt * b0.x + t * b1.x;
-    o.Qi = omt * b0.y + t * b1.y;
-    o.Tr = omt * b0.z + t * b1.z;
-    o.Ti = omt * b0.w + t * b1.w;
-  }
-  return o;
-}
-
-// ------------------------------------------------------- sub-pixel work ----
-template <int NL, int NS, bool TAB>
-__device__ __forceinline__ float surface_brightness(const SampleC& sc, const EplC& e,
-                                                    const LightC* L, const float4* tab, float x,
-                                                    float y) {
-  float ax, ay;
-  if (TAB) {
-    const float dx = x - e.xc, dy = y - e.yc;
-    const float xp = fmaf(e.cs, dx, e.sn * dy);
-    const float yp = fmaf(e.cs, dy, -e.sn * dx);
-    const float R2 = fmaxf(fmaf(e.q2 * xp, xp, yp * yp), R_MIN2);
-    const float ir = rsq(R2);
-    const float cph = e.q * xp * ir, sph = yp * ir;
-    const TabF F = table_eval<false>(tab, cph, sph);
-    const float A = e.CA * ex2(e.ht * lg2(R2));
-    const float aLr = A * fmaf(cph, F.Fr, -sph * F.Fi);
-    const float aLi = A * fmaf(cph, F.Fi, sph * F.Fr);
-    ax = fmaf(e.cs, aLr, -e.sn * aLi);
-    ay = fmaf(e.sn, aLr, e.cs * aLi);
-  } else {
-    epl_alpha(e, sc.cE, sc.nq, x, y, ax, ay);
-  }
-  const float bx = x - ax - fmaf(sc.g1, x, sc.g2 * y);
-  const float by = y - ay - fmaf(sc.g2, x, -sc.g1 * y);
-  float sb = 0.f;
-#pragma unroll
-  for (int c = 0; c < NL; ++c) sb += sersic_fwd(L[c], x, y);
-#pragma unroll
-  for (int c = 0; c < NS; ++c) sb += sersic_fwd(L[NL + c], bx, by);
-  return sb;
-}
-
-// Adds u x d SB / d(native parameters) at one sub-pixel to acc (see
-// epl_finish / sersic_finish for the accumulator meanings).
-template <int NL, int NS, bool TAB>
-__device__ __forceinline__ void subpixel_adjoint(const SampleC& sc, const EplC& e, const LightC* L,
-                                                 const float4* tab, float x, float y, float u,
-                                                 float* acc) {
-  const float dx = x - e.xc, dy = y - e.yc;
-  const float xp = fmaf(e.cs, dx, e.sn * dy);
-  const float yp = fmaf(e.cs, dy, -e.sn * dx);
-  const float R2 = fmaxf(fmaf(e.q2 * xp, xp, yp * yp), R_MIN2);
-  const float ir = rsq(R2);
-  const float iR2 = ir * ir;
-  const float cph = e.q * xp * ir, sph = yp * ir;
-  const float wr = fmaf(cph, cph, -sph * sph), wi = 2.f * cph * sph;
-  float Er, Ei, Tr, Ti, Fr, Fi, zr, zi;
-  TabF tf;
-  if (TAB) {
-    tf = table_eval<true>(tab, cph, sph);
-    Fr = tf.Fr;
-    Fi = tf.Fi;
-    Er = Ei = Tr = Ti = zr = zi = 0.f;
-  } else {
-    horner2(sc.cE, sc.cT, sc.nq, wr, wi, Er, Ei, Tr, Ti);
-    zr = -e.f * wr;
-    zi = -e.f * wi;
-    Fr = 1.f + fmaf(zr, Er, -zi * Ei);
-    Fi = fmaf(zr, Ei, zi * Er);
-  }
-  const float Lm = lg2(R2);
-  const float A = e.CA * ex2(e.ht * Lm);
-  const float Qr = A * cph, Qi = A * sph;  // A e^{i vphi}
-  const float aLr = fmaf(Qr, Fr, -Qi * Fi);
-  const float aLi = fmaf(Qr, Fi, Qi * Fr);
-  const float ax = fmaf(e.cs, aLr, -e.sn * aLi);
-  const float ay = fmaf(e.sn, aLr, e.cs * aLi);
-  const float bx = x - ax - fmaf(sc.g1, x, sc.g2 * y);
-  const float by = y - ay - fmaf(sc.g2, x, -sc.g1 * y);
-
-  float gX = 0.f, gY = 0.f;
-#pragma unroll
-  for (int c = 0; c < NL; ++c) sersic_adj<false>(L[c], x, y, u, acc + 8 + 7 * c, gX, gY);
-#pragma unroll
-  for (int c = 0; c < NS; ++c)
-    sersic_adj<true>(L[NL + c], bx, by, u, acc + 8 + 7 * (NL + c), gX, gY);
-  // adjoint of the deflection: v = d logp / d alpha = -u grad_beta S
-  const float vx = -u * gX, vy = -u * gY;
-  acc[6] = fmaf(vx, x, fmaf(-vy, y, acc[6]));
-  acc[7] = fmaf(vx, y, fmaf(vy, x, acc[7]));
-  // lens frame
-  const float vLx = fmaf(e.cs, vx, e.sn * vy);
-  const float vLy = fmaf(e.cs, vy, -e.sn * vx);
-  const float s1 = fmaf(vLx, aLr, vLy * aLi);    // v . alpha
-  const float s1i = fmaf(vLy, aLr, -vLx * aLi);  // v . (i alpha)
-  const float lnR = 0.34657359027997264f * Lm;  // ln(2)/2 log2(R^2)
-  const float dphq = -xp * yp * iR2;
-  if (TAB) {
-    // table derivatives at fixed (the other) arguments: dF/dvphi, dF/dq, dF/dt
-    const float PFr = fmaf(Qr, tf.Pr, -Qi * tf.Pi), PFi = fmaf(Qr, tf.Pi, Qi * tf.Pr);
-    const float QFr = fmaf(Qr, tf.Qr, -Qi * tf.Qi), QFi = fmaf(Qr, tf.Qi, Qi * tf.Qr);
-    const float TFr = fmaf(Qr, tf.Tr, -Qi * tf.Ti), TFi = fmaf(Qr, tf.Ti, Qi * tf.Tr);
-    const float S13 = s1i + fmaf(vLx, PFr, vLy * PFi);
-    const float sQ = fmaf(vLx, QFr, vLy * QFi), sT = fmaf(vLx, TFr, vLy * TFi);
-    acc[0] += s1;
-    acc[1] = fmaf(s1, e.lnb - lnR, acc[1] + sT);
-    acc[2] = fmaf(s1, fmaf(e.omt * e.q * xp * xp, iR2, e.a0), fmaf(S13, dphq, acc[2] + sQ));
-    const float Dx = iR2 * fmaf(e.omt * e.q2 * xp, s1, -e.q * yp * S13);
-    const float Dy = iR2 * fmaf(e.omt * yp, s1, e.q * xp * S13);
-    acc[3] += fmaf(yp, Dx, fmaf(-xp, Dy, s1i));  // d alpha/d phi (lens rotation)
-    acc[4] += Dx;
-    acc[5] += Dy;
-    return;
-  }
-  // dF/dt = z (Tr + i Ti)
-  const float TFr = fmaf(zr, Tr, -zi * Ti), TFi = fmaf(zr, Ti, zi * Tr);
-  const float QTr = fmaf(Qr, TFr, -Qi * TFi), QTi = fmaf(Qr, TFi, Qi * TFr);
-  const float sT = fmaf(vLx, QTr, vLy * QTi);
-  // F'(z) = [t F - (2-t) E] / (2 (1 - z))
-  const float nr = fmaf(e.t, Fr, -e.tmt * Er), ni = fmaf(e.t, Fi, -e.tmt * Ei);
-  const float ozr = 1.f - zr, ozi = -zi;
-  const float inv = 0.5f * rcp(fmaf(ozr, ozr, ozi * ozi));
-  const float Fpr = fmaf(nr, ozr, ni * ozi) * inv;
-  const float Fpi = fmaf(ni, ozr, -nr * ozi) * inv;
-  const float P2r = fmaf(Qr, Fpr, -Qi * Fpi), P2i = fmaf(Qr, Fpi, Qi * Fpr);
-  const float P3r = fmaf(P2r, wr, -P2i * wi), P3i = fmaf(P2r, wi, P2i * wr);
-  const float s3 = fmaf(vLx, P3r, vLy * P3i);
-  const float s3i = fmaf(vLy, P3r, -vLx * P3i);
-  const float S13 = fmaf(-2.f * e.f, s3i, s1i);
-  acc[0] += s1;
-  acc[1] = fmaf(s1, e.lnb - lnR, acc[1] + sT);
-  acc[2] = fmaf(s1, fmaf(e.omt * e.q * xp * xp, iR2, e.a0), fmaf(S13, dphq, fmaf(-e.dfdq, s3, acc[2])));
-  // rotation: d alpha'/d phi = i X with X = (2-t) alpha' - 2 kappa z' =
-  // -2 kappa f (z' w E + conj(z') F), which is O(f); acc[3] = sum kappa v.(iY)
-  const float kap = e.Kk * A * ir;
-  const float zwr = fmaf(xp, wr, -yp * wi), zwi = fmaf(xp, wi, yp * wr);  // z' w
-  const float Yr = fmaf(zwr, Er, fmaf(-zwi, Ei, fmaf(xp, Fr, yp * Fi)));
-  const float Yi = fmaf(zwr, Ei, fmaf(zwi, Er, fmaf(xp, Fi, -yp * Fr)));
-  acc[3] = fmaf(kap, fmaf(vLy, Yr, -vLx * Yi), acc[3]);
-  acc[4] = fmaf(iR2, fmaf(e.omt * e.q2 * xp, s1, -e.q * yp * S13), acc[4]);
-  acc[5] = fmaf(iR2, fmaf(e.omt * yp, s1, e.q * xp * S13), acc[5]);
-}
-
 // ---------------------------------------------------------------- kernels ----
 struct AdjSums {
   float redP[NWARPS][MAX_P];
   double gsum[MAX_P];
 };
-// Static shared memory of the kernels (the host reserves 4 KB for it, and
-// 8 KB with the surrogate table).
+// Static shared memory of the kernels (static_smem_bytes() tells the host).
 struct SmemStatic {
   SampleC sc;
   FinishC fin[MAX_COMP + 1];
   double red[NWARPS];
-  union {
-    PairC pc;     // phase 1 (exact series)
-    AdjSums adj;  // phase 4 and the chain rule
-  } u;
+  AdjSums adj;
 };
-static_assert(sizeof(SmemStatic) <= 4096, "static shared memory over its reservation");
-static_assert(sizeof(SmemStatic) + 2 * TABLE_M * sizeof(float4) <= 8192,
-              "static shared memory (with the table) over its reservation");
 
 __device__ __forceinline__ void buffers(const SysParams& sp, float* dsm, bool two, float*& A,
                                         float*& Bf, int slot_index) {
@@ -336,33 +156,12 @@ __device__ __forceinline__ void buffers(const SysParams& sp, float* dsm, bool tw
 }
 
 // Phase 1: bin the sub-pixel surface brightness into the padded buffer A.
+// Pixels go in the lanes of float2 pairs: four pixels per thread (p, p + T,
+// p + 2T, p + 3T; two interleaved pairs) while all four exist, then pairs,
+// where a missing second pixel repeats the first and is not written.
 template <int NL, int NS, bool TAB>
-__device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& sc, const EplC& e,
-                                           const LightC* L, const float4* tab, float* A) {
-  const int s = sp.s, npix = sp.ny * sp.nx;
-  const float D = sp.D;
-  PixelWalk pw(sp.nx);
-  for (int p = threadIdx.x; p < npix; p += THREADS, pw.next()) {
-    const float xj = (float)pw.j + sp.xg0, yi = (float)pw.i + sp.yg0;
-    float acc = 0.f;
-    for (int k = 0; k < s; ++k) {
-      const float y = (yi + sp.off[k]) * D;
-      for (int l = 0; l < s; ++l) {
-        const float x = (xj + sp.off[l]) * D;
-        acc += surface_brightness<NL, NS, TAB>(sc, e, L, tab, x, y);
-      }
-    }
-    A[(size_t)(pw.i + sp.cy) * sp.Wp + pw.j + sp.cx] = acc * sp.scale;
-  }
-}
-
-// Phase 1 on the exact series in the lanes of float2 pairs: four pixels per
-// thread (p, p + T, p + 2T, p + 3T; two interleaved pairs) while all four
-// exist, then pairs, where a missing second pixel repeats the first and is not
-// written. Needs pc filled (fill_pair_consts and a barrier).
-template <int NL, int NS>
-__device__ __forceinline__ void bin_pixels2(const SysParams& sp, const PairC& pc, int nq,
-                                            float* A) {
+__device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& sc,
+                                           const float4* tab, float* A) {
   const int s = sp.s, npix = sp.ny * sp.nx, Wp = sp.Wp, cy = sp.cy, cx = sp.cx;
   const float2 D = f2(sp.D), scale = f2(sp.scale);
   PixelWalk w0(sp.nx);
@@ -386,7 +185,7 @@ __device__ __forceinline__ void bin_pixels2(const SysParams& sp, const PairC& pc
         const float2 ol = f2(sp.off[l]);
         const float2 x0 = mul2(add2(xj0, ol), D), x1 = mul2(add2(xj1, ol), D);
         float2 sb0, sb1;
-        surface_brightness2x2<NL, NS>(reload(pc), nq, x0, y0, x1, y1, sb0, sb1);
+        surface_brightness4<NL, NS, TAB>(reload(sc), tab, x0, y0, x1, y1, sb0, sb1);
         acc0 = add2(acc0, sb0);
         acc1 = add2(acc1, sb1);
       }
@@ -412,7 +211,7 @@ __device__ __forceinline__ void bin_pixels2(const SysParams& sp, const PairC& pc
       const float2 y = mul2(add2(yi, f2(sp.off[k])), D);
       for (int l = 0; l < s; ++l) {
         const float2 x = mul2(add2(xj, f2(sp.off[l])), D);
-        acc = add2(acc, surface_brightness2<NL, NS>(reload(pc), nq, x, y));
+        acc = add2(acc, surface_brightness2<NL, NS, TAB>(reload(sc), tab, x, y));
       }
     }
     acc = mul2(acc, scale);
@@ -423,45 +222,57 @@ __device__ __forceinline__ void bin_pixels2(const SysParams& sp, const PairC& pc
   }
 }
 
-// Phase 4: sub-pixel adjoint; per-thread FP32 sums are flushed into the
-// per-warp sums redP every FLUSH_PIX pixels, which bounds the FP32
-// accumulation length (near the mode the gradient is a small difference of
-// large sums).
+// Phase 4: sub-pixel adjoint over pixel pairs (p, p + T) in float2 lanes (a
+// missing second pixel repeats the first with u = 0). Per-lane FP32 sums are
+// flushed into the per-warp sums redP every FLUSH_IT pairs, which bounds the
+// FP32 accumulation length (near the mode the gradient is a small difference
+// of large sums).
 template <int NL, int NS, bool TAB>
 __device__ __forceinline__ void adjoint_pixels(const SysParams& sp, const SampleC& sc,
-                                               const EplC& e, const LightC* L, const float4* tab,
-                                               const float* A, float (*redP)[MAX_P]) {
+                                               const float4* tab, const float* A,
+                                               float (*redP)[MAX_P]) {
   constexpr int P = 8 + 7 * (NL + NS);
-  constexpr int FLUSH_PIX = 2;
+  constexpr int FLUSH_IT = 2;
+  // float2 sums (one per lane) up to 22 parameters, else lane-summed floats
+  using AccT = typename std::conditional<(P <= 22), float2, float>::type;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = sp.s, npix = sp.ny * sp.nx, Wp = sp.Wp, cy = sp.cy, cx = sp.cx;
-  const float D = sp.D;
-  float acc[P];
+  const float2 D = f2(sp.D);
+  AccT acc[P];
 #pragma unroll
-  for (int k = 0; k < P; ++k) acc[k] = 0.f;
-  const int iters = (npix + THREADS - 1) / THREADS;  // same trip count in every lane
-  PixelWalk pw(sp.nx);
-  for (int it = 0; it < iters; ++it, pw.next()) {
-    const int p = threadIdx.x + it * THREADS;
+  for (int k = 0; k < P; ++k) acc[k] = acc_zero<AccT>();
+  const int iters = (npix + 2 * THREADS - 1) / (2 * THREADS);  // the same in every lane
+  PixelWalk w0(sp.nx);
+  for (int it = 0; it < iters; ++it) {
+    const int p = threadIdx.x + 2 * it * THREADS;
+    PixelWalk w1 = w0;
+    w1.next();
     if (p < npix) {
-      const float u = A[(size_t)(pw.i + cy) * Wp + pw.j + cx];
-      const float xj = (float)pw.j + sp.xg0, yi = (float)pw.i + sp.yg0;
+      const bool v1 = p + THREADS < npix;
+      const int i1 = v1 ? w1.i : w0.i, j1 = v1 ? w1.j : w0.j;
+      const float u0 = A[(size_t)(w0.i + cy) * Wp + w0.j + cx];
+      const float u1 = v1 ? A[(size_t)(i1 + cy) * Wp + j1 + cx] : 0.f;
+      const float2 u = make_float2(u0, u1);
+      const float2 xj = make_float2((float)w0.j + sp.xg0, (float)j1 + sp.xg0);
+      const float2 yi = make_float2((float)w0.i + sp.yg0, (float)i1 + sp.yg0);
       for (int k = 0; k < s; ++k) {
-        const float y = (yi + sp.off[k]) * D;
+        const float2 y = mul2(add2(yi, f2(sp.off[k])), D);
         for (int l = 0; l < s; ++l) {
-          const float x = (xj + sp.off[l]) * D;
-          subpixel_adjoint<NL, NS, TAB>(sc, e, L, tab, x, y, u, acc);
+          const float2 x = mul2(add2(xj, f2(sp.off[l])), D);
+          subpixel_adjoint2<NL, NS, TAB, AccT>(reload(sc), tab, x, y, u, acc);
         }
       }
     }
-    if ((it + 1) % FLUSH_PIX == 0 || it + 1 == iters) {
+    w0 = w1;
+    w0.next();
+    if ((it + 1) % FLUSH_IT == 0 || it + 1 == iters) {
 #pragma unroll
       for (int k = 0; k < P; ++k) {
-        float v = acc[k];
+        float v = acc_total(acc[k]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) redP[warp][k] += v;
-        acc[k] = 0.f;
+        acc[k] = acc_zero<AccT>();
       }
     }
   }
@@ -505,17 +316,10 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
     return;
   }
   load_table<SURR>(sp.table + (size_t)blockIdx.x * 2 * TABLE_M, sc, tab);
-  if (SURR && sc.use_table) {
-    const EplC e = sc.epl;
-    LightC L[NL + NS];
-#pragma unroll
-    for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
-    bin_pixels<NL, NS, true>(sp, sc, e, L, tab, A);
-  } else {
-    fill_pair_consts(sc, NL + NS, st.u.pc);
-    __syncthreads();
-    bin_pixels2<NL, NS>(sp, st.u.pc, sc.nq, A);
-  }
+  if (SURR && sc.use_table)
+    bin_pixels<NL, NS, true>(sp, sc, tab, A);
+  else
+    bin_pixels<NL, NS, false>(sp, sc, tab, A);
   __syncthreads();
   float csum = 0.f, ccomp = 0.f;
   float* out = want_img ? img + (size_t)b * npix : nullptr;
@@ -556,6 +360,7 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
     zero_halo(sp, A, 32);
     zero_halo(sp, Bf, 32);
   }
+  for (int k = threadIdx.x; k < NWARPS * MAX_P; k += THREADS) (&st.adj.redP[0][0])[k] = 0.f;
   __syncthreads();
   if (sc.status != 0) {
     const float lv = sc.status == 2 ? __int_as_float(0x7fc00000) : -__int_as_float(0x7f800000);
@@ -569,20 +374,11 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
   const bool use_tab = SURR && sc.use_table;
   const int Wp = sp.Wp, cy = sp.cy, cx = sp.cx, nx = sp.nx;
   // phase 1
-  if (use_tab) {
-    const EplC e = sc.epl;
-    LightC L[NL + NS];
-#pragma unroll
-    for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
-    bin_pixels<NL, NS, true>(sp, sc, e, L, tab, A);
-  } else {
-    fill_pair_consts(sc, NL + NS, st.u.pc);
-    __syncthreads();
-    bin_pixels2<NL, NS>(sp, st.u.pc, sc.nq, A);
-  }
+  if (use_tab)
+    bin_pixels<NL, NS, true>(sp, sc, tab, A);
+  else
+    bin_pixels<NL, NS, false>(sp, sc, tab, A);
   __syncthreads();
-  // (the per-warp adjoint sums share memory with the phase-1 constants)
-  for (int k = threadIdx.x; k < NWARPS * MAX_P; k += THREADS) (&st.u.adj.redP[0][0])[k] = 0.f;
   // phase 2
   float csum = 0.f, ccomp = 0.f;
   correlate<true>(sp, A, [&](int i, int j, float m) {
@@ -603,20 +399,16 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
     A[(size_t)(i + cy) * Wp + j + cx] = g * scale;
   });
   __syncthreads();
-  // phase 4 (per-sample constants in registers from here on)
-  const EplC e = sc.epl;
-  LightC L[NL + NS];
-#pragma unroll
-  for (int c = 0; c < NL + NS; ++c) L[c] = sc.light[c];
+  // phase 4
   if (use_tab)
-    adjoint_pixels<NL, NS, true>(sp, sc, e, L, tab, A, st.u.adj.redP);
+    adjoint_pixels<NL, NS, true>(sp, sc, tab, A, st.adj.redP);
   else
-    adjoint_pixels<NL, NS, false>(sp, sc, e, L, tab, A, st.u.adj.redP);
+    adjoint_pixels<NL, NS, false>(sp, sc, tab, A, st.adj.redP);
   __syncthreads();
   if (threadIdx.x < P) {
     double v = 0.0;
-    for (int w = 0; w < NWARPS; ++w) v += (double)st.u.adj.redP[w][threadIdx.x];
-    st.u.adj.gsum[threadIdx.x] = v;
+    for (int w = 0; w < NWARPS; ++w) v += (double)st.adj.redP[w][threadIdx.x];
+    st.adj.gsum[threadIdx.x] = v;
   }
   __syncthreads();
   // chain rule to the parameters, one lane per component
@@ -624,12 +416,12 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
     const int c = threadIdx.x;
     float g[8];
     if (c == 0) {
-      epl_finish(st.fin[0], st.u.adj.gsum, g, use_tab);
+      epl_finish(st.fin[0], st.adj.gsum, g, use_tab);
 #pragma unroll
       for (int k = 0; k < 8; ++k) grad_out[k] = g[k] + sc.dprior[k];
     } else {
       const int o = 8 + 7 * (c - 1);
-      sersic_finish(st.fin[c], st.u.adj.gsum + o, g);
+      sersic_finish(st.fin[c], st.adj.gsum + o, g);
 #pragma unroll
       for (int k = 0; k < 7; ++k) grad_out[o + k] = g[k] + sc.dprior[o + k];
     }

@@ -1,5 +1,7 @@
-// Device-side lens model: per-sample staging, the EPL series deflection, the
-// elliptical Sersic profile, and their hand-written adjoints.
+// Device-side lens model: per-sample staging of the EPL series deflection and
+// the elliptical Sersic profiles, and the conversion of the adjoint's native
+// sums to parameter gradients (the sub-pixel evaluations are in
+// gl_subpixel.cuh).
 //
 // Notation (Sec. 3 parameters; Tessore & Metcalf 2015 for the EPL):
 //   lens frame  x' = cs dx + sn dy, y' = cs dy - sn dx about the centre,
@@ -53,37 +55,58 @@ __device__ __forceinline__ float rcp(float x) {
   return y;
 }
 
-// Per-sample constants of one Sersic component.
-struct LightC {
-  float xc, yc, cs, sn;
-  float q, iq, iq2;     // q, 1/q, 1/q^2
-  float c1, c0;         // log2 p = c1 log2(R^2) + c0
-  float bl;             // b_n log2(e)
-  float Ip;             // I_e e^{b_n}
-  float kX1, kX2, kY1, kY2;  // dS/d(X,Y) = S p/R^2 (kX1 x' + kX2 y', kY1 x' + kY2 y')
+// ---- paired FP32 arithmetic ----
+// The sub-pixel code evaluates two points at a time, one in each lane of a
+// float2: the FP32 operations are paired (f32x2) instructions, MUFU ones stay
+// per lane.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
+__device__ __forceinline__ float2 max2(float2 a, float b) {
+  return make_float2(fmaxf(a.x, b), fmaxf(a.y, b));
+}
+__device__ __forceinline__ float2 ex2_2(float2 a) { return make_float2(ex2(a.x), ex2(a.y)); }
+__device__ __forceinline__ float2 lg2_2(float2 a) { return make_float2(lg2(a.x), lg2(a.y)); }
+__device__ __forceinline__ float2 rsq2(float2 a) { return make_float2(rsq(a.x), rsq(a.y)); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp(a.x), rcp(a.y)); }
+
+// Per-sample constants, each held twice (both lanes of a float2) so that the
+// paired code uses them without moves; a leading "n" marks a negated value.
+struct EplP {
+  float2 nxc, nyc;            // minus the centre
+  float2 cs, sn, ncs, nsn;    // position angle
+  float2 q, nq, q2;
+  float2 f, nf, m2f;          // f = |e|, -f, -2f
+  float2 ht, CA;              // (1 - t)/2, 2 b^t / (1 + q)
+  float2 t, omt, ntmt;        // t, 1 - t, -(2 - t)
+  float2 omtq, omtq2;         // (1 - t) q, (1 - t) q^2
+  float2 Kk;                  // kappa = Kk A / R
+  float2 a0;                  // t/(2q) - 1/(1+q)
+  float2 lnb;
+  float2 ndfdq;               // -d f / d q = 2/(1+q)^2
 };
 
-// Per-sample constants of the EPL.
-struct EplC {
-  float xc, yc, cs, sn;
-  float q, q2, f, ht;   // ht = (1 - t)/2
-  float CA;             // 2 b^t / (1 + q)
-  float t, omt, tmt;    // t, 1 - t, 2 - t
-  float Kk;             // kappa = Kk A / R
-  float a0;             // t/(2q) - 1/(1+q)
-  float lnb;
-  float dfdq;           // -2/(1+q)^2
+// Per-sample constants of one Sersic component (paired).
+struct LightP {
+  float2 nxc, nyc, cs, sn, nsn;
+  float2 q, iq, niq2;         // q, 1/q, -1/q^2
+  float2 c1, c0;              // log2 p = c1 log2(R^2) + c0
+  float2 nbl;                 // -b_n log2(e)
+  float2 Ip;                  // I_e e^{b_n}
+  float2 kX1, kX2, kY1, kY2;  // dS/d(X,Y) = S p/R^2 (kX1 x' + kX2 y', kY1 x' + kY2 y')
 };
 
 struct SampleC {
-  EplC epl;
-  float g1, g2;
-  LightC light[MAX_COMP];  // lens lights, then sources
-  float4 cE[N_MAX / 4];    // E-series coefficients c_n (-f)^{n-1}, n = 1..N (index n-1)
-  float4 cT[N_MAX / 4];    // t-derivative coefficients c_n h_n (-f)^{n-1}
-  int nq;                  // number of float4 chunks (N rounded up to a multiple of 4)
-  int status;              // 0 ok, 1 outside domain/support (-inf), 2 NaN
-  int use_table;           // surrogate table covers this row
+  EplP epl;
+  float2 omg1, opg1, ng2;    // 1 - g1, 1 + g1, -g2 (external shear)
+  LightP light[MAX_COMP];    // lens lights, then sources
+  float2 cE[N_MAX];          // E-series coefficients c_n (-f)^{n-1}, n = 1..4 nq (index n-1), paired
+  float2 cT[N_MAX];          // t-derivative coefficients c_n h_n (-f)^{n-1}, paired
+  int nq;                    // number of 4-term chunks (N rounded up to a multiple of 4)
+  int status;                // 0 ok, 1 outside domain/support (-inf), 2 NaN
+  int use_table;             // surrogate table covers this row
   double logprior;
   float dprior[MAX_P];
 };
@@ -193,38 +216,44 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
     FinishC& F = fin[lane];
     F.e1 = e1; F.e2 = e2; F.c = c; F.cs = cs; F.sn = sn; F.q = q;
     if (lane == 0) {
-      EplC& E = sc.epl;
+      EplP& E = sc.epl;
       const float t = th[1] - 1.f;
       const float b = th[0] * sqrtf(q);
-      E.xc = th[4]; E.yc = th[5]; E.cs = cs; E.sn = sn;
-      E.q = q; E.q2 = q * q; E.f = c; E.ht = 0.5f * (1.f - t);
-      E.CA = 2.f * powf(b, t) / (1.f + q);
-      E.t = t; E.omt = 1.f - t; E.tmt = 2.f - t;
-      E.Kk = (2.f - t) * (1.f + q) * 0.25f;
-      E.a0 = t / (2.f * q) - 1.f / (1.f + q);
-      E.lnb = logf(b);
-      E.dfdq = -2.f / ((1.f + q) * (1.f + q));
+      E.nxc = f2(-th[4]); E.nyc = f2(-th[5]);
+      E.cs = f2(cs); E.sn = f2(sn); E.ncs = f2(-cs); E.nsn = f2(-sn);
+      E.q = f2(q); E.nq = f2(-q); E.q2 = f2(q * q);
+      E.f = f2(c); E.nf = f2(-c); E.m2f = f2(-2.f * c);
+      E.ht = f2(0.5f * (1.f - t));
+      E.CA = f2(2.f * powf(b, t) / (1.f + q));
+      E.t = f2(t); E.omt = f2(1.f - t); E.ntmt = f2(t - 2.f);
+      E.omtq = f2((1.f - t) * q); E.omtq2 = f2((1.f - t) * q * q);
+      E.Kk = f2((2.f - t) * (1.f + q) * 0.25f);
+      E.a0 = f2(t / (2.f * q) - 1.f / (1.f + q));
+      E.lnb = f2(logf(b));
+      E.ndfdq = f2(2.f / ((1.f + q) * (1.f + q)));
       F.p0 = th[0]; F.t = t; F.n = 0.f; F.I = 0.f; F.bn = 0.f;
       t_epl = t;
       f_epl = c;
-      sc.g1 = th[6];
-      sc.g2 = th[7];
+      sc.omg1 = f2(1.f - th[6]);
+      sc.opg1 = f2(1.f + th[6]);
+      sc.ng2 = f2(-th[7]);
       sc.use_table = sp.table != nullptr && q >= sp.sq_lo && q <= sp.sq_hi &&
                      th[1] >= sp.sg_lo && th[1] <= sp.sg_hi;
     } else {
-      LightC& L = sc.light[lane - 1];
+      LightP& L = sc.light[lane - 1];
       const float* p = th + 8 + 7 * (lane - 1);
       const float Re = p[0], n = p[1];
       const float bn = 1.9992f * n - 0.3271f;
-      L.xc = p[4]; L.yc = p[5]; L.cs = cs; L.sn = sn;
-      L.q = q; L.iq = 1.f / q; L.iq2 = 1.f / (q * q);
-      L.c1 = 0.5f / n;
-      L.c0 = -log2f(Re) / n;
-      L.bl = bn * 1.4426950408889634f;
-      L.Ip = p[6] * expf(bn);
+      L.nxc = f2(-p[4]); L.nyc = f2(-p[5]);
+      L.cs = f2(cs); L.sn = f2(sn); L.nsn = f2(-sn);
+      L.q = f2(q); L.iq = f2(1.f / q); L.niq2 = f2(-1.f / (q * q));
+      L.c1 = f2(0.5f / n);
+      L.c0 = f2(-log2f(Re) / n);
+      L.nbl = f2(-bn * 1.4426950408889634f);
+      L.Ip = f2(p[6] * expf(bn));
       const float m = -bn / n;
-      L.kX1 = m * q * cs; L.kX2 = -m * sn / q;
-      L.kY1 = m * q * sn; L.kY2 = m * cs / q;
+      L.kX1 = f2(m * q * cs); L.kX2 = f2(-m * sn / q);
+      L.kY1 = f2(m * q * sn); L.kY2 = f2(m * cs / q);
       F.p0 = Re; F.n = n; F.I = p[6]; F.bn = bn; F.t = 0.f;
     }
   }
@@ -241,8 +270,7 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
   // coefficients: e_n = c_n (-f)^{n-1} = prod_{k<=n} rho_k, rho_1 = r_1,
   // rho_k = -f r_k, r_k = (2k-2+t)/(2k+2-t); t_n = e_n h_n, h_n = sum_k
   // 1/(2k-2+t) + 1/(2k+2-t): inclusive warp scans of products and sums.
-  float* ce = reinterpret_cast<float*>(sc.cE);
-  float* ct = reinterpret_cast<float*>(sc.cT);
+
   float carry_e = 1.f, carry_h = 0.f;
   for (int base = 0; base < 4 * nq; base += 32) {
     const int n = base + lane + 1;
@@ -257,8 +285,8 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
     }
     const float en = carry_e * rho, hn = carry_h + hin;
     if (n <= 4 * nq) {
-      ce[n - 1] = n <= N ? en : 0.f;
-      ct[n - 1] = n <= N ? en * hn : 0.f;
+      sc.cE[n - 1] = f2(n <= N ? en : 0.f);
+      sc.cT[n - 1] = f2(n <= N ? en * hn : 0.f);
     }
     carry_e = __shfl_sync(0xffffffffu, en, 31);
     carry_h = __shfl_sync(0xffffffffu, hn, 31);
@@ -268,119 +296,6 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
     sc.logprior = lp;
     sc.status = 0;
   }
-}
-
-// ---- forward pieces ----
-
-__device__ __forceinline__ float sersic_fwd(const LightC& c, float X, float Y) {
-  const float dx = X - c.xc, dy = Y - c.yc;
-  const float xp = fmaf(c.cs, dx, c.sn * dy);
-  const float yp = fmaf(c.cs, dy, -c.sn * dx);
-  const float R2 = fmaxf(fmaf(c.q * xp, xp, c.iq * yp * yp), R_MIN2);
-  const float p = ex2(fmaf(c.c1, lg2(R2), c.c0));
-  return c.Ip * ex2(-c.bl * p);
-}
-
-// Horner sum E = sum_{n=1}^{N} cE[n-1] w^{n-1}, coefficients in float4 chunks.
-__device__ __forceinline__ void horner1(const float4* __restrict__ cE, int nq, float wr, float wi,
-                                        float& Er, float& Ei) {
-  float er = 0.f, ei = 0.f;
-  for (int k = nq - 1; k >= 0; --k) {
-    const float4 c = cE[k];
-#define GL_H1(cc)                                      \
-  {                                                    \
-    const float nr = fmaf(wr, er, fmaf(-wi, ei, cc));  \
-    ei = fmaf(wr, ei, wi * er);                        \
-    er = nr;                                           \
-  }
-    GL_H1(c.w) GL_H1(c.z) GL_H1(c.y) GL_H1(c.x)
-#undef GL_H1
-  }
-  Er = er;
-  Ei = ei;
-}
-
-// The same for E and the t-derivative sum together.
-__device__ __forceinline__ void horner2(const float4* __restrict__ cE, const float4* __restrict__ cT,
-                                        int nq, float wr, float wi, float& Er, float& Ei,
-                                        float& Tr, float& Ti) {
-  float er = 0.f, ei = 0.f, tr = 0.f, ti = 0.f;
-  for (int k = nq - 1; k >= 0; --k) {
-    const float4 c = cE[k];
-    const float4 d = cT[k];
-#define GL_H2(cc, dd)                                  \
-  {                                                    \
-    const float nr = fmaf(wr, er, fmaf(-wi, ei, cc));  \
-    ei = fmaf(wr, ei, wi * er);                        \
-    er = nr;                                           \
-    const float mr = fmaf(wr, tr, fmaf(-wi, ti, dd));  \
-    ti = fmaf(wr, ti, wi * tr);                        \
-    tr = mr;                                           \
-  }
-    GL_H2(c.w, d.w) GL_H2(c.z, d.z) GL_H2(c.y, d.y) GL_H2(c.x, d.x)
-#undef GL_H2
-  }
-  Er = er;
-  Ei = ei;
-  Tr = tr;
-  Ti = ti;
-}
-
-// EPL deflection (world frame) at (x, y).
-__device__ __forceinline__ void epl_alpha(const EplC& e, const float4* __restrict__ cE, int nq,
-                                          float x, float y, float& ax, float& ay) {
-  const float dx = x - e.xc, dy = y - e.yc;
-  const float xp = fmaf(e.cs, dx, e.sn * dy);
-  const float yp = fmaf(e.cs, dy, -e.sn * dx);
-  const float R2 = fmaxf(fmaf(e.q2 * xp, xp, yp * yp), R_MIN2);
-  const float ir = rsq(R2);
-  const float cph = e.q * xp * ir, sph = yp * ir;
-  const float wr = fmaf(cph, cph, -sph * sph), wi = 2.f * cph * sph;
-  float Er, Ei;
-  horner1(cE, nq, wr, wi, Er, Ei);
-  const float zr = -e.f * wr, zi = -e.f * wi;
-  const float Fr = 1.f + fmaf(zr, Er, -zi * Ei);
-  const float Fi = fmaf(zr, Ei, zi * Er);
-  const float A = e.CA * ex2(e.ht * lg2(R2));
-  const float aLr = A * fmaf(cph, Fr, -sph * Fi);
-  const float aLi = A * fmaf(cph, Fi, sph * Fr);
-  ax = fmaf(e.cs, aLr, -e.sn * aLi);
-  ay = fmaf(e.sn, aLr, e.cs * aLi);
-}
-
-// ---- adjoint pieces ----
-// Native accumulators of a Sersic component (converted to parameter
-// gradients once per sample): [0] sum uS, [1] sum uSp, [2] sum uSp log2 p,
-// [3] sum uSp/R^2 (x'^2 - y'^2/q^2), [4] sum uSp/R^2 x'y',
-// [5] sum uSp/R^2 x', [6] sum uSp/R^2 y'.
-// Returns S; if grad_pos, adds dS/dX, dS/dY (without u) to gX, gY.
-template <bool grad_pos>
-__device__ __forceinline__ float sersic_adj(const LightC& c, float X, float Y, float u,
-                                            float* __restrict__ a, float& gX, float& gY) {
-  const float dx = X - c.xc, dy = Y - c.yc;
-  const float xp = fmaf(c.cs, dx, c.sn * dy);
-  const float yp = fmaf(c.cs, dy, -c.sn * dx);
-  const float R2raw = fmaf(c.q * xp, xp, c.iq * yp * yp);
-  const float R2 = fmaxf(R2raw, R_MIN2);
-  const float l2p = fmaf(c.c1, lg2(R2), c.c0);
-  const float p = ex2(l2p);
-  const float S = c.Ip * ex2(-c.bl * p);
-  const float Sp = S * p;
-  // d R^2 / d(position) vanishes where the radius is clamped
-  const float Dh = R2raw > R_MIN2 ? Sp * rcp(R2) : 0.f;
-  const float uS = u * S, uSp = u * Sp, kD = u * Dh;
-  a[0] += uS;
-  a[1] += uSp;
-  a[2] = fmaf(uSp, l2p, a[2]);
-  a[3] = fmaf(kD, fmaf(xp, xp, -c.iq2 * yp * yp), a[3]);
-  a[4] = fmaf(kD * xp, yp, a[4]);
-  a[5] = fmaf(kD, xp, a[5]);
-  a[6] = fmaf(kD, yp, a[6]);
-  if (grad_pos) {
-    gX = fmaf(Dh, fmaf(c.kX1, xp, c.kX2 * yp), gX);
-    gY = fmaf(Dh, fmaf(c.kY1, xp, c.kY2 * yp), gY);
-  }
-  return S;
 }
 
 // Converts a Sersic component's native accumulators a[0..6] to gradients

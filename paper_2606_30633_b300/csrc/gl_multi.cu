@@ -85,8 +85,9 @@ gl_status gl_multi_create(gl_system* const* systems, int n_sys, const int* rows_
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device);
   cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device);
-  const size_t reserve = 8192 + 1024;  // static shared memory (with the table) + system reserve
-  if (smem_blk <= 8192) return bail(fail(GL_ECUDA, "device shared memory too small"));
+  const size_t stat = gl::static_smem_bytes();
+  const size_t reserve = stat + 1024;  // static shared memory (with the table) + system reserve
+  if ((size_t)smem_blk <= reserve) return bail(fail(GL_ECUDA, "device shared memory too small"));
   size_t budget = 0;
   int ctas = 2;
   if (smem_policy == 1) budget = (size_t)smem_sm / 2 > reserve ? (size_t)smem_sm / 2 - reserve : 0;
@@ -147,7 +148,7 @@ gl_status gl_multi_create(gl_system* const* systems, int n_sys, const int* rows_
   if (slot && cudaMalloc(&m->scratch, (size_t)m->grid * slot * sizeof(float)) != cudaSuccess)
     return bail(fail(GL_ENOMEM, "multi scratch allocation"));
   for (auto& sp : m->h_sys) sp.scratch = m->scratch;
-  if (gl::set_smem_limits_grad((size_t)smem_blk - 8192) != cudaSuccess)
+  if (gl::set_smem_limits_grad((size_t)smem_blk - stat) != cudaSuccess)
     return bail(fail(GL_ECUDA, "kernel shared-memory limit"));
   *out = m;
   return GL_OK;
