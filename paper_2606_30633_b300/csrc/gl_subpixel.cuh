@@ -45,61 +45,79 @@ __device__ __forceinline__ Geo2 epl_geometry2(const EplP& e, float2 x, float2 y)
   return g;
 }
 
-// ------------------------------------------------------ Horner sums ----
-// One Horner step of e <- w e + c (complex w, real coefficient c).
-__device__ __forceinline__ void horner_step(const Geo2& g, float2 c, float2& er, float2& ei) {
-  const float2 nr = fma2(g.wr, er, fma2(g.nwi, ei, c));
-  ei = fma2(g.wr, ei, mul2(g.wi, er));
-  er = nr;
+// -------------------------------------------------- series summation ----
+// The series are real-coefficient power series in w = e^{i theta} (theta =
+// 2 vphi, |w| = 1), summed with Clenshaw's recurrence (Clenshaw 1955):
+//   b_k = a_k + 2 cos(theta) b_{k+1} - b_{k+2},  b_M = b_{M+1} = 0,
+//   sum_{k<M} a_k w^k = (b_0 - cos(theta) b_1) + i sin(theta) b_1,
+// two operations per term where a complex Horner step takes four, and one
+// FMA latency per term on the dependency chain. With a_k = c_{k+1}:
+//   E = sum_{n>=1} c_n w^{n-1} = (b_0 - wr b_1, wi b_1),
+//   w E = (wr b_0 - b_1, wi b_0)       (using |w|^2 = 1).
+struct Clen2 {
+  float2 b0, b1;
+};
+
+// One Clenshaw step: returns a + tw b1 - b2.
+__device__ __forceinline__ float2 clen_step(float2 tw, float2 b1, float2 b2, float2 a) {
+  return fma2(tw, b1, fma2(f2(-1.f), b2, a));
 }
 
-// E = sum_{n=1}^{4 nq} cE[n-1] w^{n-1} at two points.
-__device__ __forceinline__ void horner_E(const float2* __restrict__ cE, int nq, const Geo2& g,
-                                         float2& Er, float2& Ei) {
-  const float4* c4 = reinterpret_cast<const float4*>(cE);
-  float2 er = f2(0.f), ei = f2(0.f);
+// The sum over the staged coefficients c[0 .. 4 nq) at two points.
+__device__ __forceinline__ Clen2 clenshaw(const float2* __restrict__ c, int nq, const Geo2& g) {
+  const float4* c4 = reinterpret_cast<const float4*>(c);
+  const float2 tw = add2(g.wr, g.wr);
+  float2 b1 = f2(0.f), b2 = f2(0.f);
   for (int k = 2 * nq - 1; k >= 0; --k) {
-    const float4 c = c4[k];  // terms 2k+2 (z, w) and 2k+1 (x, y)
-    horner_step(g, make_float2(c.z, c.w), er, ei);
-    horner_step(g, make_float2(c.x, c.y), er, ei);
+    const float4 a = c4[k];  // a_{2k+1} in (z, w), a_{2k} in (x, y)
+    const float2 bh = clen_step(tw, b1, b2, make_float2(a.z, a.w));
+    const float2 bl = clen_step(tw, bh, b1, make_float2(a.x, a.y));
+    b2 = bh;
+    b1 = bl;
   }
-  Er = er;
-  Ei = ei;
+  return Clen2{b1, b2};
 }
 
 // The same at four points (two pairs interleaved for instruction-level parallelism).
-__device__ __forceinline__ void horner_E2(const float2* __restrict__ cE, int nq, const Geo2& g0,
-                                          const Geo2& g1, float2& Er0, float2& Ei0, float2& Er1,
-                                          float2& Ei1) {
-  const float4* c4 = reinterpret_cast<const float4*>(cE);
-  float2 er0 = f2(0.f), ei0 = f2(0.f), er1 = f2(0.f), ei1 = f2(0.f);
+__device__ __forceinline__ void clenshaw2(const float2* __restrict__ c, int nq, const Geo2& g0,
+                                          const Geo2& g1, Clen2& s0, Clen2& s1) {
+  const float4* c4 = reinterpret_cast<const float4*>(c);
+  const float2 tw0 = add2(g0.wr, g0.wr), tw1 = add2(g1.wr, g1.wr);
+  float2 p1 = f2(0.f), p2 = f2(0.f), q1 = f2(0.f), q2 = f2(0.f);
   for (int k = 2 * nq - 1; k >= 0; --k) {
-    const float4 c = c4[k];
-    const float2 chi = make_float2(c.z, c.w), clo = make_float2(c.x, c.y);
-    horner_step(g0, chi, er0, ei0);
-    horner_step(g1, chi, er1, ei1);
-    horner_step(g0, clo, er0, ei0);
-    horner_step(g1, clo, er1, ei1);
+    const float4 a = c4[k];
+    const float2 ah = make_float2(a.z, a.w), al = make_float2(a.x, a.y);
+    const float2 ph = clen_step(tw0, p1, p2, ah);
+    const float2 qh = clen_step(tw1, q1, q2, ah);
+    const float2 pl = clen_step(tw0, ph, p1, al);
+    const float2 ql = clen_step(tw1, qh, q1, al);
+    p2 = ph; p1 = pl;
+    q2 = qh; q1 = ql;
   }
-  Er0 = er0; Ei0 = ei0; Er1 = er1; Ei1 = ei1;
+  s0 = Clen2{p1, p2};
+  s1 = Clen2{q1, q2};
 }
 
 // E and the t-derivative sum T together.
-__device__ __forceinline__ void horner_ET(const float2* __restrict__ cE,
-                                          const float2* __restrict__ cT, int nq, const Geo2& g,
-                                          float2& Er, float2& Ei, float2& Tr, float2& Ti) {
+__device__ __forceinline__ void clenshaw_ET(const float2* __restrict__ cE,
+                                            const float2* __restrict__ cT, int nq, const Geo2& g,
+                                            Clen2& sE, Clen2& sT) {
   const float4* c4 = reinterpret_cast<const float4*>(cE);
   const float4* d4 = reinterpret_cast<const float4*>(cT);
-  float2 er = f2(0.f), ei = f2(0.f), tr = f2(0.f), ti = f2(0.f);
+  const float2 tw = add2(g.wr, g.wr);
+  float2 e1 = f2(0.f), e2 = f2(0.f), t1 = f2(0.f), t2 = f2(0.f);
   for (int k = 2 * nq - 1; k >= 0; --k) {
-    const float4 c = c4[k];
+    const float4 a = c4[k];
     const float4 d = d4[k];
-    horner_step(g, make_float2(c.z, c.w), er, ei);
-    horner_step(g, make_float2(d.z, d.w), tr, ti);
-    horner_step(g, make_float2(c.x, c.y), er, ei);
-    horner_step(g, make_float2(d.x, d.y), tr, ti);
+    const float2 eh = clen_step(tw, e1, e2, make_float2(a.z, a.w));
+    const float2 th = clen_step(tw, t1, t2, make_float2(d.z, d.w));
+    const float2 el = clen_step(tw, eh, e1, make_float2(a.x, a.y));
+    const float2 tl = clen_step(tw, th, t1, make_float2(d.x, d.y));
+    e2 = eh; e1 = el;
+    t2 = th; t1 = tl;
   }
-  Er = er; Ei = ei; Tr = tr; Ti = ti;
+  sE = Clen2{e1, e2};
+  sT = Clen2{t1, t2};
 }
 
 // ------------------------------------------------- surrogate table lookup ----
@@ -145,11 +163,11 @@ __device__ __forceinline__ TabF table_eval(const float4* __restrict__ tab, float
 }
 
 // ------------------------------------------------------ forward pieces ----
-// F = 1 + z E with z = -f w:  Fr = 1 - f (wr Er - wi Ei),  Fi = -f (wr Ei + wi Er).
-__device__ __forceinline__ void series_F(const EplP& e, const Geo2& g, float2 Er, float2 Ei,
-                                         float2& Fr, float2& Fi) {
-  Fr = fma2(e.nf, fma2(g.wr, Er, mul2(g.nwi, Ei)), f2(1.f));
-  Fi = mul2(e.nf, fma2(g.wr, Ei, mul2(g.wi, Er)));
+// F = 1 + z E = 1 - f w E with z = -f w:  Fr = 1 - f (wr b_0 - b_1),  Fi = -f wi b_0.
+__device__ __forceinline__ void series_F(const EplP& e, const Geo2& g, const Clen2& sE, float2& Fr,
+                                         float2& Fi) {
+  Fr = fma2(e.nf, fma2(g.wr, sE.b0, neg2(sE.b1)), f2(1.f));
+  Fi = mul2(e.nf, mul2(g.wi, sE.b0));
 }
 
 // The source-plane position beta = theta - alpha - (g1 x + g2 y, g2 x - g1 y)
@@ -196,9 +214,7 @@ __device__ __forceinline__ void deflection_F(const SampleC& sc, const float4* ta
     Fr = make_float2(t0.Fr, t1.Fr);
     Fi = make_float2(t0.Fi, t1.Fi);
   } else {
-    float2 Er, Ei;
-    horner_E(sc.cE, sc.nq, g, Er, Ei);
-    series_F(sc.epl, g, Er, Ei, Fr, Fi);
+    series_F(sc.epl, g, clenshaw(sc.cE, sc.nq, g), Fr, Fi);
   }
 }
 
@@ -225,10 +241,10 @@ __device__ __forceinline__ void surface_brightness4(const SampleC& sc, const flo
     deflection_F<true>(sc, tab, g0, Fr0, Fi0);
     deflection_F<true>(sc, tab, g1, Fr1, Fi1);
   } else {
-    float2 Er0, Ei0, Er1, Ei1;
-    horner_E2(sc.cE, sc.nq, g0, g1, Er0, Ei0, Er1, Ei1);
-    series_F(sc.epl, g0, Er0, Ei0, Fr0, Fi0);
-    series_F(sc.epl, g1, Er1, Ei1, Fr1, Fi1);
+    Clen2 s0, s1;
+    clenshaw2(sc.cE, sc.nq, g0, g1, s0, s1);
+    series_F(sc.epl, g0, s0, Fr0, Fi0);
+    series_F(sc.epl, g1, s1, Fr1, Fi1);
   }
   float2 bx, by;
   lens_equation2(sc, g0, x0, y0, Fr0, Fi0, bx, by);
@@ -297,7 +313,7 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
   const EplP& e = sc.epl;
   const Geo2 g = epl_geometry2(e, x, y);
   const float2 iR2 = mul2(g.ir, g.ir);
-  float2 Fr, Fi, Er, Ei, Tr, Ti, zr, zi, nzi;
+  float2 Fr, Fi, Er, Ei, dtFr, dtFi, zi, nzi;  // dtF = dF/dt
   TabF t0, t1;
   if (TAB) {
     t0 = table_eval<true>(tab, g.cph.x, g.sph.x);
@@ -305,12 +321,18 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
     Fr = make_float2(t0.Fr, t1.Fr);
     Fi = make_float2(t0.Fi, t1.Fi);
   } else {
-    horner_ET(sc.cE, sc.cT, sc.nq, g, Er, Ei, Tr, Ti);
-    zr = mul2(e.nf, g.wr);
+    Clen2 sE, sT;
+    clenshaw_ET(sc.cE, sc.cT, sc.nq, g, sE, sT);
+    const float2 nwr = neg2(g.wr);
+    Er = fma2(nwr, sE.b1, sE.b0);
+    Ei = mul2(g.wi, sE.b1);
+    Fr = fma2(e.f, fma2(nwr, sE.b0, sE.b1), f2(1.f));
+    Fi = mul2(e.nf, mul2(g.wi, sE.b0));
+    // dF/dt = z T = -f w T
+    dtFr = mul2(e.f, fma2(nwr, sT.b0, sT.b1));
+    dtFi = mul2(e.nf, mul2(g.wi, sT.b0));
     zi = mul2(e.nf, g.wi);
     nzi = mul2(e.f, g.wi);
-    Fr = fma2(zr, Er, fma2(nzi, Ei, f2(1.f)));
-    Fi = fma2(zr, Ei, mul2(zi, Er));
   }
   const float2 Lm = lg2_2(g.R2);
   const float2 A = mul2(e.CA, ex2_2(mul2(e.ht, Lm)));
@@ -367,9 +389,7 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
     acc_add(acc[5], Dy);
     return;
   }
-  // dF/dt = z (Tr + i Ti)
-  const float2 TFr = fma2(zr, Tr, mul2(nzi, Ti)), TFi = fma2(zr, Ti, mul2(zi, Tr));
-  const float2 QTr = fma2(Qr, TFr, mul2(nQi, TFi)), QTi = fma2(Qr, TFi, mul2(Qi, TFr));
+  const float2 QTr = fma2(Qr, dtFr, mul2(nQi, dtFi)), QTi = fma2(Qr, dtFi, mul2(Qi, dtFr));
   const float2 sT = fma2(vLx, QTr, mul2(vLy, QTi));
   // F'(z) = [t F - (2-t) E] / (2 (1 - z))
   const float2 nr = fma2(e.t, Fr, mul2(e.ntmt, Er)), ni = fma2(e.t, Fi, mul2(e.ntmt, Ei));
