@@ -57,20 +57,21 @@ def algorithmic_ops(theta: np.ndarray, ny: int, nx: int, s: int, k: int, n_light
     """FP32 operations (an FMA counts once) and MUFU operations of one
     log p + gradient evaluation per row, summed over rows, from the
     formulation's operation count:
-      forward sub-pixel  34 + 4N (EPL) + 8 (shear, lens equation)
+      forward sub-pixel  34 + 2N (EPL) + 8 (shear, lens equation)
                          + 15 per Sersic + 2 (grid) ... 3 MUFU EPL, 3 per Sersic
-      adjoint sub-pixel  38 + 8N (EPL, both series) + 8 + 31 per Sersic
+      adjoint sub-pixel  38 + 4N (EPL, both series) + 8 + 31 per Sersic
                          + 6 per source (position gradient) + 85 (EPL adjoint)
                          + 2 (grid) ... 4 MUFU EPL, 4 per Sersic
       per pixel          2 k^2 (PSF convolution and its adjoint) + 8
-    with N the per-row series length."""
+    with N the per-row series length; a series costs 2 operations per term
+    (Clenshaw's recurrence: one FMA and one add)."""
     nsub = ny * nx * s * s
     npix = ny * nx
     ncomp = n_light + n_src
     f = np.hypot(theta[:, 2], theta[:, 3])
     N = np.array([series_terms(float(v)) for v in f])
-    fwd = 34 + 4 * N + 8 + 15 * ncomp + 2
-    adj = 38 + 8 * N + 8 + 31 * ncomp + 6 * n_src + 85 + 2
+    fwd = 34 + 2 * N + 8 + 15 * ncomp + 2
+    adj = 38 + 4 * N + 8 + 31 * ncomp + 6 * n_src + 85 + 2
     ops = nsub * (fwd + adj) + npix * (2 * k * k + 8)
     mufu = nsub * (3 + 3 * ncomp + 4 + 4 * ncomp)
     return float(ops.sum()), float(mufu * theta.shape[0])

@@ -114,7 +114,7 @@ gl_status prepare_surrogate(gl_system* s, const float* theta, int B, SysParams& 
     cudaFree(s->d_table);
     s->d_table = nullptr;
     s->table_rows = 0;
-    GL_CUDA(cudaMalloc(&s->d_table, (size_t)B * 2 * gl::TABLE_M * sizeof(float4)),
+    GL_CUDA(cudaMalloc(&s->d_table, (size_t)B * gl::TABLE_ROW * sizeof(float4)),
             "surrogate table allocation");
     s->table_rows = B;
   }
@@ -303,20 +303,18 @@ gl_status gl_system_create(const gl_system_desc* d, gl_system** out) {
   cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const size_t static_smem = gl::static_smem_bytes() + 1024;  // static + per-CTA reservation
   size_t budget = (size_t)smem_sm / 2 > static_smem ? (size_t)smem_sm / 2 - static_smem : 0;
-  if (budget + 4096 > (size_t)smem_blk) budget = (size_t)smem_blk > 4096 ? smem_blk - 4096 : 0;
+  if (budget + static_smem > (size_t)smem_blk)
+    budget = (size_t)smem_blk > static_smem ? smem_blk - static_smem : 0;
   const size_t nbuf = align4((size_t)sp.Hp * sp.Wp);
   int bdummy = 0;
   gl::plan_buffers(nbuf, 1, budget, &s->fwd_smem, &s->fwd_A, &bdummy, &s->fwd_slot);
   gl::plan_buffers(nbuf, 2, budget, &s->grad_smem, &s->grad_A, &s->grad_B, &s->grad_slot);
-  // the attribute is per kernel and process-wide: always the device maximum,
-  // so that no system or plan lowers another's limit (it does not change
-  // occupancy, which follows each launch's own size)
-  // (the limit counts dynamic memory only: leave room for the kernels' static
-  // shared memory)
-  const size_t stat = gl::static_smem_bytes();
-  const size_t dyn_max = (size_t)smem_blk > stat ? (size_t)smem_blk - stat : 0;
-  e = gl::set_smem_limits_fwd(dyn_max);
-  if (e == cudaSuccess) e = gl::set_smem_limits_grad(dyn_max);
+  // the attribute is per kernel and process-wide: always the device maximum
+  // (less the kernel's static memory), so that no system or plan lowers
+  // another's limit (it does not change occupancy, which follows each
+  // launch's own size)
+  e = gl::set_smem_limits_fwd((size_t)smem_blk);
+  if (e == cudaSuccess) e = gl::set_smem_limits_grad((size_t)smem_blk);
   if (e != cudaSuccess) return bail(cuda_fail(e, "kernel shared-memory limit"));
   g_last_error.clear();
   *out = s;

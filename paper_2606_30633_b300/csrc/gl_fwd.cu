@@ -21,12 +21,16 @@ cudaError_t launch_forward(const SysParams& sp, const float* theta, int B, float
   return cudaErrorInvalidValue;
 }
 
-size_t static_smem_bytes() {
-  // SmemStatic + the table + k_grad_multi's work index, with alignment slack
-  return sizeof(SmemStatic) + 2 * TABLE_M * sizeof(float4) + 256;
+size_t static_smem_bytes(bool multi) {
+  // SmemStatic + the table (+ k_grad_multi's work index and parameter
+  // block), with alignment slack
+  return sizeof(SmemStatic) + TABLE_ROW * sizeof(float4) + 256 +
+         (multi ? sizeof(SysParams) + 16 : 0);
 }
 
-cudaError_t set_smem_limits_fwd(size_t bytes) {
+cudaError_t set_smem_limits_fwd(size_t block_max) {
+  const size_t st = static_smem_bytes(false);
+  const size_t bytes = block_max > st ? block_max - st : 0;
   cudaError_t e = cudaSuccess;
 #define GL_SET(a, b) \
   if (e == cudaSuccess) e = fwd_smem<a, b>(bytes);

@@ -35,11 +35,15 @@ cudaError_t launch_grad_multi(int nL, int nS, bool surr, const SysParams* system
   return cudaErrorInvalidValue;
 }
 
-cudaError_t set_smem_limits_grad(size_t bytes) {
+cudaError_t set_smem_limits_grad(size_t block_max) {
+  // dynamic limit = the per-block maximum less each kernel's static memory
+  const size_t st = static_smem_bytes(false), sm = static_smem_bytes(true);
+  const size_t bytes = block_max > st ? block_max - st : 0;
+  const size_t bytes_multi = block_max > sm ? block_max - sm : 0;
   cudaError_t e = cudaSuccess;
 #define GL_SET(a, b) \
-  if (e == cudaSuccess) e = grad_smem<a, b, false>(bytes); \
-  if (e == cudaSuccess) e = grad_smem<a, b, true>(bytes);
+  if (e == cudaSuccess) e = grad_smem<a, b, false>(bytes, bytes_multi); \
+  if (e == cudaSuccess) e = grad_smem<a, b, true>(bytes, bytes_multi);
   GL_SET(0, 1) GL_SET(0, 2) GL_SET(0, 3)
   GL_SET(1, 1) GL_SET(1, 2) GL_SET(1, 3)
   GL_SET(2, 1) GL_SET(2, 2) GL_SET(2, 3)

@@ -22,12 +22,12 @@ cudaError_t grad_multi_launch(const SysParams* systems, const void* items, int n
 }
 
 template <int NL, int NS, bool S>
-cudaError_t grad_smem(size_t bytes) {
+cudaError_t grad_smem(size_t bytes, size_t bytes_multi) {
   cudaError_t e =
       cudaFuncSetAttribute(k_grad<NL, NS, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grad_multi<NL, NS, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bytes);
+                             (int)bytes_multi);
   return e;
 }
 
@@ -44,9 +44,9 @@ cudaError_t grad_smem(size_t bytes) {
                                                        int*, int, size_t, cudaStream_t);       \
   EXT template cudaError_t grad_multi_launch<NL, 3, S>(const SysParams*, const void*, int,     \
                                                        int*, int, size_t, cudaStream_t);       \
-  EXT template cudaError_t grad_smem<NL, 1, S>(size_t);                                        \
-  EXT template cudaError_t grad_smem<NL, 2, S>(size_t);                                        \
-  EXT template cudaError_t grad_smem<NL, 3, S>(size_t);
+  EXT template cudaError_t grad_smem<NL, 1, S>(size_t, size_t);                                        \
+  EXT template cudaError_t grad_smem<NL, 2, S>(size_t, size_t);                                        \
+  EXT template cudaError_t grad_smem<NL, 3, S>(size_t, size_t);
 
 #define GL_GRAD_INST(EXT, NL)      \
   GL_GRAD_INST_S(EXT, NL, false)   \

@@ -19,7 +19,8 @@ constexpr int N_MAX = 128;     // EPL series terms for |e| < 0.8 at FP32 toleran
 constexpr int THREADS = 256;   // threads per CTA of the fused kernels
 constexpr int NWARPS = THREADS / 32;
 constexpr int ROWS_STRIP = 8;  // output rows per thread in the unrolled convolution
-constexpr int TABLE_M = 128;   // surrogate angular table points over [0, pi)
+constexpr int TABLE_M = 128;   // surrogate angular table intervals over [0, pi)
+constexpr int TABLE_ROW = 4 * TABLE_M;  // float4 per row's table (4 per interval)
 
 // One prior entry as the kernels see it; cnst is the log normalisation
 // constant, computed once at system creation.
@@ -46,7 +47,7 @@ struct SysParams {
   const PriorDev* prior;   // [P]
   const float* emax;       // [1 + nL + nS]
   float* scratch;          // global scratch base (CTA b uses slot b)
-  const float4* table;     // surrogate tables [B][TABLE_M][2] (null: exact series)
+  const float4* table;     // surrogate tables [B][TABLE_ROW] (null: exact series)
   float sq_lo, sq_hi, sg_lo, sg_hi;  // surrogate domain in q and gamma
   float kconv[MAX_K * MAX_K];  // flipped PSF: m = correlate(b_pad, kconv)
   float kcorr[MAX_K * MAX_K];  // PSF: adjoint = correlate(g_pad, kcorr)
@@ -75,14 +76,16 @@ cudaError_t launch_leapfrog_block(const SysParams& sp, size_t dyn, float* theta,
 cudaError_t launch_grad_multi(int nL, int nS, bool surr, const SysParams* systems,
                               const void* items, int n_items, int* counter, int grid, size_t dyn,
                               cudaStream_t st);
-// Surrogate tables [B][TABLE_M][2] for the rows of theta (gl_surrogate.cu).
+// Surrogate tables [B][TABLE_ROW] for the rows of theta (gl_surrogate.cu).
 cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B, float4* table,
                          cudaStream_t st);
 void surrogate_domain(const gl_surrogate* s, float* q_lo, float* q_hi, float* g_lo, float* g_hi);
 // Largest static shared memory of the forward and gradient kernels (bytes,
-// with the surrogate table).
-size_t static_smem_bytes();
-cudaError_t set_smem_limits_fwd(size_t bytes);
-cudaError_t set_smem_limits_grad(size_t bytes);
+// with the surrogate table), or of the multi-system kernel.
+size_t static_smem_bytes(bool multi = false);
+// Sets the kernels' dynamic shared-memory limit from the device's per-block
+// maximum (each kernel's own static memory deducted).
+cudaError_t set_smem_limits_fwd(size_t block_max);
+cudaError_t set_smem_limits_grad(size_t block_max);
 
 }  // namespace gl

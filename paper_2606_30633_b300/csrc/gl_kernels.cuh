@@ -24,7 +24,9 @@ namespace gl {
 // Each thread computes ROWS_STRIP outputs of one column; lanes own adjacent
 // columns (conflict-free loads); taps are compile-time indices into the
 // kernel's parameter block.
-template <int K, bool CONV, class Epi>
+// RELOAD (parameter block in shared memory): the taps are re-read for every
+// strip instead of being hoisted into registers.
+template <int K, bool CONV, bool RELOAD, class Epi>
 __device__ __forceinline__ void correlate_fixed(const SysParams& sp, const float* in, Epi epi) {
   constexpr int RS = ROWS_STRIP;
   const int ny = sp.ny, nx = sp.nx, Wp = sp.Wp;
@@ -38,6 +40,7 @@ __device__ __forceinline__ void correlate_fixed(const SysParams& sp, const float
 #pragma unroll
     for (int r = 0; r < RS; ++r) acc[r] = 0.f;
     const float* base = in + (size_t)i0 * Wp + j;
+    const SysParams& spk = RELOAD ? reload(sp) : sp;
 #pragma unroll
     for (int v = 0; v < K; ++v) {
       float col[RS + K - 1];
@@ -45,7 +48,7 @@ __device__ __forceinline__ void correlate_fixed(const SysParams& sp, const float
       for (int m = 0; m < RS + K - 1; ++m) col[m] = base[m * Wp + v];
 #pragma unroll
       for (int u = 0; u < K; ++u) {
-        const float kv = CONV ? sp.kconv[u * K + v] : sp.kcorr[u * K + v];
+        const float kv = CONV ? spk.kconv[u * K + v] : spk.kcorr[u * K + v];
 #pragma unroll
         for (int r = 0; r < RS; ++r) acc[r] = fmaf(kv, col[u + r], acc[r]);
       }
@@ -71,12 +74,12 @@ __device__ __forceinline__ void correlate_generic(const SysParams& sp, const flo
   }
 }
 
-template <bool CONV, class Epi>
+template <bool CONV, bool RELOAD = false, class Epi>
 __device__ __forceinline__ void correlate(const SysParams& sp, const float* in, Epi epi) {
   if (sp.ky == 11 && sp.kx == 11)
-    correlate_fixed<11, CONV>(sp, in, epi);
+    correlate_fixed<11, CONV, RELOAD>(sp, in, epi);
   else if (sp.ky == 21 && sp.kx == 21)
-    correlate_fixed<21, CONV>(sp, in, epi);
+    correlate_fixed<21, CONV, RELOAD>(sp, in, epi);
   else
     correlate_generic<CONV>(sp, in, epi);
 }
@@ -282,7 +285,7 @@ __device__ __forceinline__ void adjoint_pixels(const SysParams& sp, const Sample
 template <bool SURR>
 __device__ __forceinline__ void load_table(const float4* src, const SampleC& sc, float4* tab) {
   if (SURR && sc.use_table) {
-    for (int k = threadIdx.x; k < 2 * TABLE_M; k += THREADS) tab[k] = src[k];
+    for (int k = threadIdx.x; k < TABLE_ROW; k += THREADS) tab[k] = src[k];
   }
   __syncthreads();
 }
@@ -294,7 +297,7 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
           float* __restrict__ logp, float* __restrict__ img) {
   extern __shared__ __align__(16) float dsm[];
   __shared__ SmemStatic st;
-  __shared__ float4 tab[SURR ? 2 * TABLE_M : 1];
+  __shared__ float4 tab[SURR ? TABLE_ROW : 1];
   SampleC& sc = st.sc;
   const int b = blockIdx.x;
   if (b >= B) return;
@@ -315,7 +318,7 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
     }
     return;
   }
-  load_table<SURR>(sp.table + (size_t)blockIdx.x * 2 * TABLE_M, sc, tab);
+  load_table<SURR>(sp.table + (size_t)blockIdx.x * TABLE_ROW, sc, tab);
   if (SURR && sc.use_table)
     bin_pixels<NL, NS, true>(sp, sc, tab, A);
   else
@@ -344,7 +347,7 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
 // d log p / d theta of theta row th into *logp_out and grad_out[0..P).
 // slot_index picks the CTA's global-scratch slot, table_row the row's table.
 // Ends with a block barrier, so a persistent CTA can start its next row.
-template <int NL, int NS, bool SURR>
+template <int NL, int NS, bool SURR, bool MULTI = false>
 __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __restrict__ th,
                                          float* __restrict__ logp_out,
                                          float* __restrict__ grad_out,
@@ -381,7 +384,7 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
   __syncthreads();
   // phase 2
   float csum = 0.f, ccomp = 0.f;
-  correlate<true>(sp, A, [&](int i, int j, float m) {
+  correlate<true, MULTI>(sp, A, [&](int i, int j, float m) {
     const int idx = i * nx + j;
     const float r = sp.data[idx] - m;
     const float wr = sp.w[idx] * r;
@@ -395,7 +398,7 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
   // (block_sum_double synchronised the block: phase 2 is complete)
   // phase 3
   const float scale = sp.scale;
-  correlate<false>(sp, Bf, [&](int i, int j, float g) {
+  correlate<false, MULTI>(sp, Bf, [&](int i, int j, float g) {
     A[(size_t)(i + cy) * Wp + j + cx] = g * scale;
   });
   __syncthreads();
@@ -438,33 +441,39 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
   constexpr int P = 8 + 7 * (NL + NS);
   extern __shared__ __align__(16) float dsm[];
   __shared__ SmemStatic st;
-  __shared__ float4 tab[SURR ? 2 * TABLE_M : 1];
+  __shared__ float4 tab[SURR ? TABLE_ROW : 1];
   const int b = blockIdx.x;
   if (b >= B) return;
   grad_row<NL, NS, SURR>(sp, theta + (size_t)b * P, logp + b, grad + (size_t)b * P,
-                         SURR ? sp.table + (size_t)b * 2 * TABLE_M : nullptr, b, dsm, st, tab);
+                         SURR ? sp.table + (size_t)b * TABLE_ROW : nullptr, b, dsm, st, tab);
 }
 
 // Persistent forward + adjoint over uneven multi-system batches: each CTA
 // takes items from a global counter, heaviest first (the host sorts them by
 // cost), and uses its own global-scratch slot. counter must be 0 at launch.
 template <int NL, int NS, bool SURR>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 2)
 k_grad_multi(const SysParams* __restrict__ systems, const MultiItem* __restrict__ items,
              int n_items, int* __restrict__ counter) {
   extern __shared__ __align__(16) float dsm[];
   __shared__ SmemStatic st;
-  __shared__ float4 tab[SURR ? 2 * TABLE_M : 1];
+  __shared__ float4 tab[SURR ? TABLE_ROW : 1];
   __shared__ int next;
+  __shared__ SysParams sps;  // the item's parameter block
   for (;;) {
     if (threadIdx.x == 0) next = atomicAdd(counter, 1);
     __syncthreads();
     const int it = next;
-    __syncthreads();
     if (it >= n_items) break;
     const MultiItem m = items[it];
-    grad_row<NL, NS, SURR>(systems[m.sys], m.theta, m.logp, m.grad, m.table, blockIdx.x, dsm, st,
-                           tab);
+    {
+      const int* src = reinterpret_cast<const int*>(systems + m.sys);
+      int* dst = reinterpret_cast<int*>(&sps);
+      for (int k = threadIdx.x; k < (int)(sizeof(SysParams) / sizeof(int)); k += THREADS)
+        dst[k] = src[k];
+    }
+    __syncthreads();
+    grad_row<NL, NS, SURR, true>(sps, m.theta, m.logp, m.grad, m.table, blockIdx.x, dsm, st, tab);
   }
 }
 

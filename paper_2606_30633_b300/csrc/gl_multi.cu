@@ -85,7 +85,7 @@ gl_status gl_multi_create(gl_system* const* systems, int n_sys, const int* rows_
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device);
   cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device);
-  const size_t stat = gl::static_smem_bytes();
+  const size_t stat = gl::static_smem_bytes(true);
   const size_t reserve = stat + 1024;  // static shared memory (with the table) + system reserve
   if ((size_t)smem_blk <= reserve) return bail(fail(GL_ECUDA, "device shared memory too small"));
   size_t budget = 0;
@@ -148,7 +148,7 @@ gl_status gl_multi_create(gl_system* const* systems, int n_sys, const int* rows_
   if (slot && cudaMalloc(&m->scratch, (size_t)m->grid * slot * sizeof(float)) != cudaSuccess)
     return bail(fail(GL_ENOMEM, "multi scratch allocation"));
   for (auto& sp : m->h_sys) sp.scratch = m->scratch;
-  if (gl::set_smem_limits_grad((size_t)smem_blk - stat) != cudaSuccess)
+  if (gl::set_smem_limits_grad((size_t)smem_blk) != cudaSuccess)
     return bail(fail(GL_ECUDA, "kernel shared-memory limit"));
   *out = m;
   return GL_OK;
@@ -174,14 +174,14 @@ gl_status gl_multi_logp_grad(gl_multi* m, const float* const* theta, float* cons
   const bool surr = defl != GL_DEFL_SERIES;
   if (surr) {
     if (!m->d_table)
-      MU_CUDA(cudaMalloc(&m->d_table, std::max<size_t>(m->total_rows, 1) * 2 * gl::TABLE_M *
+      MU_CUDA(cudaMalloc(&m->d_table, std::max<size_t>(m->total_rows, 1) * gl::TABLE_ROW *
                                           sizeof(float4)),
               "table allocation");
     for (int k = 0; k < n_sys; ++k) {
       if (!m->counts[k]) continue;
       const gl_surrogate* src = defl == GL_DEFL_TABLE ? nullptr : m->systems[k]->sur;
       MU_CUDA(gl::launch_table(src, theta[k], m->h_sys[k].P, m->counts[k],
-                               m->d_table + m->row_offset[k] * 2 * gl::TABLE_M, st),
+                               m->d_table + m->row_offset[k] * gl::TABLE_ROW, st),
               "table launch");
     }
   }
@@ -223,7 +223,7 @@ gl_status gl_multi_logp_grad(gl_multi* m, const float* const* theta, float* cons
           it[n].theta = theta[k] + (size_t)r * P;
           it[n].logp = logp[k] + r;
           it[n].grad = grad[k] + (size_t)r * P;
-          it[n].table = surr ? m->d_table + (m->row_offset[k] + r) * 2 * gl::TABLE_M : nullptr;
+          it[n].table = surr ? m->d_table + (m->row_offset[k] + r) * gl::TABLE_ROW : nullptr;
         }
       }
       MU_CUDA(cudaMemcpyAsync(g.d_items, it, n * sizeof(gl::MultiItem), cudaMemcpyHostToDevice, st),

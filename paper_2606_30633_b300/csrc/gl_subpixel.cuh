@@ -121,45 +121,62 @@ __device__ __forceinline__ void clenshaw_ET(const float2* __restrict__ cE,
 }
 
 // ------------------------------------------------- surrogate table lookup ----
-// Table of row b: TABLE_M nodes uniform in the pseudo-angle
+// Table of row b: TABLE_M intervals uniform in the pseudo-angle
 //   pa = 1 - cos(vphi) / (|cos(vphi)| + sin(vphi)),  vphi folded into [0, pi)
 // (F has period pi in vphi; pa is monotonic, in [0, 2), with
-// d pa / d vphi = 1 / (|cos| + sin)^2), two float4 per node:
-// (F, dF/dpa) and (dF/dq, dF/dt). Cubic Hermite interpolation in pa for F and
-// its derivative, linear for the rest. One point (the gathers are per lane).
+// d pa / d vphi = 1 / (|cos| + sin)^2). Interval j holds four float4 (in
+// four arrays of TABLE_M): the cubic F(t) = a + b t + c t^2 + d t^3 in the
+// local coordinate t = pa TABLE_M/2 - j as (a, b), (c, d), then
+// (dF/dq, dF/dt) at its start and their change across it (linear in t).
 struct TabF {
   float Fr, Fi, Pr, Pi, Qr, Qi, Tr, Ti;  // F, dF/dvphi, dF/dq, dF/dt
 };
+
 template <bool DERIV>
-__device__ __forceinline__ TabF table_eval(const float4* __restrict__ tab, float cph, float sph) {
-  const float fl = sph < 0.f ? -1.f : 1.f;  // fold vphi into [0, pi)
-  const float c = cph * fl, sn = sph * fl;
-  const float rd = rcp(fmaxf(fabsf(c) + sn, 1e-20f));  // 0 only at the clamped centre
-  const float pa = fmaf(-c, rd, 1.f);
-  const float u = pa * (0.5f * TABLE_M);
-  const int i0 = min((int)u, TABLE_M - 1);
-  const float t = u - (float)i0;
-  const int i1 = (i0 + 1) & (TABLE_M - 1);
-  const float4 a0 = tab[2 * i0], a1 = tab[2 * i1];
-  const float h = 2.f / TABLE_M;
-  const float t2 = t * t, omt = 1.f - t;
-  const float h00 = (1.f + 2.f * t) * omt * omt, h10 = t * omt * omt;
-  const float h01 = t2 * (3.f - 2.f * t), h11 = t2 * (t - 1.f);
+__device__ __forceinline__ TabF table_interval(const float4* __restrict__ tab, int j, float t,
+                                               float k) {
+  const float4 p0 = tab[j], p1 = tab[TABLE_M + j];
   TabF o;
-  o.Fr = h00 * a0.x + h01 * a1.x + h * (h10 * a0.z + h11 * a1.z);
-  o.Fi = h00 * a0.y + h01 * a1.y + h * (h10 * a0.w + h11 * a1.w);
+  o.Fr = fmaf(t, fmaf(t, fmaf(t, p1.z, p1.x), p0.z), p0.x);
+  o.Fi = fmaf(t, fmaf(t, fmaf(t, p1.w, p1.y), p0.w), p0.y);
   if (DERIV) {
-    const float d00 = 6.f * (t2 - t) / h, d10 = 3.f * t2 - 4.f * t + 1.f, d11 = 3.f * t2 - 2.f * t;
-    const float k = rd * rd;  // d pa / d vphi
-    o.Pr = k * (d00 * (a0.x - a1.x) + d10 * a0.z + d11 * a1.z);
-    o.Pi = k * (d00 * (a0.y - a1.y) + d10 * a0.w + d11 * a1.w);
-    const float4 b0 = tab[2 * i0 + 1], b1 = tab[2 * i1 + 1];
-    o.Qr = omt * b0.x + t * b1.x;
-    o.Qi = omt * b0.y + t * b1.y;
-    o.Tr = omt * b0.z + t * b1.z;
-    o.Ti = omt * b0.w + t * b1.w;
+    // dF/dvphi = (b + 2c t + 3d t^2) (TABLE_M/2) (d pa / d vphi) = (...) k
+    const float t3 = 3.f * t;
+    o.Pr = k * fmaf(t, fmaf(t3, p1.z, p1.x + p1.x), p0.z);
+    o.Pi = k * fmaf(t, fmaf(t3, p1.w, p1.y + p1.y), p0.w);
+    const float4 g0 = tab[2 * TABLE_M + j], g1 = tab[3 * TABLE_M + j];
+    o.Qr = fmaf(t, g1.x, g0.x);
+    o.Qi = fmaf(t, g1.y, g0.y);
+    o.Tr = fmaf(t, g1.z, g0.z);
+    o.Ti = fmaf(t, g1.w, g0.w);
   }
   return o;
+}
+
+// Table values at two points (e^{i vphi} = cph + i sph per lane). The
+// interval index comes from rounding in the float format: (u + 1/2) + 2^23
+// holds round(u + 1/2) = floor(u) + 1 in its low mantissa bits (ties land on
+// a neighbouring interval at t = 0 or 1, the same point; u = TABLE_M and a
+// rounding below 0 wrap through the periodic table).
+template <bool DERIV>
+__device__ __forceinline__ void table_eval2(const float4* __restrict__ tab, const Geo2& g,
+                                            TabF& o0, TabF& o1) {
+  // fold vphi into [0, pi): nc = -cos, sn = |sin| of the folded angle
+  const float2 nsgn = make_float2(g.sph.x < 0.f ? 1.f : -1.f, g.sph.y < 0.f ? 1.f : -1.f);
+  const float2 nc = mul2(g.cph, nsgn);
+  const float2 rd = make_float2(rcp(fmaxf(fabsf(nc.x) + fabsf(g.sph.x), 1e-20f)),
+                                rcp(fmaxf(fabsf(nc.y) + fabsf(g.sph.y), 1e-20f)));
+  constexpr float HM = 0.5f * TABLE_M;
+  const float2 rdm = mul2(rd, f2(HM));
+  const float2 u = fma2(nc, rdm, f2(HM));  // pa TABLE_M/2
+  const float2 v = add2(add2(u, f2(0.5f)), f2(8388608.f));
+  const float2 t = fma2(add2(v, f2(-8388609.f)), f2(-1.f), u);  // u - (floor(u))
+  const int j0 = (__float_as_int(v.x) - 1) & (TABLE_M - 1);
+  const int j1 = (__float_as_int(v.y) - 1) & (TABLE_M - 1);
+  float2 k = f2(0.f);
+  if (DERIV) k = mul2(rd, rdm);  // (TABLE_M/2) d pa / d vphi
+  o0 = table_interval<DERIV>(tab, j0, t.x, k.x);
+  o1 = table_interval<DERIV>(tab, j1, t.y, k.y);
 }
 
 // ------------------------------------------------------ forward pieces ----
@@ -209,8 +226,8 @@ template <bool TAB>
 __device__ __forceinline__ void deflection_F(const SampleC& sc, const float4* tab, const Geo2& g,
                                              float2& Fr, float2& Fi) {
   if (TAB) {
-    const TabF t0 = table_eval<false>(tab, g.cph.x, g.sph.x);
-    const TabF t1 = table_eval<false>(tab, g.cph.y, g.sph.y);
+    TabF t0, t1;
+    table_eval2<false>(tab, g, t0, t1);
     Fr = make_float2(t0.Fr, t1.Fr);
     Fi = make_float2(t0.Fi, t1.Fi);
   } else {
@@ -316,8 +333,7 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
   float2 Fr, Fi, Er, Ei, dtFr, dtFi, zi, nzi;  // dtF = dF/dt
   TabF t0, t1;
   if (TAB) {
-    t0 = table_eval<true>(tab, g.cph.x, g.sph.x);
-    t1 = table_eval<true>(tab, g.cph.y, g.sph.y);
+    table_eval2<true>(tab, g, t0, t1);
     Fr = make_float2(t0.Fr, t1.Fr);
     Fi = make_float2(t0.Fi, t1.Fi);
   } else {

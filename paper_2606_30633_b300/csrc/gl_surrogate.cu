@@ -445,11 +445,38 @@ __device__ __forceinline__ void table_node(int j, float& vphi, float& dvdpa) {
   dvdpa = d * d;
 }
 
+// Writes a row's interval table from its node values (node j: (F, dF/dpa)
+// and (dF/dq, dF/dt), complex, in shared memory). Interval j covers pa in
+// [pa_j, pa_j + h), h = 2/TABLE_M, with local t = (pa - pa_j)/h, and holds
+//   (a, b), (c, d):  F(t) = a + b t + c t^2 + d t^3, the cubic Hermite
+//                    through nodes j and j+1 (the nodes are periodic);
+//   G0, G1 - G0:     (dF/dq, dF/dt) at node j and its change to node j+1,
+// stored as four arrays of TABLE_M float4 (lanes reading different intervals
+// then hit different shared-memory banks).
+__device__ void write_intervals(const float4 (*node)[2], float4* __restrict__ out) {
+  const float h = 2.f / TABLE_M;
+  for (int j = threadIdx.x; j < TABLE_M; j += blockDim.x) {
+    const int k = (j + 1) & (TABLE_M - 1);
+    const float4 n0 = node[j][0], n1 = node[k][0];
+    const float ar = n0.x, ai = n0.y, br = h * n0.z, bi = h * n0.w;
+    const float er = h * n1.z, ei = h * n1.w;  // h dF/dpa at node j+1
+    const float dr = n1.x - n0.x, di = n1.y - n0.y;
+    const float cr = 3.f * dr - 2.f * br - er, ci = 3.f * di - 2.f * bi - ei;
+    const float d3r = br + er - 2.f * dr, d3i = bi + ei - 2.f * di;
+    const float4 m0 = node[j][1], m1 = node[k][1];
+    out[j] = make_float4(ar, ai, br, bi);
+    out[TABLE_M + j] = make_float4(cr, ci, d3r, d3i);
+    out[2 * TABLE_M + j] = m0;
+    out[3 * TABLE_M + j] = make_float4(m1.x - m0.x, m1.y - m0.y, m1.z - m0.z, m1.w - m0.w);
+  }
+}
+
 // Per-sample tables for the lens kernels from the network: for row b with EPL
-// axis ratio q and slope gamma, node j holds (F, dF/dpa, dF/dq, dF/dt) as 4
+// axis ratio q and slope gamma, node j takes (F, dF/dpa, dF/dq, dF/dt) as 4
 // complex numbers, from the network at R = theta_E with forward-mode
-// derivatives. One CTA (8 warps x 16 nodes) per row; rows outside the
-// training domain are skipped (the lens kernels use the exact series there).
+// derivatives, and the row's intervals follow from the nodes. One CTA
+// (8 warps x 16 nodes) per row; rows outside the training domain are skipped
+// (the lens kernels use the exact series there).
 __global__ void k_table(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
                         const float* __restrict__ theta, int P, int B, float q_lo, float q_hi,
                         float g_lo, float g_hi, float4* __restrict__ table) {
@@ -471,17 +498,20 @@ __global__ void k_table(const __nv_bfloat16* __restrict__ wb, const float* __res
                              {0.f, 1.f / 0.3f, 0.f, 0.f}};
   float y[4], dy[3][4];
   for (int s = 0; s < 3; ++s) forward_jvp(wb, params, x[0], x[1], seeds[s], seeds[s], y, dy[s]);
+  __shared__ float4 node[TABLE_M][2];
   if (c == 0)
     for (int h = 0; h < 2; ++h) {
       const int j = warp * 16 + g + 8 * h;
       const Base bt = base_terms(q, gamma - 1.f, vp[h]);
       const float k = 1.f / OUT_SCALE;
-      float4* out = table + ((size_t)b * TABLE_M + j) * 2;
-      out[0] = make_float4(bt.Fr + k * y[2 * h], bt.Fi + k * y[2 * h + 1],
-                           dv[h] * (bt.Pr + k * dy[0][2 * h]), dv[h] * (bt.Pi + k * dy[0][2 * h + 1]));
-      out[1] = make_float4(bt.Qr + k * dy[1][2 * h], bt.Qi + k * dy[1][2 * h + 1],
-                           bt.Tr + k * dy[2][2 * h], bt.Ti + k * dy[2][2 * h + 1]);
+      node[j][0] = make_float4(bt.Fr + k * y[2 * h], bt.Fi + k * y[2 * h + 1],
+                               dv[h] * (bt.Pr + k * dy[0][2 * h]),
+                               dv[h] * (bt.Pi + k * dy[0][2 * h + 1]));
+      node[j][1] = make_float4(bt.Qr + k * dy[1][2 * h], bt.Qi + k * dy[1][2 * h + 1],
+                               bt.Tr + k * dy[2][2 * h], bt.Ti + k * dy[2][2 * h + 1]);
     }
+  __syncthreads();
+  write_intervals(node, table + (size_t)b * TABLE_ROW);
 }
 
 // The same tables from the exact series (FP64 per node): F, dF/dvphi =
@@ -498,6 +528,7 @@ __global__ void k_table_exact(const float* __restrict__ theta, int P, int B, flo
   const float qf = (1.f - cc) / (1.f + cc);
   if (!(qf >= q_lo) || !(th[1] > 1.f && th[1] < 3.f)) return;
   const double q = qf, t = (double)th[1] - 1.0, f = (1.0 - q) / (1.0 + q);
+  __shared__ float4 node[TABLE_M][2];
   for (int j = threadIdx.x; j < TABLE_M; j += blockDim.x) {
     float vpf, dv;
     table_node(j, vpf, dv);
@@ -525,10 +556,11 @@ __global__ void k_table_exact(const float* __restrict__ theta, int P, int B, flo
     const double Pr = -2.0 * (Dr * zi + Di * zr), Pi = 2.0 * (Dr * zr - Di * zi);  // F' 2iz
     const double dfdq = -2.0 / ((1.0 + q) * (1.0 + q));
     const double Qr = -(Dr * wr - Di * wi) * dfdq, Qi = -(Dr * wi + Di * wr) * dfdq;
-    float4* out = table + ((size_t)b * TABLE_M + j) * 2;
-    out[0] = make_float4((float)Fr, (float)Fi, (float)(dv * Pr), (float)(dv * Pi));
-    out[1] = make_float4((float)Qr, (float)Qi, (float)Tr, (float)Ti);
+    node[j][0] = make_float4((float)Fr, (float)Fi, (float)(dv * Pr), (float)(dv * Pi));
+    node[j][1] = make_float4((float)Qr, (float)Qi, (float)Tr, (float)Ti);
   }
+  __syncthreads();
+  write_intervals(node, table + (size_t)b * TABLE_ROW);
 }
 
 cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B, float4* table,
