@@ -235,7 +235,8 @@ def learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world) -
             "train_seconds": train_s, "train_final_loss": sur.final_loss,
             "exact_series_tables_evals_per_s": out["exact_tables"],
             "note": "speed-up comes from tabulating F per row; the exact series tabulated the "
-                    "same way (exact_series_tables) is as fast"}
+                    "same way (exact_series_tables) is nearly as fast (its FP64 table build "
+                    "costs more than the network's)"}
 
 
 def cpu_baseline_leg(budget_s: float = 12.0) -> dict:
@@ -581,7 +582,8 @@ def run_uneven(args) -> dict | None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 50; 20 for space200-leapfrog, about 40 s)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -590,6 +592,8 @@ def main():
     ap.add_argument("--workload", choices=["ground100", "space200-leapfrog", "uneven"],
                     default="ground100")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 20 if args.workload == "space200-leapfrog" else 50
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
