@@ -296,6 +296,134 @@ void gl_surrogate_destroy(gl_surrogate* sur);
  * use of GL_DEFL_SURROGATE); NULL detaches. */
 gl_status gl_system_set_surrogate(gl_system* sys, const gl_surrogate* sur);
 
+/* ------------------------------------------------------------------------
+ * Inference layer (Sec. 3): the MAP, SVI and HMC stages work on an
+ * unconstrained vector u, mapped to the parameters by a bijection theta(u)
+ * ("mapped into an unconstrained space via a bijective transformation",
+ * Sec. 3.1). The paper defers the map to its earlier release; this library
+ * takes one map per prior support:
+ *   normal, or flat on R        theta = u
+ *   uniform, truncated normal,
+ *   flat on [lo, hi]            theta = lo + (hi - lo) sigmoid(u)
+ *   log-normal                  theta = exp(u)
+ *   flat on [lo, inf) / (-inf, hi]   theta = lo + exp(u) / hi - exp(u)
+ * and, for a component whose ellipticity is restricted to |e| < emax while
+ * both e priors are unbounded, the radial map e = v emax tanh(|v|)/|v|.
+ * log p~(u) = log p(theta(u)) + log|det d theta/d u|. All arrays below are
+ * device arrays in row-major [B][P] (u, theta, gradients) or [B] (log p, log
+ * |J|), unless marked host. Calls are asynchronous on the stream.
+ * ------------------------------------------------------------------------ */
+
+/* theta(u) and log|det d theta/d u| (logdetj may be NULL). */
+gl_status gl_bijector_forward(gl_system* sys, const float* u, int B, float* theta,
+                              float* logdetj, void* stream);
+
+/* u(theta), the inverse map; theta must lie inside the support (rows outside
+ * give NaN or infinite u). */
+gl_status gl_bijector_inverse(gl_system* sys, const float* theta, int B, float* u, void* stream);
+
+/* log p~(u) and its gradient d log p~/d u = J^T grad_theta log p + grad log|J|
+ * (three launches: the map, the fused log p + gradient kernel, the
+ * pull-back). Rows whose log p is -inf/NaN keep it, with a zero/NaN gradient. */
+gl_status gl_logp_grad_unconstrained(gl_system* sys, const float* u, int B, float* logp,
+                                     float* grad, gl_deflection defl, void* stream);
+
+/* Multi-start MAP (Sec. 3.1: every particle descends independently): n_steps
+ * of Adam (Kingma & Ba 2015) on each row of u, maximising log p~(u), in place.
+ *   m, v     Adam moments [B][P]: zeros for a fresh start, or the state a
+ *            previous call left (with t0 = the steps already taken);
+ *   lr, beta1, beta2, eps   Adam's hyper-parameters (the step is
+ *            lr m^/(sqrt(v^) + eps));
+ *   logp     [B]: log p~ at the last point evaluated (before the last update).
+ * Each step is one gradient evaluation and one fused pull-back + update
+ * kernel; the n_steps run as one CUDA graph launch, captured on a private
+ * stream and re-captured when a pointer, n_steps, B or the deflection changes
+ * (t0 and the hyper-parameters are read from device memory). Do not call
+ * while the calling thread is capturing a stream. */
+gl_status gl_map_adam(gl_system* sys, float* u, float* m, float* v, int B, int n_steps, int t0,
+                      float lr, float beta1, float beta2, float eps, float* logp,
+                      gl_deflection defl, void* stream);
+
+/* HMC sampler (the pipeline's sampling stage, Sec. 3): B independent chains
+ * on log p~(u), each transition a leapfrog trajectory of n_leapfrog steps with
+ * diagonal inverse mass M^-1 and a Metropolis-Hastings accept/reject.
+ * Momenta and acceptance draws come from SplitMix64 (Steele et al. 2014) used
+ * as a counter-based generator: draw j of chain b in transition n takes the
+ * output for state seed + ((n B + b)(2P + 2) + j) * 0x9E3779B97F4A7C15, whose
+ * top 24 bits k give the uniform (k + 1/2) 2^-24; momentum k is Box-Muller on
+ * draws 2k (radius) and 2k + 1 (angle), scaled by sqrt(M); draw 2P is the
+ * acceptance uniform a, and the chain moves when log a < min(0, H0 - H1),
+ * H = -log p~ + p^T M^-1 p / 2 (a non-finite H1 rejects). Everything stays on
+ * the device: one CUDA graph per transition, no host synchronisation. */
+typedef struct gl_hmc gl_hmc;
+
+typedef struct {
+  int chains;                    /* B >= 1                                    */
+  int n_leapfrog;                /* leapfrog steps per transition, >= 1       */
+  float step_size;               /* initial step size eps > 0                 */
+  float target_accept;           /* dual-averaging target, in (0, 1)          */
+  unsigned long long seed;       /* generator seed                            */
+  int deflection;                /* gl_deflection of the gradient evaluations */
+} gl_hmc_desc;
+
+/* Flags of gl_hmc_run. */
+enum {
+  GL_HMC_ADAPT_STEP = 1,      /* dual-averaging step size (Hoffman & Gelman 2014)
+                                 on the mean acceptance probability over chains */
+  GL_HMC_COLLECT_MOMENTS = 2  /* accumulate per-parameter mean and variance of u
+                                 over chains and transitions (mass adaptation) */
+};
+
+/* Creates a sampler at u0 (device [B][P], copied); M^-1 starts at ones.
+ * Evaluates log p~ and its gradient at u0 on the stream. */
+gl_status gl_hmc_create(gl_system* sys, const gl_hmc_desc* desc, const float* u0,
+                        gl_hmc** out, void* stream);
+
+/* Sets M^-1 (device [P], copied). */
+gl_status gl_hmc_set_inv_mass(gl_hmc* hmc, const float* inv_mass, void* stream);
+
+/* Runs n transitions. draws (device [n][B][P], or NULL) receives theta(u) of
+ * every chain after each transition; accept (device [n], or NULL) the mean
+ * acceptance probability of each transition. */
+gl_status gl_hmc_run(gl_hmc* hmc, int n, int flags, float* draws, float* accept, void* stream);
+
+/* Ends adaptation (Sec. 3.3): the step size becomes the dual-averaging
+ * average; if set_inv_mass, M^-1 becomes the variances collected with
+ * GL_HMC_COLLECT_MOMENTS (the Gaussian fitted to those burn-in samples), and
+ * the collection is cleared. A later GL_HMC_ADAPT_STEP phase restarts the
+ * dual averaging from the new step size (a second burn-in that retunes the
+ * step to the new mass matrix). */
+gl_status gl_hmc_end_adaptation(gl_hmc* hmc, int set_inv_mass, void* stream);
+
+/* Current state: u [B][P], log p~ [B], inv_mass [P] (device, each may be NULL)
+ * and the step size (host, may be NULL; this waits for the stream). */
+gl_status gl_hmc_state(gl_hmc* hmc, float* u, float* logp, float* inv_mass,
+                       float* step_size_host, void* stream);
+
+/* Frees a sampler (waits for the device). NULL is accepted. */
+gl_status gl_hmc_destroy(gl_hmc* hmc);
+
+/* Stochastic variational inference (Sec. 3.1-3.2): n_steps of AdaBelief
+ * (Zhuang et al. 2020) on a full-covariance Gaussian q(u; mu, L L^T), with
+ * the score-function ELBO gradient (Eqs. elbo, elbo-grad) over n_samples draws
+ * per step: u_i = mu + L z_i, z_i ~ N(0, I) from the generator above (draw j
+ * of sample i in step n: state seed + ((n n_samples + i) 2P + j) * gamma),
+ *   ELBO = mean_i w_i,  w_i = log q(u_i) - log p~(u_i),
+ *   grad = mean_i w_i grad log q(u_i),  grad_mu log q = L^-T z,
+ *   grad_L log q = tril(L^-T z z^T) - diag(1/L_ii).
+ * The optimised vector is phi = (mu [P], then L row-major [P][P] with its
+ * diagonal stored as log L_ii); opt is AdaBelief's state [2 (P + P P)] (m then
+ * s; zeros for a fresh start) and t0 the steps already taken; elbo (device
+ * [n_steps], or NULL) receives each step's ELBO estimate. Only log p~ is
+ * evaluated (no gradient): the score-function estimator needs none. Samples
+ * whose log p~ is not finite are left out of the means. One CUDA graph per
+ * step, captured on a private stream (re-captured when a pointer, n_samples
+ * or the deflection changes). */
+gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples, int n_steps,
+                           int t0, float lr, float beta1, float beta2, float eps,
+                           unsigned long long seed, float* elbo, gl_deflection defl,
+                           void* stream);
+
 /* Last failure message on this host thread ("" if none). */
 const char* gl_last_error(void);
 

@@ -82,7 +82,32 @@ SIGNATURES = {
     "gl_multi_create": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(_VP)]),
     "gl_multi_logp_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     "gl_multi_destroy": (ctypes.c_int, [_VP]),
+    "gl_bijector_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
+    "gl_bijector_inverse": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP]),
+    "gl_logp_grad_unconstrained": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int,
+                                                  _VP]),
+    "gl_map_adam": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   _VP, ctypes.c_int, _VP]),
+    "gl_hmc_create": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(_VP), _VP]),
+    "gl_hmc_set_inv_mass": (ctypes.c_int, [_VP, _VP, _VP]),
+    "gl_hmc_run": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    "gl_hmc_end_adaptation": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    "gl_hmc_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_float), _VP]),
+    "gl_hmc_destroy": (ctypes.c_int, [_VP]),
+    "gl_svi_adabelief": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, ctypes.c_ulonglong, _VP, ctypes.c_int,
+                                        _VP]),
 }
+
+GL_HMC_ADAPT_STEP, GL_HMC_COLLECT_MOMENTS = 1, 2
+
+
+class gl_hmc_desc(ctypes.Structure):
+    _fields_ = [("chains", ctypes.c_int), ("n_leapfrog", ctypes.c_int),
+                ("step_size", ctypes.c_float), ("target_accept", ctypes.c_float),
+                ("seed", ctypes.c_ulonglong), ("deflection", ctypes.c_int)]
 
 GL_MULTI_SMEM_GLOBAL, GL_MULTI_SMEM_TWO_CTAS, GL_MULTI_SMEM_ONE_CTA = 0, 1, 2
 
@@ -230,6 +255,85 @@ class System:
                                      _ptr(inv_mass), float(eps), int(n_steps), B,
                                      _stream_ptr(stream)))
 
+    # ---- inference layer (unconstrained parameters u; see include/gl.h) ----
+    def _rows(self, x, name="u"):
+        torch = _torch()
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32):
+            raise TypeError(f"{name} must be a CUDA float32 tensor")
+        x = x.contiguous()
+        if x.dim() != 2 or x.shape[1] != self.P:
+            raise ValueError(f"{name} must be [B, {self.P}]")
+        return x
+
+    def bijector_forward(self, u, stream=None):
+        """theta(u) and log|det d theta/d u| per row."""
+        torch = _torch()
+        u = self._rows(u)
+        B = u.shape[0]
+        th = torch.empty_like(u)
+        lj = torch.empty(B, device=u.device, dtype=torch.float32)
+        _check(self._lib.gl_bijector_forward(self._h, _ptr(u), B, _ptr(th), _ptr(lj),
+                                             _stream_ptr(stream)))
+        return th, lj
+
+    def bijector_inverse(self, theta, stream=None):
+        torch = _torch()
+        theta = self._rows(theta, "theta")
+        u = torch.empty_like(theta)
+        _check(self._lib.gl_bijector_inverse(self._h, _ptr(theta), theta.shape[0], _ptr(u),
+                                             _stream_ptr(stream)))
+        return u
+
+    def logp_grad_unconstrained(self, u, defl: int = GL_DEFL_SERIES, stream=None):
+        """log p~(u) = log p(theta(u)) + log|J| and its gradient w.r.t. u."""
+        torch = _torch()
+        u = self._rows(u)
+        B = u.shape[0]
+        lp = torch.empty(B, device=u.device, dtype=torch.float32)
+        g = torch.empty_like(u)
+        _check(self._lib.gl_logp_grad_unconstrained(self._h, _ptr(u), B, _ptr(lp), _ptr(g), defl,
+                                                    _stream_ptr(stream)))
+        return lp, g
+
+    def map_adam(self, u, m, v, n_steps: int, t0: int = 0, lr: float = 1e-2, beta1: float = 0.9,
+                 beta2: float = 0.999, eps: float = 1e-8, defl: int = GL_DEFL_SERIES,
+                 logp=None, stream=None):
+        """n_steps of Adam on every row of u in place (multi-start MAP); m, v
+        are the Adam moments (zeros for a fresh start). Returns log p~ at the
+        last point evaluated."""
+        torch = _torch()
+        for t in (u, m, v):
+            self._rows(t)
+            if not t.is_contiguous():
+                raise ValueError("u, m and v must be contiguous")
+        B = u.shape[0]
+        logp = torch.empty(B, device=u.device, dtype=torch.float32) if logp is None else logp
+        _check(self._lib.gl_map_adam(self._h, _ptr(u), _ptr(m), _ptr(v), B, int(n_steps),
+                                     int(t0), float(lr), float(beta1), float(beta2), float(eps),
+                                     _ptr(logp), defl, _stream_ptr(stream)))
+        return logp
+
+    def svi_adabelief(self, phi, opt, n_samples: int, n_steps: int, t0: int = 0,
+                      lr: float = 1e-4, beta1: float = 0.95, beta2: float = 0.99,
+                      eps: float = 1e-16, seed: int = 0, defl: int = GL_DEFL_SERIES,
+                      stream=None):
+        """n_steps of SVI (AdaBelief on phi = (mu, L with log diagonal)) in
+        place; opt is AdaBelief's state [2 (P + P^2)]. Returns the per-step
+        ELBO estimates [n_steps]."""
+        torch = _torch()
+        P = self.P
+        if phi.shape != (P + P * P,) or opt.shape != (2 * (P + P * P),):
+            raise ValueError("phi must be [P + P^2] and opt [2 (P + P^2)]")
+        for t in (phi, opt):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise TypeError("phi and opt must be contiguous CUDA float32 tensors")
+        elbo = torch.empty(max(int(n_steps), 1), device=phi.device, dtype=torch.float32)
+        _check(self._lib.gl_svi_adabelief(self._h, _ptr(phi), _ptr(opt), int(n_samples),
+                                          int(n_steps), int(t0), float(lr), float(beta1),
+                                          float(beta2), float(eps), int(seed), _ptr(elbo), defl,
+                                          _stream_ptr(stream)))
+        return elbo[:int(n_steps)]
+
     def logp_grad_noalloc(self, theta, out=None, grad=None, stream=None):
         """gl_logp_grad_noalloc: the same result without any device allocation
         inside the call (fixed library scratch; see include/gl.h)."""
@@ -263,6 +367,68 @@ class System:
         _check(self._lib.gl_model_image(self._h, _ptr(theta), B, _ptr(out), defl,
                                         _stream_ptr(stream)))
         return out
+
+
+class Hmc:
+    """HMC sampler on log p~(u) (gl_hmc_*; see include/gl.h): B chains, each
+    transition a leapfrog trajectory with a Metropolis-Hastings correction,
+    all on the device."""
+
+    def __init__(self, system: System, u0, n_leapfrog: int, step_size: float,
+                 target_accept: float = 0.75, seed: int = 0, defl: int = GL_DEFL_SERIES,
+                 stream=None):
+        self._lib = system._lib
+        self.system = system
+        u0 = system._rows(u0)
+        self.B, self.P = u0.shape[0], system.P
+        desc = gl_hmc_desc(self.B, int(n_leapfrog), float(step_size), float(target_accept),
+                           int(seed), int(defl))
+        h = _VP()
+        _check(self._lib.gl_hmc_create(system._h, ctypes.byref(desc), _ptr(u0), ctypes.byref(h),
+                                       _stream_ptr(stream)))
+        self._h = h
+
+    def set_inv_mass(self, inv_mass, stream=None):
+        _check(self._lib.gl_hmc_set_inv_mass(self._h, _ptr(inv_mass.contiguous()),
+                                             _stream_ptr(stream)))
+
+    def run(self, n: int, flags: int = 0, draws=None, accept=None, stream=None):
+        """n transitions; draws [n, B, P] (theta) and accept [n] are optional
+        CUDA float32 outputs."""
+        torch = _torch()
+        for t, shape in ((draws, (n, self.B, self.P)), (accept, (n,))):
+            if t is not None and (tuple(t.shape) != shape or t.dtype != torch.float32
+                                  or not t.is_cuda or not t.is_contiguous()):
+                raise ValueError(f"output must be a contiguous CUDA float32 tensor {shape}")
+        _check(self._lib.gl_hmc_run(self._h, int(n), int(flags), _ptr(draws), _ptr(accept),
+                                    _stream_ptr(stream)))
+
+    def end_adaptation(self, set_inv_mass: bool = True, stream=None):
+        _check(self._lib.gl_hmc_end_adaptation(self._h, int(bool(set_inv_mass)),
+                                               _stream_ptr(stream)))
+
+    def state(self, stream=None):
+        """(u [B, P], log p~ [B], inv_mass [P], step size) — waits for the stream."""
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        u = torch.empty(self.B, self.P, device=dev)
+        lp = torch.empty(self.B, device=dev)
+        im = torch.empty(self.P, device=dev)
+        eps = ctypes.c_float()
+        _check(self._lib.gl_hmc_state(self._h, _ptr(u), _ptr(lp), _ptr(im), ctypes.byref(eps),
+                                      _stream_ptr(stream)))
+        return u, lp, im, eps.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gl_hmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Multi:

@@ -324,6 +324,7 @@ gl_status gl_system_create(const gl_system_desc* d, gl_system** out) {
 gl_status gl_system_destroy(gl_system* s) {
   if (!s) return GL_OK;
   cudaDeviceSynchronize();
+  gl::infer_release(s);
   if (s->lf_exec) cudaGraphExecDestroy(s->lf_exec);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   cudaFree(s->d_data);
@@ -504,6 +505,56 @@ gl_status gl_logp_grad_host(gl_system* sys, const float* theta_host, int B, floa
 namespace gl {
 // Sets the message gl_last_error() returns on this host thread.
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// Evaluations of B rows for the inference drivers (gl_infer.cu): eval_prepare
+// makes the device ready (current device, global scratch, the table buffer
+// for a surrogate or table deflection) and fills the kernel parameters of the
+// gradient kernel (with_grad) or the log-p-only kernel, allocating nothing
+// after it returns; eval_launch then launches one evaluation (the row tables
+// first, when there are any) and can be captured into a CUDA graph. The
+// parameters stay valid until the system's next call.
+gl_status eval_prepare(gl_system* s, int B, gl_deflection defl, bool with_grad, SysParams* sp,
+                       size_t* dyn) {
+  gl_status r = check_call(s, s, B, s, defl);
+  if (r != GL_OK) return r;
+  if ((r = set_device(s)) != GL_OK) return r;
+  *sp = s->sp;
+  sp->bufA_smem = with_grad ? s->grad_A : s->fwd_A;
+  sp->bufB_smem = with_grad ? s->grad_B : 0;
+  sp->slot_floats = with_grad ? s->grad_slot : s->fwd_slot;
+  sp->table = nullptr;
+  if (sp->slot_floats) {
+    r = ensure_scratch(s, (size_t)B * sp->slot_floats);
+    if (r != GL_OK) return r;
+    sp->scratch = s->scratch;
+  }
+  if (defl != GL_DEFL_SERIES) {
+    if ((size_t)B > s->table_rows) {
+      cudaFree(s->d_table);
+      s->d_table = nullptr;
+      s->table_rows = 0;
+      GL_CUDA(cudaMalloc(&s->d_table, (size_t)B * gl::TABLE_ROW * sizeof(float4)),
+              "surrogate table allocation");
+      s->table_rows = B;
+    }
+    sp->table = s->d_table;
+    gl::surrogate_domain(defl == GL_DEFL_TABLE ? nullptr : s->sur, &sp->sq_lo, &sp->sq_hi,
+                         &sp->sg_lo, &sp->sg_hi);
+  }
+  *dyn = with_grad ? s->grad_smem : s->fwd_smem;
+  return GL_OK;
+}
+
+cudaError_t eval_launch(const gl_system* s, const SysParams& sp, size_t dyn, const float* theta,
+                        int B, float* logp, float* grad, gl_deflection defl, cudaStream_t st) {
+  if (sp.table) {
+    cudaError_t e = gl::launch_table(defl == GL_DEFL_TABLE ? nullptr : s->sur, theta, sp.P, B,
+                                     const_cast<float4*>(sp.table), st);
+    if (e != cudaSuccess) return e;
+  }
+  if (grad) return gl::launch_grad(sp, theta, B, logp, grad, dyn, st);
+  return gl::launch_forward(sp, theta, B, logp, nullptr, dyn, st);
+}
 
 // Read-only view of a system's gradient-kernel plan for other translation
 // units of the library: kernel parameters with buffer placement, dynamic

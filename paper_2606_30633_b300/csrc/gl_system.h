@@ -8,6 +8,10 @@
 #include "../../include/gl.h"
 #include "gl_internal.cuh"
 
+namespace gl {
+struct InferState;  // the inference layer's per-system state (gl_infer.cu)
+}
+
 struct gl_system {
   int device = 0;
   gl::SysParams sp;
@@ -37,6 +41,7 @@ struct gl_system {
     float eps;
     int n_steps, B;
   } lf_key;
+  gl::InferState* inf = nullptr;
 };
 
 namespace gl {
@@ -45,4 +50,6 @@ namespace gl {
 void plan_buffers(size_t buf_floats, int nbufs, size_t smem_budget, size_t* dyn, int* a_smem,
                   int* b_smem, size_t* slot);
 void set_last_error(const std::string& msg);
+// Frees the inference layer's state of a system (gl_infer.cu).
+void infer_release(gl_system* s);
 }  // namespace gl
