@@ -579,6 +579,143 @@ def run_uneven(args) -> dict | None:
     return out
 
 
+def run_pipeline(args) -> dict | None:
+    """The inference stages of the paper's pipeline (Sec. 3) on the
+    ground-based system (100x100 px, s = 3), 4096 rows each, through the
+    library's device-resident drivers: multi-start MAP (Adam, one logp+grad
+    evaluation per row and step), SVI (AdaBelief, 4096 log p~ samples per
+    step, score-function gradient) and HMC (4096 chains, 10-leapfrog
+    transitions with Metropolis-Hastings). The line's value is the HMC
+    throughput in logp+grad evaluations/s; the MAP and SVI figures ride along."""
+    import torch
+    import paper_2606_30633_b300 as gl
+    from paper_2606_30633_b300 import build as glbuild, infer
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    glbuild.build()
+    dev = torch.device("cuda", local)
+    W = synth.ground_100()
+    if args.batch:
+        W.batch = args.batch
+    spec = W.prior()
+    B, L = W.batch, 10
+    blank = gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
+                      np.ones((W.ny, W.nx)), W.psf, 1, 1, spec)
+    truth = W.truth()
+    m = blank.model_image(torch.tensor(truth[None], dtype=torch.float32, device=dev))[0]
+    blank.close()
+    d, sig = synth.noisy_data(m.double().cpu().numpy(), W.noise())
+    S = gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, d, sig, W.psf, 1, 1, spec)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    # MAP from the prior draws
+    u_map = S.bijector_inverse(torch.tensor(W.samples().astype(np.float32), device=dev))
+    mm, vv = torch.zeros_like(u_map), torch.zeros_like(u_map)
+    state = {"t": 0}
+    K = 10
+
+    def map_step():
+        S.map_adam(u_map, mm, vv, K, t0=state["t"], lr=1e-2, stream=stream)
+        state["t"] += K
+
+    map_ms = timed_steps(map_step, max(2, args.steps // 5), args.warmup, stream, flush)
+    map_value = world * B * K / (statistics.mean(map_ms) / 1e3)
+    # SVI around the truth
+    u_true = S.bijector_inverse(torch.tensor(truth[None].astype(np.float32), device=dev))[0]
+    phi, opt = infer.svi_init(S, u_true, scale=1e-3)
+    sv = {"t": 0}
+
+    def svi_step():
+        S.svi_adabelief(phi, opt, B, K, t0=sv["t"], seed=11, stream=stream)
+        sv["t"] += K
+
+    svi_ms = timed_steps(svi_step, max(2, args.steps // 5), args.warmup, stream, flush)
+    svi_value = world * B * K / (statistics.mean(svi_ms) / 1e3)
+    # HMC: chains near the truth, step tuned by a short adaptation first
+    th0 = synth.jitter(truth, spec, B, W.seed_samples, rel=0.002).astype(np.float32)
+    u0 = S.bijector_inverse(torch.tensor(th0, device=dev))
+    h = gl.Hmc(S, u0, L, 1e-3, 0.75, seed=21)
+    h.run(30, gl.GL_HMC_ADAPT_STEP, stream=stream)
+    h.end_adaptation(set_inv_mass=False, stream=stream)
+    acc = torch.empty(args.warmup + args.steps, device=dev)
+    for k in range(args.warmup):
+        flush.zero_()
+        h.run(1, 0, None, acc[k:k + 1], stream=stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k, (a, b) in enumerate(ev):
+            flush.zero_()
+            a.record(stream)
+            h.run(1, 0, None, acc[args.warmup + k:args.warmup + k + 1], stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = world * B * L * args.steps / (t_ms / 1e3)
+    u_end, lp_end, _, eps = h.state()
+    h.close()
+    # end to end: chain starts from pinned host memory, one transition, the
+    # chains' log p~ back to the host
+    h_u = u0.cpu().pin_memory()
+    h_lp = torch.empty(B).pin_memory()
+    e2e_ms = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ud = h_u.to(dev, non_blocking=True)
+        h2 = gl.Hmc(S, ud, L, eps, 0.75, seed=22)
+        h2.run(1, 0, stream=stream)
+        _, lp2, _, _ = h2.state()
+        h_lp.copy_(lp2, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        h2.close()
+    e2e_value = world * B * (L + 1) / (min(e2e_ms) / 1e3)
+    th_end, _ = S.bijector_forward(u_end)
+    ops, _ = algorithmic_ops(th_end.double().cpu().numpy(), W.ny, W.nx, W.supersample,
+                             W.psf.shape[0], 1, 1)
+    peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2.032e9 / 1e12
+    achieved = ops * L / (statistics.mean(step_ms) / 1e3) / 1e12
+    out = None
+    if rank == 0:
+        out = {
+            "metric": "HMC logp+grad evals/s (100x100 px, 3x SS, 4096 chains, 10-leapfrog "
+                      "transitions with Metropolis-Hastings) on 1 B300",
+            "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded priors, library-rendered truth, seeded noise)",
+            "config": {"workload": "pipeline-" + W.name, "chains": B, "leapfrogs": L,
+                       "step_size": eps, "mean_accept": float(acc[args.warmup:].mean()),
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "map": {"value": map_value, "unit": "logp+grad evals/s",
+                    "ms_per_10_steps": statistics.mean(map_ms), "starts": B},
+            "svi": {"value": svi_value, "unit": "logp evals/s",
+                    "ms_per_10_steps": statistics.mean(svi_ms), "samples_per_step": B},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None},
+            "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": B * W.P * 4,
+                    "d2h_bytes_per_step": B * 4},
+            "gpu_launches": (2 + 2 * L + 2) * args.steps,
+            "clocks": clk.summary(),
+        }
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -589,7 +726,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=None,
                     help="rows per step (default: the workload's); for profiling runs")
-    ap.add_argument("--workload", choices=["ground100", "space200-leapfrog", "uneven"],
+    ap.add_argument("--workload", choices=["ground100", "space200-leapfrog", "uneven", "pipeline"],
                     default="ground100")
     args = ap.parse_args()
     if args.steps is None:
@@ -602,6 +739,8 @@ def main():
         res = run_leapfrog(args)
     elif args.workload == "uneven":
         res = run_uneven(args)
+    elif args.workload == "pipeline":
+        res = run_pipeline(args)
     else:
         res = run_ours(args)
     if res is not None:
