@@ -584,9 +584,10 @@ def run_pipeline(args) -> dict | None:
     ground-based system (100x100 px, s = 3), 4096 rows each, through the
     library's device-resident drivers: multi-start MAP (Adam, one logp+grad
     evaluation per row and step), SVI (AdaBelief, 4096 log p~ samples per
-    step, score-function gradient) and HMC (4096 chains, 10-leapfrog
+    step, score-function gradient), backward intensity modelling (4096 rows,
+    intensities by linear inversion) and HMC (4096 chains, 10-leapfrog
     transitions with Metropolis-Hastings). The line's value is the HMC
-    throughput in logp+grad evaluations/s; the MAP and SVI figures ride along."""
+    throughput in logp+grad evaluations/s; the other figures ride along."""
     import torch
     import paper_2606_30633_b300 as gl
     from paper_2606_30633_b300 import build as glbuild, infer
@@ -635,6 +636,11 @@ def run_pipeline(args) -> dict | None:
 
     svi_ms = timed_steps(svi_step, max(2, args.steps // 5), args.warmup, stream, flush)
     svi_value = world * B * K / (statistics.mean(svi_ms) / 1e3)
+    # backward intensities (linear inversion) on the prior draws
+    th_b = torch.tensor(W.samples().astype(np.float32), device=dev)
+    bwd_ms = timed_steps(lambda: S.logp_grad_backward(th_b, stream=stream),
+                         max(2, args.steps // 5), args.warmup, stream, flush)
+    bwd_value = world * B / (statistics.mean(bwd_ms) / 1e3)
     # HMC: chains near the truth, step tuned by a short adaptation first
     th0 = synth.jitter(truth, spec, B, W.seed_samples, rel=0.002).astype(np.float32)
     u0 = S.bijector_inverse(torch.tensor(th0, device=dev))
@@ -704,6 +710,8 @@ def run_pipeline(args) -> dict | None:
                     "ms_per_10_steps": statistics.mean(map_ms), "starts": B},
             "svi": {"value": svi_value, "unit": "logp evals/s",
                     "ms_per_10_steps": statistics.mean(svi_ms), "samples_per_step": B},
+            "backward": {"value": bwd_value, "unit": "logp+grad evals/s (intensities solved)",
+                         "ms_per_step": statistics.mean(bwd_ms), "rows": B},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None},
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": B * W.P * 4,

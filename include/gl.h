@@ -424,6 +424,27 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
                            unsigned long long seed, float* elbo, gl_deflection defl,
                            void* stream);
 
+/* "Backward" intensity modelling (Sec. 3: the light intensities solved by
+ * linear inversion instead of sampled). The model image is linear in the
+ * Sersic intensities, m = sum_k I_k M_k, so per row the intensities that
+ * maximise the likelihood solve (M^T W M) I = M^T W d, W = diag(sigma^-2)
+ * (FP64 sums over the pixels, Cholesky). The paper gives no formula; this
+ * library takes:
+ *   theta      [B][P]; its intensity entries (index 8 + 7c + 6 of light
+ *              component c, lens lights first) are ignored;
+ *   logp       [B]: the log-likelihood at the solved intensities plus the log
+ *              prior of the other parameters (intensities carry no prior and
+ *              may come out negative);
+ *   grad       [B][P]: d logp / d theta of the other parameters, the ordinary
+ *              gradient at the solved intensities (the likelihood's intensity
+ *              derivative vanishes there), and 0 in the intensity entries;
+ *   intensity  [B][n_lens_light + n_source] or NULL: the solved intensities.
+ * A row whose normal matrix is singular (a component with no light in the
+ * image) gets all intensities 0. Cost per row: n_lens_light + n_source image
+ * renders and one fused log p + gradient evaluation. */
+gl_status gl_logp_grad_backward(gl_system* sys, const float* theta, int B, float* logp,
+                                float* grad, float* intensity, gl_deflection defl, void* stream);
+
 /* Last failure message on this host thread ("" if none). */
 const char* gl_last_error(void);
 

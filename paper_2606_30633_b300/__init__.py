@@ -95,6 +95,8 @@ SIGNATURES = {
     "gl_hmc_end_adaptation": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "gl_hmc_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_float), _VP]),
     "gl_hmc_destroy": (ctypes.c_int, [_VP]),
+    "gl_logp_grad_backward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_int,
+                                             _VP]),
     "gl_svi_adabelief": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_float, ctypes.c_ulonglong, _VP, ctypes.c_int,
@@ -333,6 +335,20 @@ class System:
                                           float(beta2), float(eps), int(seed), _ptr(elbo), defl,
                                           _stream_ptr(stream)))
         return elbo[:int(n_steps)]
+
+    def logp_grad_backward(self, theta, defl: int = GL_DEFL_SERIES, stream=None):
+        """Backward intensity modelling: (log p, gradient, solved intensities
+        [B, n_lens_light + n_source]); theta's intensity entries are ignored."""
+        torch = _torch()
+        theta = self._theta(theta)
+        B = theta.shape[0]
+        lp = torch.empty(B, device=theta.device, dtype=torch.float32)
+        g = torch.empty_like(theta)
+        inten = torch.empty(B, self.n_lens_light + self.n_source, device=theta.device,
+                            dtype=torch.float32)
+        _check(self._lib.gl_logp_grad_backward(self._h, _ptr(theta), B, _ptr(lp), _ptr(g),
+                                               _ptr(inten), defl, _stream_ptr(stream)))
+        return lp, g, inten
 
     def logp_grad_noalloc(self, theta, out=None, grad=None, stream=None):
         """gl_logp_grad_noalloc: the same result without any device allocation

@@ -677,6 +677,134 @@ __global__ void k_svi_update(int P, float* __restrict__ phi, float* __restrict__
   }
 }
 
+// ------------------------------------------------ backward intensities ----
+// Intensity of light component c sits at theta index 8 + 7c + 6.
+__device__ __forceinline__ int intensity_index(int c) { return 8 + 7 * c + 6; }
+
+// Component rows: row (b, c) is theta_b with intensity k set to [k == c].
+__global__ void k_bwd_rows(const float* __restrict__ th, int B, int P, int K,
+                           float* __restrict__ rows) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t n = (size_t)B * K * P;
+  if (i >= n) return;
+  const int k = (int)(i % P);
+  const size_t bc = i / P;
+  const int c = (int)(bc % K);
+  const size_t b = bc / K;
+  float v = th[b * P + k];
+  for (int j = 0; j < K; ++j)
+    if (k == intensity_index(j)) v = j == c ? 1.f : 0.f;
+  rows[i] = v;
+}
+
+// One block per row: A = M^T W M and r = M^T W d over the pixels (FP64),
+// then A I = r by Cholesky on thread 0; theta* = theta with I. A solve that
+// fails (a component with no light in the image) sets every intensity to 0.
+template <int K>
+__global__ void k_bwd_solve(const float* __restrict__ img, const float* __restrict__ data,
+                            const float* __restrict__ w, int npix, int B, int P,
+                            const float* __restrict__ th, float* __restrict__ th_star,
+                            float* __restrict__ inten) {
+  constexpr int KM = K;
+  constexpr int NS = K * (K + 1) / 2 + K;
+  __shared__ double red[8][NS];
+  const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  constexpr int nA = K * (K + 1) / 2, ns = NS;
+  double acc[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) acc[q] = 0.0;
+  const float* M = img + (size_t)b * K * npix;
+  for (int p = t; p < npix; p += blockDim.x) {
+    const double wp_ = w[p], dp = data[p];
+    double m[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) m[k] = M[(size_t)k * npix + p];
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int l = 0; l <= k; ++l) acc[q++] += wp_ * m[k] * m[l];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[nA + k] += wp_ * m[k] * dp;
+  }
+#pragma unroll
+  for (int q = 0; q < ns; ++q) {
+    double v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wp][q] = v;
+  }
+  __syncthreads();
+  __shared__ float I_sh[KM];
+  if (t == 0) {
+    double A[KM][KM], r[KM], L[KM][KM], y[KM], x[KM];
+    int q = 0;
+    for (int k = 0; k < K; ++k)
+      for (int l = 0; l <= k; ++l) {
+        double s = 0.0;
+        for (int u = 0; u < 8; ++u) s += red[u][q];
+        A[k][l] = A[l][k] = s;
+        ++q;
+      }
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int u = 0; u < 8; ++u) s += red[u][nA + k];
+      r[k] = s;
+    }
+    bool ok = true;
+    for (int k = 0; k < K && ok; ++k) {
+      double d = A[k][k];
+      for (int j = 0; j < k; ++j) d -= L[k][j] * L[k][j];
+      if (!(d > 1e-300) || !isfinite(d)) { ok = false; break; }
+      L[k][k] = sqrt(d);
+      for (int i = k + 1; i < K; ++i) {
+        double s = A[i][k];
+        for (int j = 0; j < k; ++j) s -= L[i][j] * L[k][j];
+        L[i][k] = s / L[k][k];
+      }
+    }
+    if (ok) {
+      for (int k = 0; k < K; ++k) {
+        double s = r[k];
+        for (int j = 0; j < k; ++j) s -= L[k][j] * y[j];
+        y[k] = s / L[k][k];
+      }
+      for (int k = K - 1; k >= 0; --k) {
+        double s = y[k];
+        for (int j = k + 1; j < K; ++j) s -= L[j][k] * x[j];
+        x[k] = s / L[k][k];
+        if (!isfinite(x[k])) ok = false;
+      }
+    }
+    for (int k = 0; k < K; ++k) I_sh[k] = ok ? (float)x[k] : 0.f;
+  }
+  __syncthreads();
+  for (int k = t; k < P; k += blockDim.x) {
+    float v = th[(size_t)b * P + k];
+    for (int j = 0; j < K; ++j)
+      if (k == intensity_index(j)) v = I_sh[j];
+    th_star[(size_t)b * P + k] = v;
+  }
+  if (inten && t < K) inten[(size_t)b * K + t] = I_sh[t];
+}
+
+__global__ void k_bwd_zero(float* __restrict__ grad, int B, int P, int K) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * K) return;
+  const int b = i / K, c = i - b * K;
+  grad[(size_t)b * P + intensity_index(c)] = 0.f;
+}
+
+// The backward model's prior: intensities flat on R (no density, no support).
+__global__ void k_bwd_prior(gl::PriorDev* __restrict__ pr, int K) {
+  const int c = threadIdx.x;
+  if (c >= K) return;
+  gl::PriorDev& d = pr[intensity_index(c)];
+  d.kind = 0;
+  d.lo = -INFINITY;
+  d.hi = INFINITY;
+  d.cnst = 0.0;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ host side ----
@@ -722,6 +850,10 @@ struct InferState {
   size_t svi_buf_floats = 0;
   double* svi_sums = nullptr;
   SviCtl* svi_ctl = nullptr;
+  // backward intensities
+  gl::PriorDev* bwd_prior = nullptr;
+  float* bwd_buf = nullptr;  // component rows, images, theta*
+  size_t bwd_buf_floats = 0;
 };
 
 void infer_release(gl_system* s) {
@@ -736,6 +868,8 @@ void infer_release(gl_system* s) {
   cudaFree(f->svi_buf);
   cudaFree(f->svi_sums);
   cudaFree(f->svi_ctl);
+  cudaFree(f->bwd_prior);
+  cudaFree(f->bwd_buf);
   delete f;
   s->inf = nullptr;
 }
@@ -1213,6 +1347,72 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
     std::memcpy(&f->svi_key, &key, sizeof key);
   }
   for (int k = 0; k < n_steps; ++k) GI_CUDA(cudaGraphLaunch(f->svi_exec, st), "graph launch");
+  return GL_OK;
+}
+
+// ------------------------------------------------ backward intensities ----
+gl_status gl_logp_grad_backward(gl_system* sys, const float* theta, int B, float* logp,
+                                float* grad, float* intensity, gl_deflection defl, void* stream) {
+  if (!sys) return fail(GL_EINVAL, "system is NULL");
+  if (B < 0) return fail(GL_EINVAL, "B < 0");
+  if (B == 0) return GL_OK;
+  if (!theta || !logp || !grad) return fail(GL_EINVAL, "NULL theta, logp or grad");
+  gl_status r = set_dev(sys);
+  if (r != GL_OK) return r;
+  gl::InferState* f;
+  if ((r = infer_state(sys, &f)) != GL_OK) return r;
+  const int P = sys->sp.P, K = sys->sp.nL + sys->sp.nS;
+  const size_t npix = (size_t)sys->sp.ny * sys->sp.nx;
+  if (!f->bwd_prior) {
+    GI_CUDA(cudaMalloc(&f->bwd_prior, P * sizeof(gl::PriorDev)), "prior allocation");
+    GI_CUDA(cudaMemcpy(f->bwd_prior, sys->d_prior, P * sizeof(gl::PriorDev),
+                       cudaMemcpyDeviceToDevice), "prior copy");
+    k_bwd_prior<<<1, 32>>>(f->bwd_prior, K);
+    GI_CUDA(cudaGetLastError(), "prior set-up");
+    GI_CUDA(cudaDeviceSynchronize(), "prior set-up");
+  }
+  // prepare both launches before either runs (the second preparation may
+  // grow the scratch or table buffers the first one points into)
+  SysParams sg, sf;
+  size_t dg, df;
+  if ((r = gl::eval_prepare(sys, B, defl, true, &sg, &dg)) != GL_OK) return r;
+  if ((r = gl::eval_prepare(sys, B * K, defl, false, &sf, &df)) != GL_OK) return r;
+  if ((r = gl::eval_prepare(sys, B, defl, true, &sg, &dg)) != GL_OK) return r;
+  const size_t need = (size_t)B * K * P + (size_t)B * K * npix + (size_t)B * P;
+  if (need > f->bwd_buf_floats) {
+    cudaFree(f->bwd_buf);
+    f->bwd_buf = nullptr;
+    f->bwd_buf_floats = 0;
+    GI_CUDA(cudaMalloc(&f->bwd_buf, need * sizeof(float)), "buffer allocation");
+    f->bwd_buf_floats = need;
+  }
+  float* rows = f->bwd_buf;
+  float* imgs = rows + (size_t)B * K * P;
+  float* th_star = imgs + (size_t)B * K * npix;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nr = (size_t)B * K * P;
+  k_bwd_rows<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(theta, B, P, K, rows);
+  GI_CUDA(cudaGetLastError(), "row launch");
+  if (sf.table)
+    GI_CUDA(gl::launch_table(defl == GL_DEFL_TABLE ? nullptr : sys->sur, rows, P, B * K,
+                             const_cast<float4*>(sf.table), st),
+            "table launch");
+  GI_CUDA(gl::launch_forward(sf, rows, B * K, nullptr, imgs, df, st), "image launch");
+  switch (K) {
+#define GL_BWD(k)                                                                          \
+  case k:                                                                                  \
+    k_bwd_solve<k><<<B, 256, 0, st>>>(imgs, sys->d_data, sys->d_w, (int)npix, B, P, theta, \
+                                      th_star, intensity);                                 \
+    break;
+    GL_BWD(1) GL_BWD(2) GL_BWD(3) GL_BWD(4) GL_BWD(5)
+#undef GL_BWD
+    default: return fail(GL_EINVAL, "unsupported number of light components");
+  }
+  GI_CUDA(cudaGetLastError(), "solve launch");
+  sg.prior = f->bwd_prior;
+  GI_CUDA(gl::eval_launch(sys, sg, dg, th_star, B, logp, grad, defl, st), "gradient launch");
+  k_bwd_zero<<<(B * K + 255) / 256, 256, 0, st>>>(grad, B, P, K);
+  GI_CUDA(cudaGetLastError(), "launch");
   return GL_OK;
 }
 
