@@ -539,6 +539,25 @@ def run_uneven(args) -> dict | None:
                                                 stream=stream), args.steps, args.warmup, stream,
                          flush)
     dl = torch.cat([(a - b).abs() for a, b in zip(logps, lps_s)]).cpu().numpy()
+    # end to end: every system's rows from pinned host memory, one multi-system
+    # evaluation (exact series), log p and gradients back to pinned host memory
+    h_th = [t.cpu().pin_memory() for t in thetas]
+    h_lp = [torch.empty(t.shape[0]).pin_memory() for t in thetas]
+    h_g = [torch.empty(t.shape).pin_memory() for t in thetas]
+    e2e_ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d_, h_ in zip(thetas, h_th):
+            d_.copy_(h_, non_blocking=True)
+        plan.logp_grad(thetas, logps, grads, stream=stream)
+        for a_, b_, c_, d_ in zip(h_lp, logps, h_g, grads):
+            a_.copy_(b_, non_blocking=True)
+            c_.copy_(d_, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = sum(t.numel() * 4 for t in thetas)
+    d2h = sum(t.numel() * 4 + t.shape[0] * 4 for t in thetas)
     t_ms = sum(ms)
     if world > 1:
         t = torch.tensor([t_ms], device=dev)
@@ -570,7 +589,8 @@ def run_uneven(args) -> dict | None:
                         "dlogp_abs_p90": float(np.quantile(dl, 0.9))},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None},
-            "e2e": None,
+            "e2e": {"value": world * n_rows / (min(e2e_ms) / 1e3), "unit": "evals/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 3 * args.steps,
             "clocks": clk.summary(),
         }
