@@ -471,49 +471,6 @@ __device__ void write_intervals(const float4 (*node)[2], float4* __restrict__ ou
   }
 }
 
-// Per-sample tables for the lens kernels from the network: for row b with EPL
-// axis ratio q and slope gamma, node j takes (F, dF/dpa, dF/dq, dF/dt) as 4
-// complex numbers, from the network at R = theta_E with forward-mode
-// derivatives, and the row's intervals follow from the nodes. One CTA
-// (8 warps x 16 nodes) per row; rows outside the training domain are skipped
-// (the lens kernels use the exact series there).
-__global__ void k_table(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
-                        const float* __restrict__ theta, int P, int B, float q_lo, float q_hi,
-                        float g_lo, float g_hi, float4* __restrict__ table) {
-  const int b = blockIdx.x;
-  if (b >= B) return;
-  const float* th = theta + (size_t)b * P;
-  const float e1 = th[2], e2 = th[3];
-  const float cc = sqrtf(e1 * e1 + e2 * e2);
-  const float q = (1.f - cc) / (1.f + cc), gamma = th[1];
-  if (!(q >= q_lo && q <= q_hi && gamma >= g_lo && gamma <= g_hi)) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-  float x[2][4], vp[2], dv[2];
-  for (int h = 0; h < 2; ++h) {
-    table_node(warp * 16 + g + 8 * h, vp[h], dv[h]);
-    features(q, gamma, 0.f, vp[h], x[h]);
-  }
-  // tangents of the normalised inputs: d/dvphi, d/dq, d/dgamma (= d/dt)
-  const float seeds[3][4] = {{0.f, 0.f, 0.f, 1.f / PI_F}, {4.f, 0.f, 0.f, 0.f},
-                             {0.f, 1.f / 0.3f, 0.f, 0.f}};
-  float y[4], dy[3][4];
-  for (int s = 0; s < 3; ++s) forward_jvp(wb, params, x[0], x[1], seeds[s], seeds[s], y, dy[s]);
-  __shared__ float4 node[TABLE_M][2];
-  if (c == 0)
-    for (int h = 0; h < 2; ++h) {
-      const int j = warp * 16 + g + 8 * h;
-      const Base bt = base_terms(q, gamma - 1.f, vp[h]);
-      const float k = 1.f / OUT_SCALE;
-      node[j][0] = make_float4(bt.Fr + k * y[2 * h], bt.Fi + k * y[2 * h + 1],
-                               dv[h] * (bt.Pr + k * dy[0][2 * h]),
-                               dv[h] * (bt.Pi + k * dy[0][2 * h + 1]));
-      node[j][1] = make_float4(bt.Qr + k * dy[1][2 * h], bt.Qi + k * dy[1][2 * h + 1],
-                               bt.Tr + k * dy[2][2 * h], bt.Ti + k * dy[2][2 * h + 1]);
-    }
-  __syncthreads();
-  write_intervals(node, table + (size_t)b * TABLE_ROW);
-}
-
 // The same tables from the exact series (FP64 per node): F, dF/dvphi =
 // F'(z) 2iz, dF/dq = -F'(z) e^{2i vphi} df/dq, dF/dt = sum c_n h_n z^n, with
 // F'(z) = [t F - (2-t) E]/(2(1-z)) and F = 1 + zE. Rows with |e| above 0.5
@@ -563,13 +520,319 @@ __global__ void k_table_exact(const float* __restrict__ theta, int P, int B, flo
   write_intervals(node, table + (size_t)b * TABLE_ROW);
 }
 
+// ----------------------------------------- tables on tcgen05 (TMEM) ----
+// Per-sample tables for the lens kernels from the network: for row b with EPL
+// axis ratio q and slope gamma, node j takes (F, dF/dpa, dF/dq, dF/dt) as 4
+// complex numbers, from the network at R = theta_E with forward-mode
+// derivatives, and the row's intervals follow from the nodes; rows outside
+// the training domain are skipped (the lens kernels use the exact series
+// there). The network runs on the 5th-generation tensor
+// cores: per row, the 128 nodes are the M = 128 rows of every layer's MMA
+// (tcgen05.mma kind::f16, BF16 operands in shared memory, FP32 accumulators
+// in tensor memory), for the primal pass and the three forward-mode tangents
+// (d/dvphi, d/dq, d/dgamma) as four accumulators of 64 columns. One thread
+// per node reads its accumulator row back (tcgen05.ld), applies bias and SiLU
+// (and SiLU' to the tangents) and writes the next layer's BF16 operand.
+// Persistent CTAs of 4 warps keep the weights in shared memory across rows.
+//
+// Operands use the canonical K-major layout without swizzle: 8 x 16-byte core
+// matrices, K-adjacent ones 128 B apart (LBO), row-group-adjacent ones
+// K/8 x 128 B apart (SBO).
+namespace tc {
+
+constexpr int NT = 128;                 // threads = nodes = MMA rows
+constexpr uint32_t TMEM_COLS = 256;     // 4 streams x 64 columns
+constexpr int A0_BYTES = 128 * 16 * 2;  // layer-1 operand [128][16]
+constexpr int A_BYTES = 128 * 64 * 2;   // hidden operands [128][64]
+constexpr int W1_BYTES = 64 * 16 * 2;
+constexpr int WH_BYTES = 64 * 64 * 2;
+constexpr int W5_BYTES = 16 * 64 * 2;   // output layer padded to N = 16
+constexpr int OFF_W1 = 0;
+constexpr int OFF_WH = OFF_W1 + W1_BYTES;
+constexpr int OFF_W5 = OFF_WH + 3 * WH_BYTES;
+constexpr int OFF_A0 = OFF_W5 + W5_BYTES;
+constexpr int OFF_A = OFF_A0 + A0_BYTES;
+constexpr int OFF_NODE = OFF_A + 4 * A_BYTES;
+constexpr int SMEM_BYTES = OFF_NODE + TABLE_M * 2 * 16;
+constexpr long long WAIT_LIMIT = 1ll << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Byte offset of element (r, k) of an [R][K] BF16 operand.
+__device__ __forceinline__ uint32_t core_off(int r, int k, int K) {
+  return (uint32_t)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor (no swizzle, base offset 0, version 1).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::f16: FP32 D, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id,
+                                    uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_u32(bar)));
+}
+
+// Bounded wait for the barrier's phase; false on timeout.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t phase) {
+  uint32_t done = 0;
+  for (long long it = 0; it < WAIT_LIMIT && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase));
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void ld16(uint32_t addr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void ld2(uint32_t addr, float (&v)[2]) {
+  uint32_t r0, r1;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
+               : "=r"(r0), "=r"(r1)
+               : "r"(addr));
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+}
+
+__device__ __forceinline__ void wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Operand writes by the threads are made visible to the tensor cores, and the
+// accumulator reads finished, before thread 0 issues the next MMAs.
+__device__ __forceinline__ void to_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Copies an [N][K] BF16 row-major matrix (rows >= n_src zero) into the operand layout.
+__device__ void load_operand(unsigned char* dst, const __nv_bfloat16* __restrict__ src, int N,
+                             int K, int n_src) {
+  for (int i = threadIdx.x; i < N * K; i += NT) {
+    const int n = i / K, k = i - n * K;
+    *reinterpret_cast<__nv_bfloat16*>(dst + core_off(n, k, K)) =
+        n < n_src ? src[n * K + k] : __float2bfloat16(0.f);
+  }
+}
+
+// 8 consecutive BF16 values of row r at column k0 (a multiple of 8), one store.
+__device__ __forceinline__ void put8(unsigned char* base, int r, int k0, int K, const float* v) {
+  uint4 u;
+  u.x = pack_bf16(v[0], v[1]);
+  u.y = pack_bf16(v[2], v[3]);
+  u.z = pack_bf16(v[4], v[5]);
+  u.w = pack_bf16(v[6], v[7]);
+  *reinterpret_cast<uint4*>(base + core_off(r, k0, K)) = u;
+}
+
+}  // namespace tc
+
+__global__ void __launch_bounds__(tc::NT, 1)
+k_table_tc(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
+           const float* __restrict__ theta, int P, int B, float q_lo, float q_hi, float g_lo,
+           float g_hi, float4* __restrict__ table, int* __restrict__ timeout) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t bar;
+  const int t = threadIdx.x, w = t >> 5;
+  load_operand(sm + OFF_W1, wb + BOFF_P1, 64, 16, 64);
+  load_operand(sm + OFF_WH, wb + BOFF_P2, 64, 64, 64);
+  load_operand(sm + OFF_WH + WH_BYTES, wb + BOFF_P3, 64, 64, 64);
+  load_operand(sm + OFF_WH + 2 * WH_BYTES, wb + BOFF_P4, 64, 64, 64);
+  load_operand(sm + OFF_W5, wb + BOFF_P5, 16, 64, 8);
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  to_async();
+  const uint32_t tb = tmem_base;
+  const uint32_t lane_addr = tb + ((uint32_t)(32 * w) << 16);
+  unsigned char* A0 = sm + OFF_A0;
+  unsigned char* A = sm + OFF_A;
+  float4(*node)[2] = reinterpret_cast<float4(*)[2]>(sm + OFF_NODE);
+  const uint32_t a0 = smem_u32(A0), aa = smem_u32(A), w1 = smem_u32(sm + OFF_W1);
+  const uint32_t wh = smem_u32(sm + OFF_WH), w5 = smem_u32(sm + OFF_W5);
+  uint32_t phase = 0;
+  bool ok = true;
+  // tangent seeds of the normalised inputs, rounded to BF16 like every operand
+  const float seed[3] = {__bfloat162float(__float2bfloat16(1.f / PI_F)), 4.f,
+                         __bfloat162float(__float2bfloat16(1.f / 0.3f))};
+  const int seed_in[3] = {3, 0, 1};
+  for (int b = blockIdx.x; b < B && ok; b += gridDim.x) {
+    const float* th = theta + (size_t)b * P;
+    const float e1 = th[2], e2 = th[3];
+    const float cc = sqrtf(e1 * e1 + e2 * e2);
+    const float q = (1.f - cc) / (1.f + cc), gamma = th[1];
+    if (!(q >= q_lo && q <= q_hi && gamma >= g_lo && gamma <= g_hi)) continue;
+    float vp, dv, x[4];
+    table_node(t, vp, dv);
+    features(q, gamma, 0.f, vp, x);
+    {
+      const float v[8] = {x[0], x[1], x[2], x[3], 0.f, 0.f, 0.f, 0.f};
+      const float zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      put8(A0, t, 0, 16, v);
+      put8(A0, t, 8, 16, zero);
+    }
+    to_async();
+    // layer 1 (primal only: the tangents' first pre-activations are W1 seed)
+    if (t == 0) {
+      mma(tb, sdesc(a0, 256), sdesc(w1, 256), idesc(128, 64), 0u);
+      commit(&bar);
+    }
+    for (int layer = 1; layer <= 5 && ok; ++layer) {
+      // the decision is the block's (a thread leaving alone would desert a barrier)
+      if (!__syncthreads_and(wait_phase(&bar, phase))) {
+        ok = false;
+        break;
+      }
+      phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (layer == 5) break;
+      // epilogue of layer `layer`: bias, SiLU, SiLU' on the tangents, BF16 operands
+      const float* bias = params + (layer == 1 ? OFF_B1 : layer == 2 ? OFF_B2
+                                                        : layer == 3 ? OFF_B3 : OFF_B4);
+#pragma unroll 1
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        float z[16], d1[16], d2[16], d3[16];
+        ld16(lane_addr + c0, z);
+        if (layer > 1) {
+          ld16(lane_addr + 64 + c0, d1);
+          ld16(lane_addr + 128 + c0, d2);
+          ld16(lane_addr + 192 + c0, d3);
+        }
+        wait_ld();
+        if (layer == 1) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const __nv_bfloat16* wrow = wb + BOFF_P1 + (c0 + j) * 16;
+            d1[j] = __bfloat162float(wrow[seed_in[0]]) * seed[0];
+            d2[j] = __bfloat162float(wrow[seed_in[1]]) * seed[1];
+            d3[j] = __bfloat162float(wrow[seed_in[2]]) * seed[2];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float zz = z[j] + bias[c0 + j];
+          const float sg = sigm(zz);
+          const float dsl = sg * (1.f + zz * (1.f - sg));
+          z[j] = zz * sg;
+          d1[j] *= dsl;
+          d2[j] *= dsl;
+          d3[j] *= dsl;
+        }
+        put8(A, t, c0, 64, z);
+        put8(A, t, c0 + 8, 64, z + 8);
+        put8(A + A_BYTES, t, c0, 64, d1);
+        put8(A + A_BYTES, t, c0 + 8, 64, d1 + 8);
+        put8(A + 2 * A_BYTES, t, c0, 64, d2);
+        put8(A + 2 * A_BYTES, t, c0 + 8, 64, d2 + 8);
+        put8(A + 3 * A_BYTES, t, c0, 64, d3);
+        put8(A + 3 * A_BYTES, t, c0 + 8, 64, d3 + 8);
+      }
+      to_async();
+      if (t == 0) {
+        const bool out = layer == 4;
+        const uint32_t wl = out ? w5 : wh + (uint32_t)(layer - 1) * WH_BYTES;
+        const uint32_t id = out ? idesc(128, 16) : idesc(128, 64);
+        for (int s = 0; s < 4; ++s)
+          for (int kk = 0; kk < 4; ++kk)
+            mma(tb + 64u * s, sdesc(aa + s * A_BYTES + kk * 256, 1024), sdesc(wl + kk * 256, 1024),
+                id, kk > 0 ? 1u : 0u);
+        commit(&bar);
+      }
+    }
+    if (!ok) break;
+    // output layer: y (primal) and the three tangents' dy, two columns each
+    float y[2], dy[3][2];
+    ld2(lane_addr, y);
+    ld2(lane_addr + 64, dy[0]);
+    ld2(lane_addr + 128, dy[1]);
+    ld2(lane_addr + 192, dy[2]);
+    wait_ld();
+    y[0] += params[OFF_B5];
+    y[1] += params[OFF_B5 + 1];
+    const Base bt = base_terms(q, gamma - 1.f, vp);
+    const float k = 1.f / OUT_SCALE;
+    node[t][0] = make_float4(bt.Fr + k * y[0], bt.Fi + k * y[1], dv * (bt.Pr + k * dy[0][0]),
+                             dv * (bt.Pi + k * dy[0][1]));
+    node[t][1] = make_float4(bt.Qr + k * dy[1][0], bt.Qi + k * dy[1][1], bt.Tr + k * dy[2][0],
+                             bt.Ti + k * dy[2][1]);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    write_intervals(node, table + (size_t)b * TABLE_ROW);
+    __syncthreads();
+  }
+  if (!ok && t == 0) atomicExch(timeout, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (w == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tb),
+                 "r"(TMEM_COLS));
+}
+
+__device__ int g_table_timeout = 0;
+
 cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B, float4* table,
                          cudaStream_t st) {
-  if (s)
-    k_table<<<B, 256, 0, st>>>(s->wb, s->params, theta, P, B, s->q_lo, s->q_hi, s->g_lo, s->g_hi,
-                               table);
-  else
+  if (s) {
+    static thread_local int configured_dev = -1;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && configured_dev != dev) {
+      e = cudaFuncSetAttribute(k_table_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tc::SMEM_BYTES);
+      if (e == cudaSuccess) configured_dev = dev;
+    }
+    if (e != cudaSuccess) return e;
+    int* flag = nullptr;
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), g_table_timeout);
+    if (e != cudaSuccess) return e;
+    const int grid = B < 2 * sms ? B : 2 * sms;
+    k_table_tc<<<grid, tc::NT, tc::SMEM_BYTES, st>>>(s->wb, s->params, theta, P, B, s->q_lo,
+                                                     s->q_hi, s->g_lo, s->g_hi, table, flag);
+  } else {
     k_table_exact<<<B, TABLE_M, 0, st>>>(theta, P, B, 1.f / 3.f, table);
+  }
   return cudaGetLastError();
 }
 
