@@ -24,8 +24,9 @@ namespace gl {
 // Each thread computes ROWS_STRIP outputs of one column; lanes own adjacent
 // columns (conflict-free loads); taps are compile-time indices into the
 // kernel's parameter block.
-// RELOAD (parameter block in shared memory): the taps are re-read for every
-// strip instead of being hoisted into registers.
+// RELOAD (parameter block in shared memory): the tap columns are a loop
+// unrolled by 3, so a few columns of taps are live (fully unrolled, the
+// compiler hoisted all K^2 shared-memory taps into registers and spilled).
 template <int K, bool CONV, bool RELOAD, class Epi>
 __device__ __forceinline__ void correlate_fixed(const SysParams& sp, const float* in, Epi epi) {
   constexpr int RS = ROWS_STRIP;
@@ -40,18 +41,24 @@ __device__ __forceinline__ void correlate_fixed(const SysParams& sp, const float
 #pragma unroll
     for (int r = 0; r < RS; ++r) acc[r] = 0.f;
     const float* base = in + (size_t)i0 * Wp + j;
-    const SysParams& spk = RELOAD ? reload(sp) : sp;
-#pragma unroll
-    for (int v = 0; v < K; ++v) {
+    auto column = [&](int v, const float* taps) {
       float col[RS + K - 1];
 #pragma unroll
       for (int m = 0; m < RS + K - 1; ++m) col[m] = base[m * Wp + v];
 #pragma unroll
       for (int u = 0; u < K; ++u) {
-        const float kv = CONV ? spk.kconv[u * K + v] : spk.kcorr[u * K + v];
+        const float kv = taps[u * K + v];
 #pragma unroll
         for (int r = 0; r < RS; ++r) acc[r] = fmaf(kv, col[u + r], acc[r]);
       }
+    };
+    if constexpr (RELOAD) {
+      const float* taps = CONV ? sp.kconv : sp.kcorr;
+#pragma unroll 3
+      for (int v = 0; v < K; ++v) column(v, taps);
+    } else {
+#pragma unroll
+      for (int v = 0; v < K; ++v) column(v, CONV ? sp.kconv : sp.kcorr);
     }
 #pragma unroll
     for (int r = 0; r < RS; ++r)
