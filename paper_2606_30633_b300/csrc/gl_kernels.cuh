@@ -276,13 +276,36 @@ __device__ __forceinline__ void adjoint_pixels(const SysParams& sp, const Sample
     w0 = w1;
     w0.next();
     if ((it + 1) % FLUSH_IT == 0 || it + 1 == iters) {
+      if constexpr (P <= 32) {
+        // reduce-scatter over the warp: each xor step halves the values a
+        // lane holds (it keeps the half its lane bit selects and adds the
+        // partner's copy of it), so lane k ends with the warp sum of value k;
+        // 31 shuffles for all P sums instead of 5 per sum
+        float v[32];
 #pragma unroll
-      for (int k = 0; k < P; ++k) {
-        float v = acc_total(acc[k]);
+        for (int k = 0; k < 32; ++k) v[k] = k < P ? acc_total(acc[k]) : 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) redP[warp][k] += v;
-        acc[k] = acc_zero<AccT>();
+        for (int o = 16; o > 0; o >>= 1) {
+          const bool up = (lane & o) != 0;
+#pragma unroll
+          for (int i = 0; i < o; ++i) {
+            const float keep = up ? v[i + o] : v[i];
+            const float give = up ? v[i] : v[i + o];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+          }
+        }
+        if (lane < P) redP[warp][lane] += v[0];
+#pragma unroll
+        for (int k = 0; k < P; ++k) acc[k] = acc_zero<AccT>();
+      } else {
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          float v = acc_total(acc[k]);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) redP[warp][k] += v;
+          acc[k] = acc_zero<AccT>();
+        }
       }
     }
   }
