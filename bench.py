@@ -736,7 +736,7 @@ def run_pipeline(args) -> dict | None:
                          "frac": achieved / peak, "traffic": None},
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": B * W.P * 4,
                     "d2h_bytes_per_step": B * 4},
-            "gpu_launches": (2 + 2 * L + 2) * args.steps,
+            "gpu_launches": (2 * L + 4) * args.steps,
             "clocks": clk.summary(),
         }
     if world > 1:

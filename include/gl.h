@@ -375,7 +375,7 @@ enum {
 };
 
 /* Creates a sampler at u0 (device [B][P], copied); M^-1 starts at ones.
- * Evaluates log p~ and its gradient at u0 on the stream. */
+ * Evaluates log p~ and its gradient at u0 on the stream and waits for it. */
 gl_status gl_hmc_create(gl_system* sys, const gl_hmc_desc* desc, const float* u0,
                         gl_hmc** out, void* stream);
 

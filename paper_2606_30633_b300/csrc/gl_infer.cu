@@ -805,6 +805,17 @@ __global__ void k_bwd_prior(gl::PriorDev* __restrict__ pr, int K) {
   d.cnst = 0.0;
 }
 
+// Control-block setters: launched on the caller's stream ahead of a graph,
+// so a run's parameters need no host staging or synchronisation.
+__global__ void k_set_map_ctl(MapCtl* c, MapCtl v) { *c = v; }
+__global__ void k_set_svi_ctl(SviCtl* c, SviCtl v) { *c = v; }
+__global__ void k_set_hmc_run(HmcDev* c, int flags, float* draws, float* accept) {
+  c->flags = flags;
+  c->local = 0;
+  c->draws = draws;
+  c->accept = accept;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ host side ----
@@ -816,7 +827,7 @@ struct gl_hmc {
   HmcBufs b{};
   float* pool = nullptr;
   HmcDev* ctl = nullptr;
-  HmcDev* h_ctl = nullptr;  // pinned staging of the run fields
+  HmcDev* h_ctl = nullptr;  // pinned staging: initial control block, step-size reads
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   void *key_scratch = nullptr, *key_table = nullptr;
@@ -1006,7 +1017,8 @@ gl_status gl_map_adam(gl_system* sys, float* u, float* m, float* v, int B, int n
   if (!f->map_ctl) GI_CUDA(cudaMalloc(&f->map_ctl, sizeof(MapCtl)), "control allocation");
   cudaStream_t st = (cudaStream_t)stream;
   const MapCtl hc{t0, lr, beta1, beta2, eps};
-  GI_CUDA(cudaMemcpyAsync(f->map_ctl, &hc, sizeof hc, cudaMemcpyHostToDevice, st), "control");
+  k_set_map_ctl<<<1, 1, 0, st>>>(f->map_ctl, hc);
+  GI_CUDA(cudaGetLastError(), "control");
   float* th = f->map_buf;
   float* gth = th + (size_t)B * P;
   float* lpth = gth + (size_t)B * P;
@@ -1127,7 +1139,7 @@ gl_status gl_hmc_create(gl_system* sys, const gl_hmc_desc* d, const float* u0, g
                                              h->b.g);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // h_ctl is reused by the runs
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // creation waits for its evaluation
   if (e != cudaSuccess) {
     gl_hmc_destroy(h);
     return cuda_fail(e, "sampler set-up");
@@ -1200,20 +1212,8 @@ gl_status gl_hmc_run(gl_hmc* h, int n, int flags, float* draws, float* accept, v
     h->key_scratch = sp.scratch;
     h->key_table = const_cast<float4*>(sp.table);
   }
-  // the run's fields, from pinned staging (the previous run's copy has
-  // completed: the staging is written only after the stream is drained)
-  GI_CUDA(cudaStreamSynchronize(st), "stream");
-  HmcDev& c = *h->h_ctl;
-  c.flags = flags;
-  c.local = 0;
-  c.draws = draws;
-  c.accept = accept;
-  GI_CUDA(cudaMemcpyAsync(&h->ctl->flags, &c.flags, sizeof(int), cudaMemcpyHostToDevice, st),
-          "control");
-  GI_CUDA(cudaMemcpyAsync(&h->ctl->local, &c.local, sizeof(int), cudaMemcpyHostToDevice, st),
-          "control");
-  GI_CUDA(cudaMemcpyAsync(&h->ctl->draws, &c.draws, 2 * sizeof(float*), cudaMemcpyHostToDevice, st),
-          "control");
+  k_set_hmc_run<<<1, 1, 0, st>>>(h->ctl, flags, draws, accept);
+  GI_CUDA(cudaGetLastError(), "control");
   for (int k = 0; k < n; ++k) GI_CUDA(cudaGraphLaunch(h->exec, st), "graph launch");
   return GL_OK;
 }
@@ -1298,7 +1298,8 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
   if (!f->svi_ctl) GI_CUDA(cudaMalloc(&f->svi_ctl, sizeof(SviCtl)), "control allocation");
   cudaStream_t st = (cudaStream_t)stream;
   const SviCtl hc{(unsigned long long)t0, 0, lr, beta1, beta2, eps, elbo};
-  GI_CUDA(cudaMemcpyAsync(f->svi_ctl, &hc, sizeof hc, cudaMemcpyHostToDevice, st), "control");
+  k_set_svi_ctl<<<1, 1, 0, st>>>(f->svi_ctl, hc);
+  GI_CUDA(cudaGetLastError(), "control");
   float* z = f->svi_buf;
   float* a = z + nP;
   float* u = a + nP;

@@ -801,7 +801,15 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ param
     write_intervals(node, table + (size_t)b * TABLE_ROW);
     __syncthreads();
   }
-  if (!ok && t == 0) atomicExch(timeout, 1);
+  if (!ok) {
+    // a wait ran out: flag it and make every row this CTA still owned NaN, so
+    // the lens results show the failure instead of reading stale tables
+    if (t == 0) atomicExch(timeout, 1);
+    const float nan = __int_as_float(0x7fc00000);
+    for (int b = blockIdx.x; b < B; b += gridDim.x)
+      for (int k = t; k < TABLE_ROW; k += NT)
+        table[(size_t)b * TABLE_ROW + k] = make_float4(nan, nan, nan, nan);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (w == 0)
