@@ -511,6 +511,8 @@ def run_uneven(args) -> dict | None:
     Ws = synth.uneven_systems()
     systems, thetas, rows = [], [], []
     for W in Ws:
+        if args.batch:
+            W.batch = args.batch  # rows per system (profiling runs)
         spec = W.prior()
         blank = gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
                           np.ones((W.ny, W.nx)), W.psf, W.n_lens_light, W.n_source, spec)
@@ -753,7 +755,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=None,
-                    help="rows per step (default: the workload's); for profiling runs")
+                    help="rows per step (rows per system for uneven; default: the "
+                         "workload's); for profiling runs")
     ap.add_argument("--workload", choices=["ground100", "space200-leapfrog", "uneven", "pipeline"],
                     default="ground100")
     args = ap.parse_args()
