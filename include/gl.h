@@ -302,11 +302,11 @@ gl_status gl_system_set_surrogate(gl_system* sys, const gl_surrogate* sur);
  * ("mapped into an unconstrained space via a bijective transformation",
  * Sec. 3.1). The paper defers the map to its earlier release; this library
  * takes one map per prior support:
- *   normal, or flat on R        theta = u
- *   uniform, truncated normal,
- *   flat on [lo, hi]            theta = lo + (hi - lo) sigmoid(u)
+ *   normal, or no finite bound  theta = u
+ *   both bounds finite          theta = lo + (hi - lo) sigmoid(u)
  *   log-normal                  theta = exp(u)
- *   flat on [lo, inf) / (-inf, hi]   theta = lo + exp(u) / hi - exp(u)
+ *   one finite bound            theta = lo + exp(u) / hi - exp(u)
+ * (the bounds of a uniform, truncated-normal or flat prior)
  * and, for a component whose ellipticity is restricted to |e| < emax while
  * both e priors are unbounded, the radial map e = v emax tanh(|v|)/|v|.
  * log p~(u) = log p(theta(u)) + log|det d theta/d u|. All arrays below are

@@ -11,8 +11,9 @@ published algorithms it names; it shares no code with the CUDA library.
         unbounded (normal, flat on R)    theta = u
         interval [lo, hi]                theta = lo + (hi - lo) sigmoid(u)
         (0, inf) (log-normal)            theta = exp(u)
-        [lo, inf) / (-inf, hi] (flat)    theta = lo + exp(u) / hi - exp(u)
-    and, for a component whose ellipticity is restricted to the disc
+        [lo, inf) / (-inf, hi]           theta = lo + exp(u) / hi - exp(u)
+    (uniform, truncated-normal and flat priors take the form their finite
+    bounds give) and, for a component whose ellipticity is restricted to the disc
     |e| < emax while both e priors are unbounded, the radial map
         e = v emax tanh(|v|)/|v|.
   * Counter-based random numbers: SplitMix64 (Steele, Lea & Flood 2014), used
@@ -59,14 +60,14 @@ class Bijector:
         self.rmax = np.zeros(P)  # disc radius, on the e1 index of a disc pair
         for k, kind in enumerate(kinds):
             lo_k, hi_k = self.lo[k], self.hi[k]
+            bounded = kind in ("uniform", "truncnorm", "flat")
             if kind == "lognormal":
                 self.mode[k] = EXP
-            elif kind in ("uniform", "truncnorm") or (
-                    kind == "flat" and math.isfinite(lo_k) and math.isfinite(hi_k)):
+            elif bounded and math.isfinite(lo_k) and math.isfinite(hi_k):
                 self.mode[k] = INTERVAL
-            elif kind == "flat" and math.isfinite(lo_k):
+            elif bounded and math.isfinite(lo_k):
                 self.mode[k] = LOWER
-            elif kind == "flat" and math.isfinite(hi_k):
+            elif bounded and math.isfinite(hi_k):
                 self.mode[k] = UPPER
             else:
                 self.mode[k] = ID

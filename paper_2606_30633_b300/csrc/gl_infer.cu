@@ -62,14 +62,17 @@ __global__ void k_bij_setup(const gl::PriorDev* pr, const float* emax, int P, in
   for (int k = 0; k < P; ++k) {
     const int kind = pr[k].kind;
     const float lo = pr[k].lo, hi = pr[k].hi;
+    // normal: unbounded; log-normal: (0, inf); uniform, truncated normal and
+    // flat: by which of their bounds are finite
+    const bool bounded = kind == 0 || kind == 1 || kind == 3;
     int m = BJ_ID;
     if (kind == 4)
       m = BJ_EXP;
-    else if (kind == 1 || kind == 3 || (kind == 0 && isfinite(lo) && isfinite(hi)))
+    else if (bounded && isfinite(lo) && isfinite(hi))
       m = BJ_INTERVAL;
-    else if (kind == 0 && isfinite(lo))
+    else if (bounded && isfinite(lo))
       m = BJ_LOWER;
-    else if (kind == 0 && isfinite(hi))
+    else if (bounded && isfinite(hi))
       m = BJ_UPPER;
     bj[k] = BijDev{m, lo, hi, 0.f};
   }

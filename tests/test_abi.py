@@ -93,3 +93,26 @@ def test_invalid_sigma_and_prior(lib):
     keep[3][0].lo, keep[3][0].hi = 2.0, 1.0
     assert lib.gl_system_create(ctypes.byref(d), ctypes.byref(h)) == gl.GL_EINVAL
     assert "prior" in gl.last_error()
+
+
+def test_inference_entry_points_reject_bad_arguments(lib):
+    """Host-side validation of the inference layer (no GPU work is issued)."""
+    P = ctypes.c_void_p
+    assert lib.gl_bijector_forward(None, None, 0, None, None, None) == gl.GL_EINVAL
+    assert lib.gl_bijector_inverse(None, None, 0, None, None) == gl.GL_EINVAL
+    assert lib.gl_logp_grad_unconstrained(None, None, 0, None, None, 0, None) == gl.GL_EINVAL
+    assert lib.gl_logp_grad_backward(None, None, 0, None, None, None, 0, None) == gl.GL_EINVAL
+    assert lib.gl_map_adam(None, None, None, None, 0, 0, 0, 1e-2, 0.9, 0.999, 1e-8, None, 0,
+                           None) == gl.GL_EINVAL
+    assert lib.gl_svi_adabelief(None, None, None, 1, 1, 0, 1e-4, 0.95, 0.99, 1e-16, 0, None, 0,
+                                None) == gl.GL_EINVAL
+    h = P()
+    assert lib.gl_hmc_create(None, None, None, ctypes.byref(h), None) == gl.GL_EINVAL
+    assert h.value is None
+    assert lib.gl_hmc_create(None, None, None, None, None) == gl.GL_EINVAL
+    assert lib.gl_hmc_run(None, 1, 0, None, None, None) == gl.GL_EINVAL
+    assert lib.gl_hmc_end_adaptation(None, 1, None) == gl.GL_EINVAL
+    assert lib.gl_hmc_set_inv_mass(None, None, None) == gl.GL_EINVAL
+    assert lib.gl_hmc_state(None, None, None, None, None, None) == gl.GL_EINVAL
+    assert lib.gl_hmc_destroy(None) == gl.GL_OK
+    assert "NULL" in gl.last_error() or "sampler" in gl.last_error()
