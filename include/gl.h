@@ -375,7 +375,9 @@ enum {
 };
 
 /* Creates a sampler at u0 (device [B][P], copied); M^-1 starts at ones.
- * Evaluates log p~ and its gradient at u0 on the stream and waits for it. */
+ * Evaluates log p~ and its gradient at u0 on the stream and waits for it.
+ * The sampler uses the system (and its attached surrogate) until it is
+ * destroyed: destroy it first. */
 gl_status gl_hmc_create(gl_system* sys, const gl_hmc_desc* desc, const float* u0,
                         gl_hmc** out, void* stream);
 

@@ -834,6 +834,7 @@ struct gl_hmc {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   void *key_scratch = nullptr, *key_table = nullptr;
+  const void* key_sur = nullptr;
 };
 
 namespace gl {
@@ -847,6 +848,7 @@ struct InferState {
   struct MapKey {
     float *u, *m, *v, *logp;
     void *scratch, *table;
+    const void* sur;
     int B, n, defl;
   } map_key{};
   float* map_buf = nullptr;  // theta, logp, grad [B(2P + 1)]
@@ -857,6 +859,7 @@ struct InferState {
   struct SviKey {
     float *phi, *opt;
     void *scratch, *table;
+    const void* sur;
     int n, defl;
     unsigned long long seed;
   } svi_key{};
@@ -1030,6 +1033,7 @@ gl_status gl_map_adam(gl_system* sys, float* u, float* m, float* v, int B, int n
   key.u = u; key.m = m; key.v = v; key.logp = logp;
   key.scratch = sp.scratch;
   key.table = const_cast<float4*>(sp.table);
+  key.sur = sys->sur;
   key.B = B; key.n = n_steps; key.defl = (int)defl;
   if (!f->map_exec || std::memcmp(&key, &f->map_key, sizeof key) != 0) {
     if (f->map_exec) {
@@ -1175,7 +1179,8 @@ gl_status gl_hmc_run(gl_hmc* h, int n, int flags, float* draws, float* accept, v
   size_t dyn;
   if ((r = gl::eval_prepare(sys, h->B, h->defl, true, &sp, &dyn)) != GL_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
-  if (!h->exec || h->key_scratch != (void*)sp.scratch || h->key_table != (const void*)sp.table) {
+  if (!h->exec || h->key_scratch != (void*)sp.scratch || h->key_table != (const void*)sp.table ||
+      h->key_sur != (const void*)sys->sur) {
     if (h->exec) {
       cudaGraphExecDestroy(h->exec);
       h->exec = nullptr;
@@ -1214,6 +1219,7 @@ gl_status gl_hmc_run(gl_hmc* h, int n, int flags, float* draws, float* accept, v
     }
     h->key_scratch = sp.scratch;
     h->key_table = const_cast<float4*>(sp.table);
+    h->key_sur = sys->sur;
   }
   k_set_hmc_run<<<1, 1, 0, st>>>(h->ctl, flags, draws, accept);
   GI_CUDA(cudaGetLastError(), "control");
@@ -1315,6 +1321,7 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
   key.phi = phi; key.opt = opt;
   key.scratch = sp.scratch;
   key.table = const_cast<float4*>(sp.table);
+  key.sur = sys->sur;
   key.n = n; key.defl = (int)defl; key.seed = seed;
   if (!f->svi_exec || std::memcmp(&key, &f->svi_key, sizeof key) != 0) {
     if (f->svi_exec) {
