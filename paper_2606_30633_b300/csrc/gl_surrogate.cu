@@ -31,9 +31,7 @@ struct gl_surrogate {
 
 namespace {
 
-constexpr int TILE = 128;   // rows per training CTA (8 warps x 16)
-constexpr int SROW = 136;   // padded row stride (bf16) of transposed tiles
-constexpr int SPROW = 72;   // padded row stride (bf16) of the SiLU' tiles
+constexpr int TILE = 128;   // samples per training CTA (one per thread)
 
 gl_status fail(gl_status st, const std::string& msg) {
   gl::set_last_error(msg);
@@ -148,226 +146,6 @@ __global__ void k_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ 
     v = o < NOUT ? p[OFF_W5 + o * H + i] : 0.f;
   }
   wb[k] = __float2bfloat16_rn(v);
-}
-
-__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) {
-  return *reinterpret_cast<const uint32_t*>(p);
-}
-
-// CTA-wide weight-gradient contraction dW[o][i] = sum_rows dZ[row][o] A[row][i]
-// over the 128 rows of the tile, from transposed tiles dZT[o][row], AT[i][row]
-// (row stride SROW). Warp w owns output rows 16 mt.., columns 8 nt.. as listed.
-__device__ __forceinline__ void dw_tile(const __nv_bfloat16* dZT, const __nv_bfloat16* AT, int mt,
-                                        int nt, float (&acc)[4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-  acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
-#pragma unroll
-  for (int kk = 0; kk < TILE / 16; ++kk) {
-    uint32_t a[4];
-    const __nv_bfloat16* za = dZT + (16 * mt + g) * SROW + kk * 16 + 2 * c;
-    a[0] = lds32(za);
-    a[1] = lds32(za + 8 * SROW);
-    a[2] = lds32(za + 8);
-    a[3] = lds32(za + 8 * SROW + 8);
-    const __nv_bfloat16* bb = AT + (8 * nt + g) * SROW + kk * 16 + 2 * c;
-    mma16816(acc, a, lds32(bb), lds32(bb + 8));
-  }
-}
-
-struct TrainSmem {
-  __nv_bfloat16 sp[4][TILE * SPROW];  // SiLU'(z) per hidden layer, [row][col]
-  __nv_bfloat16 AT0[16 * SROW];       // inputs, transposed [col][row]
-  __nv_bfloat16 AT[4][H * SROW];      // hidden activations, transposed
-  __nv_bfloat16 dZT[H * SROW];        // current layer's dZ, transposed
-  float loss[8];
-};
-
-// One training step for a 128-row tile: forward, MSE loss, backward; the
-// tile's loss and gradient go to its own slot (no atomics).
-// grid = batch / 128, block = 256.
-__global__ void __launch_bounds__(256, 1)
-k_train(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
-        const float4* __restrict__ X, const float2* __restrict__ Y, long long n_data,
-        long long row0, long long stride, float inv_batch, float* __restrict__ gpart,
-        float* __restrict__ lpart) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, c = lane & 3;
-  const int r0 = warp * 16;
-  float* gp = gpart + (size_t)blockIdx.x * NPARAM;
-
-  for (int k = tid; k < 16 * SROW; k += 256) S.AT0[k] = __float2bfloat16_rn(0.f);
-  for (int k = tid; k < H * SROW; k += 256) S.dZT[k] = __float2bfloat16_rn(0.f);
-  __syncthreads();
-
-  // rows of this thread: r0+g and r0+g+8 (data index by a strided permutation)
-  long long idx[2];
-  float x[2][4], tgt[2][2];
-  for (int h = 0; h < 2; ++h) {
-    const long long tr = (long long)blockIdx.x * TILE + r0 + g + 8 * h;
-    idx[h] = (row0 + tr * stride) % n_data;
-    const float4 v = X[idx[h]];
-    features(v.x, v.y, v.z, v.w, x[h]);
-    const float2 t = Y[idx[h]];
-    tgt[h][0] = t.x;
-    tgt[h][1] = t.y;
-  }
-  if (c < 2)
-    for (int h = 0; h < 2; ++h) {
-      S.AT0[(2 * c) * SROW + r0 + g + 8 * h] = __float2bfloat16_rn(x[h][2 * c]);
-      S.AT0[(2 * c + 1) * SROW + r0 + g + 8 * h] = __float2bfloat16_rn(x[h][2 * c + 1]);
-    }
-  // forward
-  uint32_t a1[1][4];
-  input_frag(x[0], x[1], a1);
-  float z[8][4];
-  uint32_t a[4][4];
-  layer_mma<1>(a1, wb + BOFF_P1, z);
-  const float* bias[4] = {params + OFF_B1, params + OFF_B2, params + OFF_B3, params + OFF_B4};
-  const __nv_bfloat16* Wl[3] = {wb + BOFF_P2, wb + BOFF_P3, wb + BOFF_P4};
-  for (int l = 0; l < 4; ++l) {
-    if (l > 0) layer_mma<4>(a, Wl[l - 1], z);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int col = nt * 8 + 2 * c + (j & 1), row = r0 + g + 8 * (j >> 1);
-        const float zz = z[nt][j] + bias[l][col];
-        const float s = sigm(zz);
-        const float act = zz * s;
-        z[nt][j] = act;
-        S.sp[l][row * SPROW + col] = __float2bfloat16_rn(s * (1.f + zz * (1.f - s)));
-        S.AT[l][col * SROW + row] = __float2bfloat16_rn(act);
-      }
-    c_to_a(z, a);
-  }
-  float y[4];
-  out_mma(a, wb + BOFF_P5, y);
-  // loss and output gradient (cols 0, 1 live in lanes c == 0)
-  float dz5[4] = {0.f, 0.f, 0.f, 0.f};
-  float lsum = 0.f;
-  if (c == 0) {
-    for (int h = 0; h < 2; ++h)
-      for (int o = 0; o < 2; ++o) {
-        const float e = y[2 * h + o] + params[OFF_B5 + o] - tgt[h][o];
-        lsum += e * e;
-        dz5[2 * h + o] = 2.f * e * inv_batch;
-      }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-  if (lane == 0) S.loss[warp] = lsum;
-  // output layer: dZ5^T (rows 0, 1 of dZT)
-  if (c == 0)
-    for (int h = 0; h < 2; ++h)
-      for (int o = 0; o < 2; ++o)
-        S.dZT[o * SROW + r0 + g + 8 * h] = __float2bfloat16_rn(dz5[2 * h + o]);
-  // db5
-  {
-    float s0 = dz5[0] + dz5[2], s1 = dz5[1] + dz5[3];
-    for (int o = 4; o < 32; o <<= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    }
-    // per-warp partial: summed over warps below through shared memory
-    __shared__ float db5[8][2];
-    if (lane == 0) {
-      db5[warp][0] = s0;
-      db5[warp][1] = s1;
-    }
-    __syncthreads();
-    if (tid < 2) {
-      float v = 0.f;
-      for (int w = 0; w < 8; ++w) v += db5[w][tid];
-      gp[OFF_B5 + tid] = v;
-    }
-    if (tid == 0) {
-      float v = 0.f;
-      for (int w = 0; w < 8; ++w) v += S.loss[w];
-      lpart[blockIdx.x] = v;
-    }
-  }
-  // dW5 = dZ5^T A4: warp w -> output rows 0..15 (0, 1 real), columns 8w..8w+7
-  {
-    float acc[4];
-    dw_tile(S.dZT, S.AT[3], 0, warp, acc);
-    if (g < NOUT) {
-      gp[OFF_W5 + g * H + warp * 8 + 2 * c] = acc[0];
-      gp[OFF_W5 + g * H + warp * 8 + 2 * c + 1] = acc[1];
-    }
-  }
-  // dA4 = dZ5 W5
-  float dA[8][4];
-  {
-    uint32_t ad[1][4];
-    ad[0][0] = pack_bf16(dz5[0], dz5[1]);
-    ad[0][1] = pack_bf16(dz5[2], dz5[3]);
-    ad[0][2] = 0u;
-    ad[0][3] = 0u;
-    layer_mma<1>(ad, wb + BOFF_T5, dA);
-  }
-  const __nv_bfloat16* Tl[3] = {wb + BOFF_T2, wb + BOFF_T3, wb + BOFF_T4};
-  const int OFF_W[4] = {OFF_W1, OFF_W2, OFF_W3, OFF_W4};
-  const int OFF_B[4] = {OFF_B1, OFF_B2, OFF_B3, OFF_B4};
-  for (int l = 3; l >= 0; --l) {
-    __syncthreads();  // dZT / previous dW reads done
-    // dZ_l = dA_l * SiLU'(z_l)
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int col = nt * 8 + 2 * c + (j & 1), row = r0 + g + 8 * (j >> 1);
-        const float v = dA[nt][j] * __bfloat162float(S.sp[l][row * SPROW + col]);
-        dA[nt][j] = v;
-        S.dZT[col * SROW + row] = __float2bfloat16_rn(v);
-      }
-    // db_l (row sums): rows g and g+8, then over g
-    __shared__ float dbw[8][H];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        float s = dA[nt][e] + dA[nt][2 + e];
-        for (int o = 4; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (g == 0) dbw[warp][nt * 8 + 2 * c + e] = s;
-      }
-    __syncthreads();
-    if (tid < H) {
-      float v = 0.f;
-      for (int w = 0; w < 8; ++w) v += dbw[w][tid];
-      gp[OFF_B[l] + tid] = v;
-    }
-    // dW_l = dZ_l^T A_{l-1}
-    if (l > 0) {
-      const int mt = warp >> 1;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int nt = 4 * (warp & 1) + q;
-        float acc[4];
-        dw_tile(S.dZT, S.AT[l - 1], mt, nt, acc);
-        const int o = 16 * mt + g, i = nt * 8 + 2 * c;
-        gp[OFF_W[l] + o * H + i] = acc[0];
-        gp[OFF_W[l] + o * H + i + 1] = acc[1];
-        gp[OFF_W[l] + (o + 8) * H + i] = acc[2];
-        gp[OFF_W[l] + (o + 8) * H + i + 1] = acc[3];
-      }
-      // dA_{l-1} = dZ_l W_l
-      uint32_t ad[4][4];
-      c_to_a(dA, ad);
-      layer_mma<4>(ad, Tl[l - 1], dA);
-    } else if (warp < 4) {
-      // dW1 = dZ1^T X: output rows 16 warp.., input columns 0..7 (0..3 real)
-      float acc[4];
-      dw_tile(S.dZT, S.AT0, warp, 0, acc);
-      const int o = 16 * warp + g;
-      if (c < 2) {
-        gp[OFF_W1 + o * NIN + 2 * c] = acc[0];
-        gp[OFF_W1 + o * NIN + 2 * c + 1] = acc[1];
-        gp[OFF_W1 + (o + 8) * NIN + 2 * c] = acc[2];
-        gp[OFF_W1 + (o + 8) * NIN + 2 * c + 1] = acc[3];
-      }
-    }
-  }
 }
 
 // Sum of the tiles' gradients and Adam (FP32 master weights); writes the
@@ -547,13 +325,13 @@ constexpr int A_BYTES = 128 * 64 * 2;   // hidden operands [128][64]
 constexpr int W1_BYTES = 64 * 16 * 2;
 constexpr int WH_BYTES = 64 * 64 * 2;
 constexpr int W5_BYTES = 16 * 64 * 2;   // output layer padded to N = 16
-constexpr int OFF_W1 = 0;
-constexpr int OFF_WH = OFF_W1 + W1_BYTES;
-constexpr int OFF_W5 = OFF_WH + 3 * WH_BYTES;
-constexpr int OFF_A0 = OFF_W5 + W5_BYTES;
-constexpr int OFF_A = OFF_A0 + A0_BYTES;
-constexpr int OFF_NODE = OFF_A + 4 * A_BYTES;
-constexpr int SMEM_BYTES = OFF_NODE + TABLE_M * 2 * 16;
+constexpr int TB_W1 = 0;  // shared-memory byte offsets of the table kernel
+constexpr int TB_WH = TB_W1 + W1_BYTES;
+constexpr int TB_W5 = TB_WH + 3 * WH_BYTES;
+constexpr int TB_A0 = TB_W5 + W5_BYTES;
+constexpr int TB_A = TB_A0 + A0_BYTES;
+constexpr int TB_NODE = TB_A + 4 * A_BYTES;
+constexpr int SMEM_BYTES = TB_NODE + TABLE_M * 2 * 16;
 constexpr long long WAIT_LIMIT = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -668,11 +446,11 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ param
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t bar;
   const int t = threadIdx.x, w = t >> 5;
-  load_operand(sm + OFF_W1, wb + BOFF_P1, 64, 16, 64);
-  load_operand(sm + OFF_WH, wb + BOFF_P2, 64, 64, 64);
-  load_operand(sm + OFF_WH + WH_BYTES, wb + BOFF_P3, 64, 64, 64);
-  load_operand(sm + OFF_WH + 2 * WH_BYTES, wb + BOFF_P4, 64, 64, 64);
-  load_operand(sm + OFF_W5, wb + BOFF_P5, 16, 64, 8);
+  load_operand(sm + TB_W1, wb + BOFF_P1, 64, 16, 64);
+  load_operand(sm + TB_WH, wb + BOFF_P2, 64, 64, 64);
+  load_operand(sm + TB_WH + WH_BYTES, wb + BOFF_P3, 64, 64, 64);
+  load_operand(sm + TB_WH + 2 * WH_BYTES, wb + BOFF_P4, 64, 64, 64);
+  load_operand(sm + TB_W5, wb + BOFF_P5, 16, 64, 8);
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -686,11 +464,11 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ param
   to_async();
   const uint32_t tb = tmem_base;
   const uint32_t lane_addr = tb + ((uint32_t)(32 * w) << 16);
-  unsigned char* A0 = sm + OFF_A0;
-  unsigned char* A = sm + OFF_A;
-  float4(*node)[2] = reinterpret_cast<float4(*)[2]>(sm + OFF_NODE);
-  const uint32_t a0 = smem_u32(A0), aa = smem_u32(A), w1 = smem_u32(sm + OFF_W1);
-  const uint32_t wh = smem_u32(sm + OFF_WH), w5 = smem_u32(sm + OFF_W5);
+  unsigned char* A0 = sm + TB_A0;
+  unsigned char* A = sm + TB_A;
+  float4(*node)[2] = reinterpret_cast<float4(*)[2]>(sm + TB_NODE);
+  const uint32_t a0 = smem_u32(A0), aa = smem_u32(A), w1 = smem_u32(sm + TB_W1);
+  const uint32_t wh = smem_u32(sm + TB_WH), w5 = smem_u32(sm + TB_W5);
   uint32_t phase = 0;
   bool ok = true;
   // tangent seeds of the normalised inputs, rounded to BF16 like every operand
@@ -815,6 +593,301 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ param
   if (w == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tb),
                  "r"(TMEM_COLS));
+}
+
+// --------------------------------------- training step on tcgen05 ----
+// One training step for a 128-sample tile (thread t = sample t): forward,
+// MSE loss, backward, with every 64-wide contraction on tcgen05.mma and FP32
+// accumulators in tensor memory:
+//   forward   z_l = A_{l-1} W_l^T          (M = 128 samples, N = 64, K = 16 / 64)
+//   backward  dA_{l-1} = dZ_l W_l          (M = 128, N = 64, K = 64; B = W_l^T)
+//             dW_l = dZ_l^T A_{l-1}        (M = 64 outputs padded to 128 with zero
+//                                           rows, N = 64 / 16, K = 128 samples)
+// The 2-wide output layer and its gradients run on the CUDA cores. BF16
+// rounding happens where the warp-level version rounds: inputs, activations,
+// SiLU', dZ and the weights. The tile's loss and gradient go to its own slot.
+namespace tc {
+
+constexpr int TR_W1 = 0;                      // P1 [64][16]
+constexpr int TR_WH = TR_W1 + 64 * 16 * 2;    // P2..P4 [64][64]
+constexpr int TR_TH = TR_WH + 3 * 64 * 64 * 2;  // T2..T4 [64][64]
+constexpr int TR_A = TR_TH + 3 * 64 * 64 * 2;   // [128][64]: forward operand, then dZ
+constexpr int TR_X0 = TR_A + 128 * 64 * 2;      // inputs [128][16]
+constexpr int TR_XT = TR_X0 + 128 * 16 * 2;     // inputs^T [16][128]
+constexpr int TR_AT = TR_XT + 16 * 128 * 2;     // a_1^T..a_3^T [64][128]
+constexpr int TR_SP = TR_AT + 3 * 64 * 128 * 2; // SiLU'_1..3 [128][64] row-major
+constexpr int TR_DZT = TR_SP + 3 * 128 * 64 * 2;  // dZ^T [128][128], rows 64.. zero
+constexpr int TR_RED = TR_DZT + 128 * 128 * 2;  // column-sum scratch [4][128] float
+constexpr int TR_SMEM = TR_RED + 4 * 128 * 4;
+constexpr uint32_t TR_TMEM_COLS = 128;          // [0, 64) forward / dA, [64, 128) dW
+
+// Element (r, k) of an [R][128] operand in the core-matrix layout.
+__device__ __forceinline__ void put_t(unsigned char* base, int r, int k, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(base + core_off(r, k, 128)) = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// Sums of N per-thread values over the 128 threads: each warp's 32-value
+// chunks by reduce-scatter, then the four warps; dst[k] = sum (k < N).
+template <int N>
+__device__ void colsum(const float (&v)[N], float* red, float* __restrict__ dst) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < N / 32; ++c) {
+    float x[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x[k] = v[32 * c + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < o; ++i) {
+        const float keep = up ? x[i + o] : x[i];
+        const float give = up ? x[i] : x[i + o];
+        x[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+      }
+    }
+    red[w * N + 32 * c + lane] = x[0];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < N; k += NT) dst[k] = red[k] + red[N + k] + red[2 * N + k] + red[3 * N + k];
+  __syncthreads();
+}
+
+}  // namespace tc
+
+__global__ void __launch_bounds__(tc::NT, 1)
+k_train_tc(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
+           const float4* __restrict__ X, const float2* __restrict__ Y, long long n_data,
+           long long row0, long long stride, float inv_batch, float* __restrict__ gpart,
+           float* __restrict__ lpart, int* __restrict__ timeout) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ float lsum_w[4];
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  float* gp = gpart + (size_t)blockIdx.x * NPARAM;
+  float* red = reinterpret_cast<float*>(sm + TR_RED);
+  // weights in the operand layout; zero the transposed buffers (padding rows)
+  load_operand(sm + TR_W1, wb + BOFF_P1, 64, 16, 64);
+  load_operand(sm + TR_WH, wb + BOFF_P2, 64, 64, 64);
+  load_operand(sm + TR_WH + 8192, wb + BOFF_P3, 64, 64, 64);
+  load_operand(sm + TR_WH + 16384, wb + BOFF_P4, 64, 64, 64);
+  load_operand(sm + TR_TH, wb + BOFF_T2, 64, 64, 64);
+  load_operand(sm + TR_TH + 8192, wb + BOFF_T3, 64, 64, 64);
+  load_operand(sm + TR_TH + 16384, wb + BOFF_T4, 64, 64, 64);
+  for (int k = t; k < (TR_AT - TR_XT) / 16; k += NT)
+    reinterpret_cast<uint4*>(sm + TR_XT)[k] = make_uint4(0u, 0u, 0u, 0u);
+  for (int k = t; k < (TR_RED - TR_DZT) / 16; k += NT)
+    reinterpret_cast<uint4*>(sm + TR_DZT)[k] = make_uint4(0u, 0u, 0u, 0u);
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TR_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  // the sample
+  const long long tr = (long long)blockIdx.x * NT + t;
+  const long long idx = (row0 + tr * stride) % n_data;
+  float x[4];
+  {
+    const float4 v = X[idx];
+    features(v.x, v.y, v.z, v.w, x);
+  }
+  const float2 tgt = Y[idx];
+  {
+    const float v8[8] = {x[0], x[1], x[2], x[3], 0.f, 0.f, 0.f, 0.f};
+    const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    put8(sm + TR_X0, t, 0, 16, v8);
+    put8(sm + TR_X0, t, 8, 16, z8);
+    for (int f = 0; f < 4; ++f) put_t(sm + TR_XT, f, t, x[f]);
+  }
+  to_async();
+  const uint32_t tb = tmem_base;
+  const uint32_t lane_addr = tb + ((uint32_t)(32 * w) << 16);
+  const uint32_t sA = smem_u32(sm + TR_A), sX0 = smem_u32(sm + TR_X0), sXT = smem_u32(sm + TR_XT);
+  const uint32_t sAT = smem_u32(sm + TR_AT), sDZT = smem_u32(sm + TR_DZT);
+  const uint32_t sW1 = smem_u32(sm + TR_W1), sWH = smem_u32(sm + TR_WH), sTH = smem_u32(sm + TR_TH);
+  uint32_t phase = 0;
+  bool ok = true;
+  auto wait = [&]() -> bool {
+    const bool got = __syncthreads_and(wait_phase(&bar, phase));
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return got;
+  };
+  // ---- forward ----
+  if (t == 0) {
+    mma(tb, sdesc(sX0, 256), sdesc(sW1, 256), idesc(128, 64), 0u);
+    commit(&bar);
+  }
+  float a4[64], s4[64];
+  const int OFFB[4] = {mlp::OFF_B1, mlp::OFF_B2, mlp::OFF_B3, mlp::OFF_B4};
+  for (int l = 1; l <= 4 && ok; ++l) {
+    if (!wait()) { ok = false; break; }
+    const float* bias = params + OFFB[l - 1];
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+      float z[16];
+      ld16(lane_addr + c0, z);
+      wait_ld();
+      float a[16], sp[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float zz = z[j] + bias[c0 + j];
+        const float sg = sigm(zz);
+        a[j] = bfr(zz * sg);
+        sp[j] = bfr(sg * (1.f + zz * (1.f - sg)));
+      }
+      if (l < 4) {
+        put8(sm + TR_A, t, c0, 64, a);
+        put8(sm + TR_A, t, c0 + 8, 64, a + 8);
+        unsigned char* at = sm + TR_AT + (l - 1) * 16384;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) put_t(at, c0 + j, t, a[j]);
+        uint4* spr = reinterpret_cast<uint4*>(sm + TR_SP + (l - 1) * 16384 + t * 128 + c0 * 2);
+        spr[0] = make_uint4(pack_bf16(sp[0], sp[1]), pack_bf16(sp[2], sp[3]),
+                            pack_bf16(sp[4], sp[5]), pack_bf16(sp[6], sp[7]));
+        spr[1] = make_uint4(pack_bf16(sp[8], sp[9]), pack_bf16(sp[10], sp[11]),
+                            pack_bf16(sp[12], sp[13]), pack_bf16(sp[14], sp[15]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          a4[c0 + j] = a[j];
+          s4[c0 + j] = sp[j];
+        }
+      }
+    }
+    if (l < 4) {
+      to_async();
+      if (t == 0) {
+        const uint32_t wl = sWH + (uint32_t)(l - 1) * 8192;
+        for (int kk = 0; kk < 4; ++kk)
+          mma(tb, sdesc(sA + kk * 256, 1024), sdesc(wl + kk * 256, 1024), idesc(128, 64),
+              kk > 0 ? 1u : 0u);
+        commit(&bar);
+      }
+    }
+  }
+  if (ok) {
+    // ---- output layer, loss and its gradients (CUDA cores) ----
+    float y[2], dz5[2], dz5b[2];
+    for (int o = 0; o < 2; ++o) {
+      float acc = 0.f;
+      for (int i = 0; i < 64; ++i) acc = fmaf(__bfloat162float(wb[BOFF_P5 + o * 64 + i]), a4[i], acc);
+      y[o] = acc;
+    }
+    const float e0 = y[0] + params[mlp::OFF_B5] - tgt.x, e1 = y[1] + params[mlp::OFF_B5 + 1] - tgt.y;
+    float ls = e0 * e0 + e1 * e1;
+    dz5[0] = 2.f * e0 * inv_batch;
+    dz5[1] = 2.f * e1 * inv_batch;
+    dz5b[0] = bfr(dz5[0]);
+    dz5b[1] = bfr(dz5[1]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
+    if (lane == 0) lsum_w[w] = ls;
+    {
+      float db5[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) db5[k] = k < 2 ? dz5[k] : 0.f;
+      float tmp[2];
+      colsum<32>(db5, red, red + 512 - 32);  // scratch tail, read back below
+      if (t < 2) tmp[0] = red[512 - 32 + t];
+      __syncthreads();
+      if (t < 2) gp[mlp::OFF_B5 + t] = tmp[0];
+      if (t == 0) lpart[blockIdx.x] = lsum_w[0] + lsum_w[1] + lsum_w[2] + lsum_w[3];
+    }
+    {
+      float dw5[128];
+#pragma unroll
+      for (int k = 0; k < 128; ++k) dw5[k] = dz5b[k >> 6] * a4[k & 63];
+      colsum<128>(dw5, red, gp + mlp::OFF_W5);
+    }
+    // dA4 = dZ5 W5, dZ4 = dA4 * SiLU'(z4)
+    float dz[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) {
+      const float da = dz5b[0] * __bfloat162float(wb[BOFF_P5 + i]) +
+                       dz5b[1] * __bfloat162float(wb[BOFF_P5 + 64 + i]);
+      dz[i] = da * s4[i];
+    }
+    // ---- backward through the hidden layers ----
+    const int OFFW[4] = {mlp::OFF_W1, mlp::OFF_W2, mlp::OFF_W3, mlp::OFF_W4};
+    for (int l = 4; l >= 1 && ok; --l) {
+      colsum<64>(dz, red, gp + OFFB[l - 1]);  // db_l
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 8) {
+        float v8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v8[j] = dz[c0 + j];
+        put8(sm + TR_A, t, c0, 64, v8);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) put_t(sm + TR_DZT, c0 + j, t, v8[j]);
+      }
+      to_async();
+      if (t == 0) {
+        // dW_l = dZ_l^T A_{l-1}: rows 64.. of dZ^T are zero
+        const uint32_t bmat = l > 1 ? sAT + (uint32_t)(l - 2) * 16384 : sXT;
+        const uint32_t idw = idesc(128, l > 1 ? 64 : 16);
+        for (int kk = 0; kk < 8; ++kk)
+          mma(tb + 64u, sdesc(sDZT + kk * 256, 2048), sdesc(bmat + kk * 256, 2048), idw,
+              kk > 0 ? 1u : 0u);
+        if (l > 1) {  // dA_{l-1} = dZ_l W_l with B = W_l^T
+          const uint32_t tl = sTH + (uint32_t)(l - 2) * 8192;
+          for (int kk = 0; kk < 4; ++kk)
+            mma(tb, sdesc(sA + kk * 256, 1024), sdesc(tl + kk * 256, 1024), idesc(128, 64),
+                kk > 0 ? 1u : 0u);
+        }
+        commit(&bar);
+      }
+      if (!wait()) { ok = false; break; }
+      // dW_l rows (outputs) live in TMEM lanes 0..63: warps 0 and 1
+      const int in_dim = l > 1 ? 64 : NIN;
+      if (w < 2) {
+        for (int c0 = 0; c0 < (l > 1 ? 64 : 16); c0 += 16) {
+          float v[16];
+          ld16(lane_addr + 64 + c0, v);
+          wait_ld();
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < in_dim) gp[OFFW[l - 1] + t * in_dim + c0 + j] = v[j];
+        }
+      }
+      if (l > 1) {
+        const unsigned char* spl = sm + TR_SP + (l - 2) * 16384 + t * 128;
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+          float v[16];
+          ld16(lane_addr + c0, v);
+          wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            dz[c0 + j] = v[j] * __bfloat162float(
+                                    reinterpret_cast<const __nv_bfloat16*>(spl)[c0 + j]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+  }
+  if (!ok) {
+    if (t == 0) {
+      atomicExch(timeout, 1);
+      lpart[blockIdx.x] = __int_as_float(0x7fc00000);
+    }
+    for (int k = t; k < NPARAM; k += NT) gp[k] = __int_as_float(0x7fc00000);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (w == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tb),
+                 "r"(TR_TMEM_COLS));
 }
 
 __device__ int g_table_timeout = 0;
@@ -954,12 +1027,14 @@ gl_status gl_surrogate_loss_grad(const gl_surrogate* s, const float* x, const fl
   SUR_CUDA(cudaMalloc(&tb.gpart, (size_t)ntiles * NPARAM * sizeof(float)), "alloc");
   SUR_CUDA(cudaMalloc(&tb.lpart, ntiles * sizeof(float)), "alloc");
   SUR_CUDA(cudaMalloc(&tb.loss, NPARAM * sizeof(float) + sizeof(float)), "alloc");
-  SUR_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(TrainSmem)),
+  SUR_CUDA(cudaFuncSetAttribute(gl::k_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                gl::tc::TR_SMEM),
            "smem limit");
-  k_train<<<ntiles, 256, sizeof(TrainSmem)>>>(s->wb, s->params, reinterpret_cast<const float4*>(x),
-                                              reinterpret_cast<const float2*>(target), N, 0, 1,
-                                              1.f / N, tb.gpart, tb.lpart);
+  int* flag = nullptr;
+  SUR_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), gl::g_table_timeout), "flag");
+  gl::k_train_tc<<<ntiles, gl::tc::NT, gl::tc::TR_SMEM>>>(
+      s->wb, s->params, reinterpret_cast<const float4*>(x),
+      reinterpret_cast<const float2*>(target), N, 0, 1, 1.f / N, tb.gpart, tb.lpart, flag);
   k_adam<<<(NPARAM + 255) / 256, 256>>>(nullptr, nullptr, nullptr, tb.gpart, ntiles, 0.f, 0.f, 0.f,
                                        0.f, 1.f, 1.f, tb.loss);
   k_sum<<<1, 256>>>(tb.lpart, ntiles, tb.loss + NPARAM);
@@ -1008,9 +1083,12 @@ gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** ou
   k_gen_data<<<1184, 256>>>(tb.X, tb.Y, n, d->seed_data, d->q_lo, d->q_hi, d->gamma_lo,
                             d->gamma_hi, logf(d->r_lo), logf(d->r_hi));
   k_init_params<<<(NPARAM + 255) / 256, 256>>>(s->params, d->seed_init);
-  if (cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(TrainSmem)) != cudaSuccess)
+  if (cudaFuncSetAttribute(gl::k_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           gl::tc::TR_SMEM) != cudaSuccess)
     return bail(fail(GL_ECUDA, "training kernel shared-memory limit"));
+  int* flag = nullptr;
+  if (cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), gl::g_table_timeout) != cudaSuccess)
+    return bail(fail(GL_ECUDA, "training kernel flag"));
   const long long steps_per_epoch = (n + d->batch - 1) / d->batch;
   const long long total = steps_per_epoch * d->epochs;
   const float b1 = 0.9f, b2 = 0.999f;
@@ -1025,8 +1103,9 @@ gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** ou
     bc2 *= b2;
     k_pack<<<(NBF16 + 255) / 256, 256>>>(s->params, s->wb);
     const long long row0 = (it * (long long)d->batch) % n;
-    k_train<<<ntiles, 256, sizeof(TrainSmem)>>>(s->wb, s->params, tb.X, tb.Y, n, row0, stride,
-                                                1.f / d->batch, tb.gpart, tb.lpart);
+    gl::k_train_tc<<<ntiles, gl::tc::NT, gl::tc::TR_SMEM>>>(s->wb, s->params, tb.X, tb.Y, n, row0,
+                                                            stride, 1.f / d->batch, tb.gpart,
+                                                            tb.lpart, flag);
     k_adam<<<(NPARAM + 255) / 256, 256>>>(s->params, tb.m, tb.v, tb.gpart, ntiles, lr, b1, b2,
                                          1e-8f, (float)(1.0 - bc1), (float)(1.0 - bc2), nullptr);
     if ((it & 255) == 0) {
