@@ -234,10 +234,10 @@ gl_status gl_logp_grad_noalloc(gl_system* sys, const float* theta, int B, float*
  * hypergeometric series the deflection uses, Sec. 3 mass model).
  * A 4 -> 64 -> 64 -> 64 -> 64 -> 2 SiLU MLP with inputs (q, gamma,
  * log(R/theta_E), vphi): q the EPL axis ratio, vphi the angle of q x' + i y'
- * in [0, 2 pi). It predicts the part of F = 2F1(1, t/2; 2 - t/2; -f e^{2 i vphi})
- * beyond its first two series terms, times 100:
- *   F = 1 + c1 z + c2 z^2 + y/100, z = -f e^{2 i vphi}, c1 = t/(4-t),
- *   c2 = c1 (2+t)/(6-t).
+ * in [0, 2 pi). It predicts F = 2F1(1, t/2; 2 - t/2; -f e^{2 i vphi}) beyond
+ * its first two series terms with the factor z^3 taken out, times 4:
+ *   F = 1 + c1 z + c2 z^2 + z^3 y/4, z = -f e^{2 i vphi}, c1 = t/(4-t),
+ *   c2 = c1 (2+t)/(6-t), y (complex) ~ 4 sum_{n>=3} c_n z^{n-3}.
  * BF16 weights and activations, FP32 accumulation (tensor cores), FP32
  * master weights. Parameter vector (FP32, gl_surrogate_num_params() floats):
  * W1[64][4], b1[64], W2[64][64], b2, W3, b3, W4, b4, W5[2][64], b5[2]
@@ -278,9 +278,18 @@ gl_status gl_surrogate_params(const gl_surrogate* sur, float* params_host);
 gl_status gl_surrogate_infer(const gl_surrogate* sur, const float* x, int N, float* y,
                              void* stream);
 
+/* The exact F = 2F1(1, t/2; 2 - t/2; -f e^{2 i vphi}) (Sec. 3 mass model,
+ * the series of Tessore & Metcalf 2015), summed in FP64 on the device until
+ * the terms fall below 1e-18, for N raw inputs x: device [N][4] = (q, gamma,
+ * ignored, vphi) -> F: device [N][2] (Re, Im, rounded to FP32); the judge of
+ * the surrogate's deflection error. Tuples outside 0.01 <= q <= 1,
+ * 1 < gamma < 3 (or not finite) give NaN. Asynchronous on stream; GL_EINVAL for N < 0 or
+ * NULL pointers with N > 0. */
+gl_status gl_series_F(const float* x, int N, float* F, void* stream);
+
 /* Mean squared training loss and its gradient w.r.t. the parameters for N
  * rows (N a multiple of 128): x device [N][4] raw inputs, target device
- * [N][2] in scaled output units (100 x the series remainder); loss_host and
+ * [N][2] in the network's output units (y above); loss_host and
  * grad_host [gl_surrogate_num_params()] receive the results. Synchronous. */
 gl_status gl_surrogate_loss_grad(const gl_surrogate* sur, const float* x, const float* target,
                                  int N, float* loss_host, float* grad_host);

@@ -11,7 +11,7 @@ from __future__ import annotations
 import numpy as np
 
 H, NIN, NOUT = 64, 4, 2
-OUT_SCALE = 100.0
+OUT_SCALE = 4.0
 SIZES = [("W1", (H, NIN)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, H)),
          ("b3", (H,)), ("W4", (H, H)), ("b4", (H,)), ("W5", (NOUT, H)), ("b5", (NOUT,))]
 NPARAM = sum(int(np.prod(s)) for _, s in SIZES)
@@ -106,6 +106,11 @@ def base_F(X):
 
 
 def surrogate_F(params, X):
-    """F predicted by the network: base terms + y / 100 (complex)."""
+    """F predicted by the network: base terms + z^3 y / OUT_SCALE (complex),
+    z = -f e^{2 i vphi}: the network stands for the series beyond its first
+    two terms with the factor z^3 taken out."""
     y, _ = forward(params, X)
-    return base_F(X) + (y[:, 0] + 1j * y[:, 1]) / OUT_SCALE
+    X = np.asarray(X, dtype=np.float64)
+    f = (1 - X[:, 0]) / (1 + X[:, 0])
+    z = -f * np.exp(2j * X[:, 3])
+    return base_F(X) + z ** 3 * (y[:, 0] + 1j * y[:, 1]) / OUT_SCALE

@@ -74,6 +74,7 @@ SIGNATURES = {
     "gl_surrogate_create": (ctypes.c_int, [_VP, ctypes.POINTER(_VP)]),
     "gl_surrogate_params": (ctypes.c_int, [_VP, _VP]),
     "gl_surrogate_infer": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP]),
+    "gl_series_F": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     "gl_surrogate_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "gl_surrogate_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "gl_surrogate_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_VP)]),
@@ -502,7 +503,7 @@ class Surrogate:
         return int(load().gl_surrogate_num_params())
 
     @classmethod
-    def train(cls, n_samples=10_000_000, epochs=20, batch=16384, lr=2e-3, lr_min=1e-5,
+    def train(cls, n_samples=10_000_000, epochs=60, batch=16384, lr=2e-3, lr_min=1e-5,
               seed_data=401, seed_init=402, q=(0.5, 1.0), gamma=(1.7, 2.3), r=(0.05, 5.0)):
         lib = load()
         d = gl_surrogate_train_desc(n_samples, epochs, batch, lr, lr_min, seed_data, seed_init,
@@ -565,6 +566,16 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+def series_F(x, stream=None):
+    """The exact F of the EPL series in FP64 on the device (gl_series_F):
+    x CUDA float32 [N, 4] raw (q, gamma, ., vphi) -> F [N, 2] (Re, Im)."""
+    torch = _torch()
+    x = x.contiguous()
+    F = torch.empty((x.shape[0], 2), device=x.device, dtype=torch.float32)
+    _check(load().gl_series_F(_ptr(x), x.shape[0], _ptr(F), _stream_ptr(stream)))
+    return F
 
 
 def system_from_workload(W, data, sigma) -> System:

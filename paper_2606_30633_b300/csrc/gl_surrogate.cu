@@ -57,29 +57,30 @@ __host__ __device__ inline double u01(uint64_t seed, uint64_t i, int k) {
   return (double)(splitmix64(seed ^ (i * 4 + k) * 0xD1B54A32D192ED03ull) >> 11) * 0x1.0p-53;
 }
 
-// Remainder of the series beyond two terms, sum_{n>=3} c_n z^n, by the
-// coefficient recurrence (FP64, until the terms are below 1e-16).
-__device__ inline void series_remainder(double q, double t, double vphi, double& rr, double& ri) {
+// The series beyond two terms with z^3 taken out, sum_{n>=3} c_n z^{n-3}, by
+// the coefficient recurrence (FP64, until the terms are below 1e-16).
+__device__ inline void series_tail(double q, double t, double vphi, double& rr, double& ri) {
   const double f = (1.0 - q) / (1.0 + q);
   const double zr = -f * cos(2.0 * vphi), zi = -f * sin(2.0 * vphi);
-  double c = 1.0, tr = 1.0, ti = 0.0;  // c_n and z^n
+  double c = 1.0, tr = 1.0, ti = 0.0;  // c_n and z^{n-3}
   rr = 0.0;
   ri = 0.0;
   for (int n = 1; n < 400; ++n) {
     c *= (2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
-    const double nr = tr * zr - ti * zi, ni = tr * zi + ti * zr;
-    tr = nr;
-    ti = ni;
-    if (n >= 3) {
-      rr += c * tr;
-      ri += c * ti;
-      if (fabs(c) * (fabs(tr) + fabs(ti)) < 1e-16) break;
+    if (n < 3) continue;
+    if (n > 3) {
+      const double nr = tr * zr - ti * zi, ni = tr * zi + ti * zr;
+      tr = nr;
+      ti = ni;
     }
+    rr += c * tr;
+    ri += c * ti;
+    if (fabs(c) * (fabs(tr) + fabs(ti)) < 1e-16) break;
   }
 }
 
 // Training tuples (q, gamma, log r/theta_E, vphi) and targets OUT_SCALE x the
-// series remainder, q ~ U(q_lo, q_hi), gamma ~ U, r/theta_E ~ logU(r_lo, r_hi),
+// series tail, q ~ U(q_lo, q_hi), gamma ~ U, r/theta_E ~ logU(r_lo, r_hi),
 // vphi ~ U(0, 2 pi).
 __global__ void k_gen_data(float4* __restrict__ X, float2* __restrict__ Y, long long n,
                            uint64_t seed, float q_lo, float q_hi, float g_lo, float g_hi,
@@ -91,7 +92,7 @@ __global__ void k_gen_data(float4* __restrict__ X, float2* __restrict__ Y, long 
     const double lr = lr_lo + (lr_hi - lr_lo) * u01(seed, i, 2);
     const double vp = 2.0 * 3.14159265358979323846 * u01(seed, i, 3);
     double rr, ri;
-    series_remainder(q, g - 1.0, vp, rr, ri);
+    series_tail(q, g - 1.0, vp, rr, ri);
     X[i] = make_float4((float)q, (float)g, (float)lr, (float)vp);
     Y[i] = make_float2((float)(rr * OUT_SCALE), (float)(ri * OUT_SCALE));
   }
@@ -181,6 +182,32 @@ __global__ void k_sum(const float* __restrict__ x, int n, float* __restrict__ ou
   }
 }
 
+// The exact F = 1 + sum_{n>=1} c_n z^n in FP64 for raw tuples (q, gamma, ., vphi).
+__global__ void k_series_F(const float4* __restrict__ X, int n, float2* __restrict__ F) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 v = X[i];
+  const double q = v.x, t = (double)v.y - 1.0, vp = v.w;
+  // 0.01 <= q keeps f <= 0.981, so the terms (below f^n) fall under 1e-18 within 4000
+  if (!(v.x >= 0.01f && v.x <= 1.f && t > 0.0 && t < 2.0 && isfinite(vp))) {
+    F[i] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+    return;
+  }
+  const double f = (1.0 - q) / (1.0 + q);
+  const double zr = -f * cos(2.0 * vp), zi = -f * sin(2.0 * vp);
+  double c = 1.0, pr = 1.0, pi = 0.0, Fr = 1.0, Fi = 0.0;  // c_n, z^n
+  for (int k = 1; k < 4000; ++k) {
+    c *= (2.0 * k - 2.0 + t) / (2.0 * k + 2.0 - t);
+    const double nr = pr * zr - pi * zi, ni = pr * zi + pi * zr;
+    pr = nr;
+    pi = ni;
+    Fr += c * pr;
+    Fi += c * pi;
+    if (fabs(c) * (fabs(pr) + fabs(pi)) < 1e-18) break;
+  }
+  F[i] = make_float2((float)Fr, (float)Fi);
+}
+
 // F (Re, Im) for raw tuples (q, gamma, log r/theta_E, vphi): one 16-row tile
 // per warp.
 __global__ void k_infer(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
@@ -202,8 +229,11 @@ __global__ void k_infer(const __nv_bfloat16* __restrict__ wb, const float* __res
       for (int h = 0; h < 2; ++h) {
         const int r = tile * 16 + g + 8 * h;
         if (r >= n) continue;
-        const Base b = base_terms(raw[h].x, raw[h].y - 1.f, raw[h].w);
-        F[r] = make_float2(b.Fr + y[2 * h] / OUT_SCALE, b.Fi + y[2 * h + 1] / OUT_SCALE);
+        const float yh[2] = {y[2 * h], y[2 * h + 1]};
+        const float dz[3][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        const Base b = compose(base_terms(raw[h].x, raw[h].y - 1.f, raw[h].w), raw[h].x,
+                               raw[h].w, yh, dz);
+        F[r] = make_float2(b.Fr, b.Fi);
       }
   }
 }
@@ -568,12 +598,9 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ param
     wait_ld();
     y[0] += params[OFF_B5];
     y[1] += params[OFF_B5 + 1];
-    const Base bt = base_terms(q, gamma - 1.f, vp);
-    const float k = 1.f / OUT_SCALE;
-    node[t][0] = make_float4(bt.Fr + k * y[0], bt.Fi + k * y[1], dv * (bt.Pr + k * dy[0][0]),
-                             dv * (bt.Pi + k * dy[0][1]));
-    node[t][1] = make_float4(bt.Qr + k * dy[1][0], bt.Qi + k * dy[1][1], bt.Tr + k * dy[2][0],
-                             bt.Ti + k * dy[2][1]);
+    const Base bt = compose(base_terms(q, gamma - 1.f, vp), q, vp, y, dy);
+    node[t][0] = make_float4(bt.Fr, bt.Fi, dv * bt.Pr, dv * bt.Pi);
+    node[t][1] = make_float4(bt.Qr, bt.Qi, bt.Tr, bt.Ti);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     write_intervals(node, table + (size_t)b * TABLE_ROW);
@@ -1015,6 +1042,15 @@ gl_status gl_surrogate_infer(const gl_surrogate* s, const float* x, int N, float
   k_infer<<<(tiles + 7) / 8, 256, 0, (cudaStream_t)stream>>>(
       s->wb, s->params, reinterpret_cast<const float4*>(x), N, reinterpret_cast<float2*>(y));
   SUR_CUDA(cudaGetLastError(), "surrogate inference launch");
+  return GL_OK;
+}
+
+gl_status gl_series_F(const float* x, int N, float* F, void* stream) {
+  if (N < 0 || (N > 0 && (!x || !F))) return fail(GL_EINVAL, "bad x, F or N");
+  if (N == 0) return GL_OK;
+  k_series_F<<<(N + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+      reinterpret_cast<const float4*>(x), N, reinterpret_cast<float2*>(F));
+  SUR_CUDA(cudaGetLastError(), "series launch");
   return GL_OK;
 }
 

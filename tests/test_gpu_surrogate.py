@@ -33,8 +33,8 @@ def gl():
 @pytest.fixture(scope="module")
 def trained(gl):
     torch, g = gl
-    # the benchmark's training run: 1e7 exact-series tuples, 20 epochs
-    return g.Surrogate.train(n_samples=10_000_000, epochs=20, batch=16384, lr=2e-3, lr_min=1e-5,
+    # the benchmark's training run: 1e7 exact-series tuples, 60 epochs
+    return g.Surrogate.train(n_samples=10_000_000, epochs=60, batch=16384, lr=2e-3, lr_min=1e-5,
                              seed_data=401, seed_init=402)
 
 
@@ -83,10 +83,28 @@ def test_trained_network_against_the_exact_series(gl, trained):
     b = thE * np.sqrt(q)
     dal = 2 * b / (1 + q) * (b / R) ** (t - 1) * d
     base = np.abs(mlp.base_F(Xd) - Fe)
-    assert np.sqrt(np.mean(d ** 2)) < 2e-4, np.sqrt(np.mean(d ** 2))
-    assert np.sqrt(np.mean(dal ** 2)) < 3e-4 and dal.max() < 1e-2
-    assert np.sqrt(np.mean(d ** 2)) < 0.1 * np.sqrt(np.mean(base ** 2))  # the network's gain
-    assert trained.final_loss < 1e-3
+    assert np.sqrt(np.mean(d ** 2)) < 3e-5, np.sqrt(np.mean(d ** 2))
+    assert np.sqrt(np.mean(dal ** 2)) < 6e-5 and dal.max() < 3e-3, (np.sqrt(np.mean(dal ** 2)),
+                                                                    dal.max())
+    assert np.sqrt(np.mean(d ** 2)) < 0.01 * np.sqrt(np.mean(base ** 2))  # the network's gain
+    assert trained.final_loss < 1e-4
+    # the library's own exact series (the surrogate's judge) on the same tuples
+    Fx = g.series_F(torch.tensor(X, device="cuda")).cpu().numpy()
+    np.testing.assert_allclose(Fx[:, 0] + 1j * Fx[:, 1], Fe, rtol=0, atol=3e-7)
+
+
+def test_series_F_edges(gl):
+    """gl_series_F: q = 1 gives F = 1 exactly; tuples outside the series'
+    domain give NaN; an empty call is a no-op."""
+    torch, g = gl
+    X = np.array([[1.0, 2.1, 0.0, 0.4], [0.005, 2.0, 0.0, 0.1], [0.7, 3.0, 0.0, 0.2],
+                  [0.7, 2.0, 0.0, np.nan], [0.01, 2.99, 0.0, 1.3]], dtype=np.float32)
+    F = g.series_F(torch.tensor(X, device="cuda")).cpu().numpy()
+    np.testing.assert_array_equal(F[0], [1.0, 0.0])
+    assert np.all(np.isnan(F[1:4]))
+    Fe = oracle.hyp2f1_series(X[4, 1] - 1.0, (1 - X[4, 0]) / (1 + X[4, 0]), X[4, 3])
+    assert abs(F[4, 0] + 1j * F[4, 1] - Fe) <= 1e-6 * abs(Fe)
+    assert g.series_F(torch.zeros((0, 4), device="cuda")).shape == (0, 2)
 
 
 @pytest.fixture(scope="module")
