@@ -41,13 +41,19 @@ MUFU_PER_SM_CLK = 16
 
 
 # ------------------------------------------------------------ op counts ----
-def series_terms(f: float) -> int:
-    """EPL series length the kernels use for |e| = f (before rounding up to
-    a multiple of 4): smallest N >= 1 with f^N <= 2^-24 (1-f)^2 / 2."""
+def series_terms(f: float, t: float) -> int:
+    """EPL series length the kernels use for |e| = f and slope t = gamma - 1
+    (before rounding up to a multiple of 2): the smallest N >= 1 whose next
+    coefficient |e_{N+1}| = prod_{k<=N+1} |rho_k| (rho_1 = r_1, rho_k = f r_k,
+    r_k = (2k-2+t)/(2k+2-t)) is at most 2^-24 (1-f)^2 / 2."""
     tol = 2.0 ** -24 * (1 - f) ** 2 * 0.5
-    n, fn = 1, f
-    while fn > tol and n < 128:
-        fn *= f
+    e = t / (4.0 - t)
+    n = 1
+    while n < 128:
+        k = n + 1
+        e *= f * (2 * k - 2 + t) / (2 * k + 2 - t)
+        if e <= tol:
+            break
         n += 1
     return n
 
@@ -69,7 +75,7 @@ def algorithmic_ops(theta: np.ndarray, ny: int, nx: int, s: int, k: int, n_light
     npix = ny * nx
     ncomp = n_light + n_src
     f = np.hypot(theta[:, 2], theta[:, 3])
-    N = np.array([series_terms(float(v)) for v in f])
+    N = np.array([series_terms(float(v), float(g) - 1.0) for v, g in zip(f, theta[:, 1])])
     fwd = 34 + 2 * N + 8 + 15 * ncomp + 2
     adj = 38 + 4 * N + 8 + 31 * ncomp + 6 * n_src + 85 + 2
     ops = nsub * (fwd + adj) + npix * (2 * k * k + 8)

@@ -102,9 +102,9 @@ struct SampleC {
   EplP epl;
   float2 omg1, opg1, ng2;    // 1 - g1, 1 + g1, -g2 (external shear)
   LightP light[MAX_COMP];    // lens lights, then sources
-  float2 cE[N_MAX];          // E-series coefficients c_n (-f)^{n-1}, n = 1..4 nq (index n-1), paired
+  float2 cE[N_MAX];          // E-series coefficients c_n (-f)^{n-1}, n = 1..2 n2 (index n-1), paired
   float2 cT[N_MAX];          // t-derivative coefficients c_n h_n (-f)^{n-1}, paired
-  int nq;                    // number of 4-term chunks (N rounded up to a multiple of 4)
+  int n2;                    // number of 2-term chunks (N rounded up to a multiple of 2)
   int status;                // 0 ok, 1 outside domain/support (-inf), 2 NaN
   int use_table;             // surrogate table covers this row
   double logprior;
@@ -259,20 +259,17 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
   }
   t_epl = __shfl_sync(0xffffffffu, t_epl, 0);
   f_epl = __shfl_sync(0xffffffffu, f_epl, 0);
-  // series length: smallest N >= 1 with f^N <= 2^-24 (1-f)^2 / 2
-  int N = 1;
-  {
-    const float tol = (float)SERIES_EPS * (1.f - f_epl) * (1.f - f_epl) * 0.5f;
-    float fn = f_epl;
-    while (fn > tol && N < N_MAX) { fn *= f_epl; ++N; }
-  }
-  const int nq = (N + 3) >> 2;
-  // coefficients: e_n = c_n (-f)^{n-1} = prod_{k<=n} rho_k, rho_1 = r_1,
-  // rho_k = -f r_k, r_k = (2k-2+t)/(2k+2-t); t_n = e_n h_n, h_n = sum_k
-  // 1/(2k-2+t) + 1/(2k+2-t): inclusive warp scans of products and sums.
-
+  // Coefficients e_n = c_n (-f)^{n-1} = prod_{k<=n} rho_k, rho_1 = r_1,
+  // rho_k = -f r_k, r_k = (2k-2+t)/(2k+2-t); t_n = e_n h_n, h_n = sum_{k<=n}
+  // 1/(2k-2+t) + 1/(2k+2-t): inclusive warp scans of products and sums, 32
+  // terms per pass. |e_n| decreases (|rho_k| < f for k >= 2), so the tail
+  // after N terms is at most |e_{N+1}| / (1 - f); the series stops at the
+  // first N with |e_{N+1}| <= 2^-24 (1-f)^2 / 2, and 2 ceil(N/2) coefficients
+  // are staged (zeros past N), the summation loops taking two per step.
+  const float tol = (float)SERIES_EPS * (1.f - f_epl) * (1.f - f_epl) * 0.5f;
   float carry_e = 1.f, carry_h = 0.f;
-  for (int base = 0; base < 4 * nq; base += 32) {
+  int N = N_MAX;
+  for (int base = 0; base < N_MAX; base += 32) {
     const int n = base + lane + 1;
     const float a = 2.f * n - 2.f + t_epl, bb = 2.f * n + 2.f - t_epl;
     float rho = (n == 1 ? 1.f : -f_epl) * (a / bb);
@@ -284,15 +281,17 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
       if (lane >= o) { rho *= r2; hin += h2; }
     }
     const float en = carry_e * rho, hn = carry_h + hin;
-    if (n <= 4 * nq) {
-      sc.cE[n - 1] = f2(n <= N ? en : 0.f);
-      sc.cT[n - 1] = f2(n <= N ? en * hn : 0.f);
-    }
+    const unsigned cut = __ballot_sync(0xffffffffu, n >= 2 && fabsf(en) <= tol);
+    if (cut) N = base + __ffs(cut) - 1;  // the first n past the cut is N + 1
+    sc.cE[n - 1] = f2(n <= N ? en : 0.f);
+    sc.cT[n - 1] = f2(n <= N ? en * hn : 0.f);
+    if (cut) break;
     carry_e = __shfl_sync(0xffffffffu, en, 31);
     carry_h = __shfl_sync(0xffffffffu, hn, 31);
   }
+  const int n2 = (N + 1) >> 1;
   if (lane == 0) {
-    sc.nq = nq;
+    sc.n2 = n2;
     sc.logprior = lp;
     sc.status = 0;
   }

@@ -5,7 +5,7 @@
 // and the table gathers stay per lane.
 //
 // Notation as in gl_model.cuh. The EPL deflection comes from the exact
-// series (Horner in w over the staged coefficients) or, for rows that the
+// series (Clenshaw's recurrence in w over the staged coefficients) or, for rows that the
 // surrogate covers, from the row's table (F and its derivatives).
 #pragma once
 
@@ -63,12 +63,12 @@ __device__ __forceinline__ float2 clen_step(float2 tw, float2 b1, float2 b2, flo
   return fma2(tw, b1, fma2(f2(-1.f), b2, a));
 }
 
-// The sum over the staged coefficients c[0 .. 4 nq) at two points.
-__device__ __forceinline__ Clen2 clenshaw(const float2* __restrict__ c, int nq, const Geo2& g) {
+// The sum over the staged coefficients c[0 .. 2 n2) at two points.
+__device__ __forceinline__ Clen2 clenshaw(const float2* __restrict__ c, int n2, const Geo2& g) {
   const float4* c4 = reinterpret_cast<const float4*>(c);
   const float2 tw = add2(g.wr, g.wr);
   float2 b1 = f2(0.f), b2 = f2(0.f);
-  for (int k = 2 * nq - 1; k >= 0; --k) {
+  for (int k = n2 - 1; k >= 0; --k) {
     const float4 a = c4[k];  // a_{2k+1} in (z, w), a_{2k} in (x, y)
     const float2 bh = clen_step(tw, b1, b2, make_float2(a.z, a.w));
     const float2 bl = clen_step(tw, bh, b1, make_float2(a.x, a.y));
@@ -79,12 +79,12 @@ __device__ __forceinline__ Clen2 clenshaw(const float2* __restrict__ c, int nq, 
 }
 
 // The same at four points (two pairs interleaved for instruction-level parallelism).
-__device__ __forceinline__ void clenshaw2(const float2* __restrict__ c, int nq, const Geo2& g0,
+__device__ __forceinline__ void clenshaw2(const float2* __restrict__ c, int n2, const Geo2& g0,
                                           const Geo2& g1, Clen2& s0, Clen2& s1) {
   const float4* c4 = reinterpret_cast<const float4*>(c);
   const float2 tw0 = add2(g0.wr, g0.wr), tw1 = add2(g1.wr, g1.wr);
   float2 p1 = f2(0.f), p2 = f2(0.f), q1 = f2(0.f), q2 = f2(0.f);
-  for (int k = 2 * nq - 1; k >= 0; --k) {
+  for (int k = n2 - 1; k >= 0; --k) {
     const float4 a = c4[k];
     const float2 ah = make_float2(a.z, a.w), al = make_float2(a.x, a.y);
     const float2 ph = clen_step(tw0, p1, p2, ah);
@@ -100,13 +100,13 @@ __device__ __forceinline__ void clenshaw2(const float2* __restrict__ c, int nq, 
 
 // E and the t-derivative sum T together.
 __device__ __forceinline__ void clenshaw_ET(const float2* __restrict__ cE,
-                                            const float2* __restrict__ cT, int nq, const Geo2& g,
+                                            const float2* __restrict__ cT, int n2, const Geo2& g,
                                             Clen2& sE, Clen2& sT) {
   const float4* c4 = reinterpret_cast<const float4*>(cE);
   const float4* d4 = reinterpret_cast<const float4*>(cT);
   const float2 tw = add2(g.wr, g.wr);
   float2 e1 = f2(0.f), e2 = f2(0.f), t1 = f2(0.f), t2 = f2(0.f);
-  for (int k = 2 * nq - 1; k >= 0; --k) {
+  for (int k = n2 - 1; k >= 0; --k) {
     const float4 a = c4[k];
     const float4 d = d4[k];
     const float2 eh = clen_step(tw, e1, e2, make_float2(a.z, a.w));
@@ -231,7 +231,7 @@ __device__ __forceinline__ void deflection_F(const SampleC& sc, const float4* ta
     Fr = make_float2(t0.Fr, t1.Fr);
     Fi = make_float2(t0.Fi, t1.Fi);
   } else {
-    series_F(sc.epl, g, clenshaw(sc.cE, sc.nq, g), Fr, Fi);
+    series_F(sc.epl, g, clenshaw(sc.cE, sc.n2, g), Fr, Fi);
   }
 }
 
@@ -259,7 +259,7 @@ __device__ __forceinline__ void surface_brightness4(const SampleC& sc, const flo
     deflection_F<true>(sc, tab, g1, Fr1, Fi1);
   } else {
     Clen2 s0, s1;
-    clenshaw2(sc.cE, sc.nq, g0, g1, s0, s1);
+    clenshaw2(sc.cE, sc.n2, g0, g1, s0, s1);
     series_F(sc.epl, g0, s0, Fr0, Fi0);
     series_F(sc.epl, g1, s1, Fr1, Fi1);
   }
@@ -338,7 +338,7 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
     Fi = make_float2(t0.Fi, t1.Fi);
   } else {
     Clen2 sE, sT;
-    clenshaw_ET(sc.cE, sc.cT, sc.nq, g, sE, sT);
+    clenshaw_ET(sc.cE, sc.cT, sc.n2, g, sE, sT);
     const float2 nwr = neg2(g.wr);
     Er = fma2(nwr, sE.b1, sE.b0);
     Ei = mul2(g.wi, sE.b1);
