@@ -83,6 +83,20 @@ def algorithmic_ops(theta: np.ndarray, ny: int, nx: int, s: int, k: int, n_light
     return float(ops.sum()), float(mufu * theta.shape[0])
 
 
+def unit_rate_roofline(gl, mufu_ops: float, step_s: float, clocks: dict) -> tuple:
+    """The pipe rates measured on this GPU (gl_unit_rates, operations per SM
+    per SM clock) and the MUFU side of the roofline: MUFU operations per step
+    over the step time against n_SM x r_MUFU x the sampled SM clock."""
+    r = gl.unit_rates()
+    rates = {k: round(v, 2) for k, v in r.items()}
+    rates["unit"] = "ops per SM per SM clock"
+    mhz = clocks.get("sm_mhz") or 2032.0
+    peak = SM_COUNT_B300 * r["mufu"] * mhz * 1e6 / 1e12
+    achieved = mufu_ops / step_s / 1e12
+    return rates, {"achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                   "clock_mhz": mhz}
+
+
 # ------------------------------------------------------------- clocks ----
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -367,6 +381,7 @@ def run_ours(args) -> dict | None:
     peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2.032e9 / 1e12
     achieved = ops / mean_s / 1e12
     clocks = clk.summary()
+    rates, mufu_roof = unit_rate_roofline(gl, mufu, mean_s, clocks)
     out = None
     if rank == 0:
         out = {
@@ -385,7 +400,9 @@ def run_ours(args) -> dict | None:
                          "note": "FP32 lane-operations (FMA = 1) of the formulation's op "
                                  "count per evaluation / mean step time; peak = 148 SM x 128 "
                                  "lanes x 2032 MHz",
-                         "mufu_ops_per_step": mufu},
+                         "mufu_ops_per_step": mufu,
+                         "measured_unit_rates": rates,
+                         "mufu": mufu_roof},
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": B * W.P * 4,
                     "d2h_bytes_per_step": B * (W.P + 1) * 4},
             "gpu_launches": args.steps,

@@ -456,6 +456,14 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
 gl_status gl_logp_grad_backward(gl_system* sys, const float* theta, int B, float* logp,
                                 float* grad, float* intensity, gl_deflection defl, void* stream);
 
+/* Throughput of the pipes that bound the lens kernels, measured on the
+ * current device in operations per SM per SM clock (the roofline's r_FP32
+ * and r_MUFU): fp32 with scalar FMAs, fp32x2 with paired (two-lane) FMAs, an
+ * FMA counting one operation per lane; mufu with ex2 / lg2 approximations.
+ * One CTA per SM, independent dependency chains, clock64 timing; runs about
+ * 10 ms on the device, synchronously. GL_EINVAL for NULL outputs. */
+gl_status gl_unit_rates(double* fp32, double* fp32x2, double* mufu);
+
 /* Last failure message on this host thread ("" if none). */
 const char* gl_last_error(void);
 

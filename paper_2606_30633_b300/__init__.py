@@ -75,6 +75,7 @@ SIGNATURES = {
     "gl_surrogate_params": (ctypes.c_int, [_VP, _VP]),
     "gl_surrogate_infer": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP]),
     "gl_series_F": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    "gl_unit_rates": (ctypes.c_int, [_VP, _VP, _VP]),
     "gl_surrogate_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "gl_surrogate_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "gl_surrogate_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_VP)]),
@@ -576,6 +577,14 @@ def series_F(x, stream=None):
     F = torch.empty((x.shape[0], 2), device=x.device, dtype=torch.float32)
     _check(load().gl_series_F(_ptr(x), x.shape[0], _ptr(F), _stream_ptr(stream)))
     return F
+
+
+def unit_rates() -> dict:
+    """Measured pipe throughput of the current device in operations per SM per
+    SM clock (gl_unit_rates): {"fp32", "fp32x2", "mufu"}."""
+    v = [ctypes.c_double() for _ in range(3)]
+    _check(load().gl_unit_rates(*[ctypes.addressof(x) for x in v]))
+    return {"fp32": v[0].value, "fp32x2": v[1].value, "mufu": v[2].value}
 
 
 def system_from_workload(W, data, sigma) -> System:
