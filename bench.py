@@ -246,7 +246,7 @@ def learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world) -
     d_near = (S.logp(tn, defl=gl.GL_DEFL_SURROGATE) - S.logp(tn)).abs().cpu().numpy()
     d_prior = (S.logp(theta, defl=gl.GL_DEFL_SURROGATE) - S.logp(theta)).abs().cpu().numpy()
     e = np.hypot(theta_np[:, 2], theta_np[:, 3])
-    in_dom = float(np.mean((1 - e) / (1 + e) >= 0.5))
+    in_dom = float(np.mean(((1 - e) / (1 + e) >= 0.5) & (e >= 0.01)))
     # deflection error against the library's FP64 series on 2e5 held-out tuples
     # of the training distribution, in arcsec at theta_E = 1.25"
     r = np.random.default_rng(403)

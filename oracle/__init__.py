@@ -201,6 +201,10 @@ class System:
         return out
 
     def logp_grad(self, theta, nthreads: int = 0):
+        """log p and its gradient by forward-mode dual numbers. Undefined (NaN)
+        where a component's ellipticity is exactly e = 0: |e| = sqrt(e1^2 + e2^2)
+        has no derivative there although log p is smooth in (e1, e2); the tests
+        use central differences of logp() at such points."""
         th = self._theta(theta)
         lp = np.empty(th.shape[0])
         g = np.empty_like(th)

@@ -16,6 +16,7 @@ constexpr int MAX_SRC = 3;     // source components
 constexpr int MAX_COMP = MAX_LIGHT + MAX_SRC;
 constexpr int MAX_P = 8 + 7 * MAX_COMP;
 constexpr int N_MAX = 128;     // EPL series terms for |e| < 0.8 at FP32 tolerance
+constexpr float TABLE_MIN_E = 1e-2f;  // rows with a smaller |e| use the series, not tables
 constexpr int THREADS = 256;   // threads per CTA of the fused kernels
 constexpr int NWARPS = THREADS / 32;
 constexpr int ROWS_STRIP = 8;  // output rows per thread in the unrolled convolution

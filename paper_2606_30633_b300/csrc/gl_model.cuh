@@ -237,8 +237,10 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
       sc.omg1 = f2(1.f - th[6]);
       sc.opg1 = f2(1.f + th[6]);
       sc.ng2 = f2(-th[7]);
+      // the table path's rotation term divides d log p / d phi by 2 |e|^2, so
+      // nearly round lenses (|e| < TABLE_MIN_E) take the series
       sc.use_table = sp.table != nullptr && q >= sp.sq_lo && q <= sp.sq_hi &&
-                     th[1] >= sp.sg_lo && th[1] <= sp.sg_hi;
+                     th[1] >= sp.sg_lo && th[1] <= sp.sg_hi && c >= TABLE_MIN_E;
     } else {
       LightP& L = sc.light[lane - 1];
       const float* p = th + 8 + 7 * (lane - 1);
@@ -308,8 +310,10 @@ __device__ inline void sersic_finish(const FinishC& F, const double* a, float* g
   const float dq = 0.5f * m * A3;
   const float rot = 2.f * m * A4 / (1.f - F.c * F.c);
   const float Sx = m * F.q * A5, Sy = m * A6 / F.q;  // sum u dS/dx', sum u dS/dy'
-  const float cc = fmaxf(F.c, 1e-30f);
-  const float c2p = F.e1 / cc, s2p = F.e2 / cc;  // cos 2phi, sin 2phi (0 for a round profile)
+  // cos 2phi, sin 2phi of the staged angle phi = atan2(e2, e1)/2: e/|e| for e != 0, and
+  // (1, 0) at e = 0, where the gradient is the limit along e1 -> 0+ (the model is
+  // smooth in (e1, e2) there)
+  const float c2p = F.cs * F.cs - F.sn * F.sn, s2p = 2.f * F.cs * F.sn;
   const float dqdc = -2.f / ((1.f + F.c) * (1.f + F.c));
   g[0] = F.bn / (F.n * F.p0) * A1;
   g[1] = -1.9992f * (A1 - A0) + F.bn * 0.69314718f / F.n * A2;
@@ -331,7 +335,7 @@ __device__ inline void epl_finish(const FinishC& F, const double* a, float* g,
                                   bool rot_is_dphi = false) {
   const float gxl = -(float)a[4], gyl = -(float)a[5];
   const float cc = fmaxf(F.c, 1e-30f);
-  const float c2p = F.e1 / cc, s2p = F.e2 / cc;
+  const float c2p = F.cs * F.cs - F.sn * F.sn, s2p = 2.f * F.cs * F.sn;  // as in sersic_finish
   const float dqdc = -2.f / ((1.f + F.c) * (1.f + F.c));
   const float dq = (float)a[2], rot = (float)a[3];
   g[0] = F.t / F.p0 * (float)a[0];
