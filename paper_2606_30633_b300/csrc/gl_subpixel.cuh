@@ -203,9 +203,9 @@ __device__ __forceinline__ void lens_equation2(const SampleC& sc, const Geo2& g,
 
 __device__ __forceinline__ float2 sersic_fwd2(const LightP& c, float2 X, float2 Y) {
   const float2 dx = add2(X, c.nxc), dy = add2(Y, c.nyc);
-  const float2 xp = fma2(c.cs, dx, mul2(c.sn, dy));
-  const float2 yp = fma2(c.cs, dy, mul2(c.nsn, dx));
-  const float2 R2 = max2(fma2(mul2(c.q, xp), xp, mul2(mul2(c.iq, yp), yp)), R_MIN2);
+  const float2 u = fma2(c.ucs, dx, mul2(c.usn, dy));
+  const float2 v = fma2(c.vcs, dy, mul2(c.vnsn, dx));
+  const float2 R2 = max2(fma2(u, u, mul2(v, v)), R_MIN2);
   const float2 p = ex2_2(fma2(c.c1, lg2_2(R2), c.c0));
   return mul2(c.Ip, ex2_2(mul2(c.nbl, p)));
 }
@@ -286,17 +286,18 @@ template <> __device__ __forceinline__ float2 acc_zero<float2>() { return f2(0.f
 template <> __device__ __forceinline__ float acc_zero<float>() { return 0.f; }
 
 // Native accumulators of a Sersic component (converted to parameter
-// gradients once per sample): [0] sum uS, [1] sum uSp, [2] sum uSp log2 p,
-// [3] sum uSp/R^2 (x'^2 - y'^2/q^2), [4] sum uSp/R^2 x'y',
-// [5] sum uSp/R^2 x', [6] sum uSp/R^2 y' (one sum per lane).
+// gradients once per sample), in the scaled frame us = sqrt(q) x',
+// vs = y'/sqrt(q): [0] sum uS, [1] sum uSp, [2] sum uSp log2 p,
+// [3] sum uSp/R^2 (us^2 - vs^2), [4] sum uSp/R^2 us vs,
+// [5] sum uSp/R^2 us, [6] sum uSp/R^2 vs (one sum per lane).
 // If grad_pos, adds dS/dX, dS/dY (without u) to gX, gY.
 template <bool grad_pos, class AccT>
 __device__ __forceinline__ void sersic_adj2(const LightP& c, float2 X, float2 Y, float2 u,
                                             AccT* __restrict__ a, float2& gX, float2& gY) {
   const float2 dx = add2(X, c.nxc), dy = add2(Y, c.nyc);
-  const float2 xp = fma2(c.cs, dx, mul2(c.sn, dy));
-  const float2 yp = fma2(c.cs, dy, mul2(c.nsn, dx));
-  const float2 R2raw = fma2(mul2(c.q, xp), xp, mul2(mul2(c.iq, yp), yp));
+  const float2 us = fma2(c.ucs, dx, mul2(c.usn, dy));   // sqrt(q) x'
+  const float2 vs = fma2(c.vcs, dy, mul2(c.vnsn, dx));  // y' / sqrt(q)
+  const float2 R2raw = fma2(us, us, mul2(vs, vs));
   const float2 R2 = max2(R2raw, R_MIN2);
   const float2 l2p = fma2(c.c1, lg2_2(R2), c.c0);
   const float2 p = ex2_2(l2p);
@@ -310,13 +311,13 @@ __device__ __forceinline__ void sersic_adj2(const LightP& c, float2 X, float2 Y,
   acc_fma(a[0], u, S);
   acc_add(a[1], uSp);
   acc_fma(a[2], uSp, l2p);
-  acc_fma(a[3], kD, fma2(xp, xp, mul2(mul2(c.niq2, yp), yp)));
-  acc_fma(a[4], mul2(kD, xp), yp);
-  acc_fma(a[5], kD, xp);
-  acc_fma(a[6], kD, yp);
+  acc_fma(a[3], kD, fma2(us, us, mul2(neg2(vs), vs)));
+  acc_fma(a[4], mul2(kD, us), vs);
+  acc_fma(a[5], kD, us);
+  acc_fma(a[6], kD, vs);
   if (grad_pos) {
-    gX = fma2(Dh, fma2(c.kX1, xp, mul2(c.kX2, yp)), gX);
-    gY = fma2(Dh, fma2(c.kY1, xp, mul2(c.kY2, yp)), gY);
+    gX = fma2(Dh, fma2(c.kX1, us, mul2(c.kX2, vs)), gX);
+    gY = fma2(Dh, fma2(c.kY1, us, mul2(c.kY2, vs)), gY);
   }
 }
 
