@@ -274,7 +274,8 @@ gl_status gl_surrogate_create(const float* params_host, gl_surrogate** out);
 gl_status gl_surrogate_params(const gl_surrogate* sur, float* params_host);
 
 /* F (Re, Im) for N raw inputs x: device [N][4] = (q, gamma, log(R/theta_E),
- * vphi) -> y: device [N][2]. */
+ * vphi) -> y: device [N][2]. x is read as float4 and must be 16-byte aligned,
+ * y 8-byte aligned (else GL_EINVAL). */
 gl_status gl_surrogate_infer(const gl_surrogate* sur, const float* x, int N, float* y,
                              void* stream);
 
@@ -283,13 +284,14 @@ gl_status gl_surrogate_infer(const gl_surrogate* sur, const float* x, int N, flo
  * the terms fall below 1e-18, for N raw inputs x: device [N][4] = (q, gamma,
  * ignored, vphi) -> F: device [N][2] (Re, Im, rounded to FP32); the judge of
  * the surrogate's deflection error. Tuples outside 0.01 <= q <= 1,
- * 1 < gamma < 3 (or not finite) give NaN. Asynchronous on stream; GL_EINVAL for N < 0 or
- * NULL pointers with N > 0. */
+ * 1 < gamma < 3 (or not finite) give NaN. Asynchronous on stream; GL_EINVAL for N < 0, NULL
+ * pointers with N > 0, or x not 16-byte / F not 8-byte aligned. */
 gl_status gl_series_F(const float* x, int N, float* F, void* stream);
 
 /* Mean squared training loss and its gradient w.r.t. the parameters for N
- * rows (N a multiple of 128): x device [N][4] raw inputs, target device
- * [N][2] in the network's output units (y above); loss_host and
+ * rows (N a multiple of 128): x device [N][4] raw inputs (16-byte aligned),
+ * target device [N][2] (8-byte aligned) in the network's output units (y
+ * above); loss_host and
  * grad_host [gl_surrogate_num_params()] receive the results. Synchronous. */
 gl_status gl_surrogate_loss_grad(const gl_surrogate* sur, const float* x, const float* target,
                                  int N, float* loss_host, float* grad_host);

@@ -23,6 +23,8 @@
 //   * dF/dt = z sum_{n>=1} c_n h_n z^{n-1},  h_n = sum_{k<=n} 1/(2k-2+t) + 1/(2k+2-t).
 #pragma once
 
+#include <cstddef>
+
 #include "gl_internal.cuh"
 
 namespace gl {
@@ -80,7 +82,8 @@ __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp(a.x), 
 struct EplP {
   float2 nxc, nyc;            // minus the centre
   float2 cs, sn, ncs, nsn;    // position angle
-  float2 q, nq, q2;
+  float2 qcs, qsn;            // q (cos, sin): q x' = qcs dx + qsn dy
+  float2 iq, nq;              // 1/q, -q
   float2 f, nf, m2f;          // f = |e|, -f, -2f
   float2 ht, CA;              // (1 - t)/2, 2 b^t / (1 + q)
   float2 t, omt, ntmt;        // t, 1 - t, -(2 - t)
@@ -108,14 +111,19 @@ struct SampleC {
   EplP epl;
   float2 omg1, opg1, ng2;    // 1 - g1, 1 + g1, -g2 (external shear)
   LightP light[MAX_COMP];    // lens lights, then sources
-  float2 cE[N_MAX];          // E-series coefficients c_n (-f)^{n-1}, n = 1..2 n2 (index n-1), paired
-  float2 cT[N_MAX];          // t-derivative coefficients c_n h_n (-f)^{n-1}, paired
+  // the summation loops read two coefficients at a time as float4: 16-byte aligned
+  alignas(16) float2 cE[N_MAX];  // E-series coefficients c_n (-f)^{n-1}, n = 1..2 n2 (index n-1), paired
+  alignas(16) float2 cT[N_MAX];  // t-derivative coefficients c_n h_n (-f)^{n-1}, paired
   int n2;                    // number of 2-term chunks (N rounded up to a multiple of 2)
   int status;                // 0 ok, 1 outside domain/support (-inf), 2 NaN
   int use_table;             // surrogate table covers this row
   double logprior;
   float dprior[MAX_P];
 };
+
+static_assert(offsetof(SampleC, cE) % 16 == 0 && offsetof(SampleC, cT) % 16 == 0,
+              "series coefficients must be 16-byte aligned (read as float4)");
+static_assert(alignof(SampleC) >= 16, "SampleC must keep its 16-byte members aligned");
 
 __device__ __forceinline__ int ellip_index(int c) { return c == 0 ? 2 : 8 + 7 * (c - 1) + 2; }
 
@@ -227,7 +235,7 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
       const float b = th[0] * sqrtf(q);
       E.nxc = f2(-th[4]); E.nyc = f2(-th[5]);
       E.cs = f2(cs); E.sn = f2(sn); E.ncs = f2(-cs); E.nsn = f2(-sn);
-      E.q = f2(q); E.nq = f2(-q); E.q2 = f2(q * q);
+      E.qcs = f2(q * cs); E.qsn = f2(q * sn); E.iq = f2(1.f / q); E.nq = f2(-q);
       E.f = f2(c); E.nf = f2(-c); E.m2f = f2(-2.f * c);
       E.ht = f2(0.5f * (1.f - t));
       E.CA = f2(2.f * powf(b, t) / (1.f + q));

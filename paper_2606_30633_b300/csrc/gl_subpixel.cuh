@@ -24,18 +24,19 @@ __device__ __forceinline__ const T& reload(const T& v) {
 }
 
 // ------------------------------------------------------ EPL geometry ----
+// qx = q x' and yp = y' in the lens frame (R^2 = q^2 x'^2 + y'^2 = qx^2 + yp^2).
 struct Geo2 {
-  float2 xp, yp, R2, ir, cph, sph, nsph, wr, wi, nwi;
+  float2 qx, yp, R2, ir, cph, sph, nsph, wr, wi, nwi;
 };
 
 __device__ __forceinline__ Geo2 epl_geometry2(const EplP& e, float2 x, float2 y) {
   Geo2 g;
   const float2 dx = add2(x, e.nxc), dy = add2(y, e.nyc);
-  g.xp = fma2(e.cs, dx, mul2(e.sn, dy));
+  g.qx = fma2(e.qcs, dx, mul2(e.qsn, dy));
   g.yp = fma2(e.cs, dy, mul2(e.nsn, dx));
-  g.R2 = max2(fma2(mul2(e.q2, g.xp), g.xp, mul2(g.yp, g.yp)), R_MIN2);
+  g.R2 = max2(fma2(g.qx, g.qx, mul2(g.yp, g.yp)), R_MIN2);
   g.ir = rsq2(g.R2);
-  g.cph = mul2(mul2(e.q, g.xp), g.ir);
+  g.cph = mul2(g.qx, g.ir);
   g.sph = mul2(g.yp, g.ir);
   g.nsph = neg2(g.sph);
   g.wr = fma2(g.cph, g.cph, mul2(g.nsph, g.sph));
@@ -349,11 +350,11 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
     dtFr = mul2(e.f, fma2(nwr, sT.b0, sT.b1));
     dtFi = mul2(e.nf, mul2(g.wi, sT.b0));
     zi = mul2(e.nf, g.wi);
-    nzi = mul2(e.f, g.wi);
+    nzi = neg2(zi);
   }
   const float2 Lm = lg2_2(g.R2);
   const float2 A = mul2(e.CA, ex2_2(mul2(e.ht, Lm)));
-  const float2 Qr = mul2(A, g.cph), Qi = mul2(A, g.sph), nQi = mul2(A, g.nsph);  // A e^{i vphi}
+  const float2 Qr = mul2(A, g.cph), Qi = mul2(A, g.sph), nQi = neg2(Qi);  // A e^{i vphi}
   const float2 aLr = fma2(Qr, Fr, mul2(nQi, Fi));
   const float2 aLi = fma2(Qr, Fi, mul2(Qi, Fr));
   const float2 nax = fma2(e.ncs, aLr, mul2(e.sn, aLi));
@@ -369,7 +370,7 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
     sersic_adj2<true>(sc.light[NL + c], bx, by, u, acc + 8 + 7 * (NL + c), gX, gY);
   // adjoint of the deflection: v = d logp / d alpha = -u grad_beta S
   const float2 nu = neg2(u);
-  const float2 vx = mul2(nu, gX), vy = mul2(nu, gY), nvy = mul2(u, gY);
+  const float2 vx = mul2(nu, gX), vy = mul2(nu, gY), nvy = neg2(vy);
   acc_fma(acc[6], nvy, y);
   acc_fma(acc[6], vx, x);
   acc_fma(acc[7], vy, x);
@@ -381,8 +382,9 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
   const float2 s1 = fma2(vLx, aLr, mul2(vLy, aLi));    // v . alpha
   const float2 s1i = fma2(vLy, aLr, mul2(nvLx, aLi));  // v . (i alpha)
   const float2 lnbR = fma2(f2(-0.34657359027997264f), Lm, e.lnb);  // ln b - ln R
-  const float2 dphq = mul2(mul2(g.xp, g.yp), neg2(iR2));           // d vphi / d ln q
-  const float2 aq = fma2(mul2(mul2(e.omtq, g.xp), g.xp), iR2, e.a0);
+  const float2 xp = mul2(g.qx, e.iq);                               // x'
+  const float2 dphq = mul2(mul2(xp, g.yp), neg2(iR2));              // d vphi / d ln q
+  const float2 aq = fma2(mul2(mul2(e.omtq, xp), xp), iR2, e.a0);
   if (TAB) {
     // table derivatives at fixed (the other) arguments: dF/dvphi, dF/dq, dF/dt
     const float2 Pr = make_float2(t0.Pr, t1.Pr), Pi = make_float2(t0.Pi, t1.Pi);
@@ -399,9 +401,9 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
     acc_add(acc[2], sQ);
     acc_fma(acc[2], S13, dphq);
     acc_fma(acc[2], s1, aq);
-    const float2 Dx = mul2(iR2, fma2(mul2(e.omtq2, g.xp), s1, mul2(mul2(e.nq, g.yp), S13)));
-    const float2 Dy = mul2(iR2, fma2(mul2(e.omt, g.yp), s1, mul2(mul2(e.q, g.xp), S13)));
-    acc_add(acc[3], fma2(g.yp, Dx, fma2(neg2(g.xp), Dy, s1i)));  // d alpha/d phi
+    const float2 Dx = mul2(iR2, fma2(mul2(e.omtq2, xp), s1, mul2(mul2(e.nq, g.yp), S13)));
+    const float2 Dy = mul2(iR2, fma2(mul2(e.omt, g.yp), s1, mul2(g.qx, S13)));
+    acc_add(acc[3], fma2(g.yp, Dx, fma2(neg2(xp), Dy, s1i)));  // d alpha/d phi
     acc_add(acc[4], Dx);
     acc_add(acc[5], Dy);
     return;
@@ -428,12 +430,12 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
   // rotation: d alpha'/d phi = i X with X = (2-t) alpha' - 2 kappa z' =
   // -2 kappa f (z' w E + conj(z') F), which is O(f); acc[3] = sum kappa v.(iY)
   const float2 kap = mul2(mul2(e.Kk, A), g.ir);
-  const float2 zwr = fma2(g.xp, g.wr, mul2(g.yp, g.nwi)), zwi = fma2(g.xp, g.wi, mul2(g.yp, g.wr));
-  const float2 Yr = fma2(zwr, Er, fma2(neg2(zwi), Ei, fma2(g.xp, Fr, mul2(g.yp, Fi))));
-  const float2 Yi = fma2(zwr, Ei, fma2(zwi, Er, fma2(g.xp, Fi, mul2(neg2(g.yp), Fr))));
+  const float2 zwr = fma2(xp, g.wr, mul2(g.yp, g.nwi)), zwi = fma2(xp, g.wi, mul2(g.yp, g.wr));
+  const float2 Yr = fma2(zwr, Er, fma2(neg2(zwi), Ei, fma2(xp, Fr, mul2(g.yp, Fi))));
+  const float2 Yi = fma2(zwr, Ei, fma2(zwi, Er, fma2(xp, Fi, mul2(neg2(g.yp), Fr))));
   acc_fma(acc[3], kap, fma2(vLy, Yr, mul2(nvLx, Yi)));
-  acc_fma(acc[4], iR2, fma2(mul2(e.omtq2, g.xp), s1, mul2(mul2(e.nq, g.yp), S13)));
-  acc_fma(acc[5], iR2, fma2(mul2(e.omt, g.yp), s1, mul2(mul2(e.q, g.xp), S13)));
+  acc_fma(acc[4], iR2, fma2(mul2(e.omtq2, xp), s1, mul2(mul2(e.nq, g.yp), S13)));
+  acc_fma(acc[5], iR2, fma2(mul2(e.omt, g.yp), s1, mul2(g.qx, S13)));
 }
 
 }  // namespace gl

@@ -1034,10 +1034,13 @@ void gl_surrogate_destroy(gl_surrogate* s) {
   delete s;
 }
 
+static bool aligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
 gl_status gl_surrogate_infer(const gl_surrogate* s, const float* x, int N, float* y, void* stream) {
   if (!s) return fail(GL_EINVAL, "surrogate is NULL");
   if (N < 0 || (N > 0 && (!x || !y))) return fail(GL_EINVAL, "bad x, y or N");
   if (N == 0) return GL_OK;
+  if (!aligned(x, 16) || !aligned(y, 8)) return fail(GL_EINVAL, "x must be 16-byte, y 8-byte aligned");
   const int tiles = (N + 15) / 16;
   k_infer<<<(tiles + 7) / 8, 256, 0, (cudaStream_t)stream>>>(
       s->wb, s->params, reinterpret_cast<const float4*>(x), N, reinterpret_cast<float2*>(y));
@@ -1048,6 +1051,7 @@ gl_status gl_surrogate_infer(const gl_surrogate* s, const float* x, int N, float
 gl_status gl_series_F(const float* x, int N, float* F, void* stream) {
   if (N < 0 || (N > 0 && (!x || !F))) return fail(GL_EINVAL, "bad x, F or N");
   if (N == 0) return GL_OK;
+  if (!aligned(x, 16) || !aligned(F, 8)) return fail(GL_EINVAL, "x must be 16-byte, F 8-byte aligned");
   k_series_F<<<(N + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
       reinterpret_cast<const float4*>(x), N, reinterpret_cast<float2*>(F));
   SUR_CUDA(cudaGetLastError(), "series launch");
@@ -1058,6 +1062,8 @@ gl_status gl_surrogate_loss_grad(const gl_surrogate* s, const float* x, const fl
                                  float* loss_host, float* grad_host) {
   if (!s || !x || !target || !loss_host || !grad_host) return fail(GL_EINVAL, "NULL argument");
   if (N <= 0 || N % TILE != 0) return fail(GL_EINVAL, "N must be a positive multiple of 128");
+  if (!aligned(x, 16) || !aligned(target, 8))
+    return fail(GL_EINVAL, "x must be 16-byte, target 8-byte aligned");
   const int ntiles = N / TILE;
   TrainBuffers tb;
   SUR_CUDA(cudaMalloc(&tb.gpart, (size_t)ntiles * NPARAM * sizeof(float)), "alloc");
