@@ -332,7 +332,7 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
   const EplP& e = sc.epl;
   const Geo2 g = epl_geometry2(e, x, y);
   const float2 iR2 = mul2(g.ir, g.ir);
-  float2 Fr, Fi, Er, Ei, dtFr, dtFi, zi, nzi;  // dtF = dF/dt
+  float2 Fr, Fi, Er, Ei, dtFr, dtFi;  // dtF = dF/dt
   TabF t0, t1;
   if (TAB) {
     table_eval2<true>(tab, g, t0, t1);
@@ -349,8 +349,6 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
     // dF/dt = z T = -f w T
     dtFr = mul2(e.f, fma2(nwr, sT.b0, sT.b1));
     dtFi = mul2(e.nf, mul2(g.wi, sT.b0));
-    zi = mul2(e.nf, g.wi);
-    nzi = neg2(zi);
   }
   const float2 Lm = lg2_2(g.R2);
   const float2 A = mul2(e.CA, ex2_2(mul2(e.ht, Lm)));
@@ -381,6 +379,10 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
   const float2 nvLx = neg2(vLx);
   const float2 s1 = fma2(vLx, aLr, mul2(vLy, aLi));    // v . alpha
   const float2 s1i = fma2(vLy, aLr, mul2(nvLx, aLi));  // v . (i alpha)
+  // G = conj(vL) A e^{i vphi}: for any lens-frame factor X of the deflection,
+  // v . (A e^{i vphi} X) = Re(G X) and v . (i A e^{i vphi} X) = -Im(G X)
+  const float2 Gr = fma2(vLx, Qr, mul2(vLy, Qi)), Gi = fma2(vLx, Qi, mul2(neg2(vLy), Qr));
+  const float2 nGi = neg2(Gi);
   const float2 lnbR = fma2(f2(-0.34657359027997264f), Lm, e.lnb);  // ln b - ln R
   const float2 xp = mul2(g.qx, e.iq);                               // x'
   const float2 dphq = mul2(mul2(xp, g.yp), neg2(iR2));              // d vphi / d ln q
@@ -390,11 +392,8 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
     const float2 Pr = make_float2(t0.Pr, t1.Pr), Pi = make_float2(t0.Pi, t1.Pi);
     const float2 Qtr = make_float2(t0.Qr, t1.Qr), Qti = make_float2(t0.Qi, t1.Qi);
     const float2 Ttr = make_float2(t0.Tr, t1.Tr), Tti = make_float2(t0.Ti, t1.Ti);
-    const float2 PFr = fma2(Qr, Pr, mul2(nQi, Pi)), PFi = fma2(Qr, Pi, mul2(Qi, Pr));
-    const float2 QFr = fma2(Qr, Qtr, mul2(nQi, Qti)), QFi = fma2(Qr, Qti, mul2(Qi, Qtr));
-    const float2 TFr = fma2(Qr, Ttr, mul2(nQi, Tti)), TFi = fma2(Qr, Tti, mul2(Qi, Ttr));
-    const float2 S13 = add2(s1i, fma2(vLx, PFr, mul2(vLy, PFi)));
-    const float2 sQ = fma2(vLx, QFr, mul2(vLy, QFi)), sT = fma2(vLx, TFr, mul2(vLy, TFi));
+    const float2 S13 = add2(s1i, fma2(Gr, Pr, mul2(nGi, Pi)));
+    const float2 sQ = fma2(Gr, Qtr, mul2(nGi, Qti)), sT = fma2(Gr, Ttr, mul2(nGi, Tti));
     acc_add(acc[0], s1);
     acc_add(acc[1], sT);
     acc_fma(acc[1], s1, lnbR);
@@ -408,19 +407,18 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
     acc_add(acc[5], Dy);
     return;
   }
-  const float2 QTr = fma2(Qr, dtFr, mul2(nQi, dtFi)), QTi = fma2(Qr, dtFi, mul2(Qi, dtFr));
-  const float2 sT = fma2(vLx, QTr, mul2(vLy, QTi));
-  // F'(z) = [t F - (2-t) E] / (2 (1 - z))
+  const float2 sT = fma2(Gr, dtFr, mul2(nGi, dtFi));  // v . (A e^{i vphi} dF/dt)
+  // H = F'(z) w with F'(z) = [t F - (2-t) E] / (2 (1 - z)), 1 - z = 1 + f w and
+  // |w| = 1: H = n / (2 (conj(w) + f)), n = t F - (2-t) E
   const float2 nr = fma2(e.t, Fr, mul2(e.ntmt, Er)), ni = fma2(e.t, Fi, mul2(e.ntmt, Ei));
-  const float2 ozr = fma2(e.f, g.wr, f2(1.f));  // 1 - z = (ozr, -zi)
-  const float2 inv = mul2(f2(0.5f), rcp2(fma2(ozr, ozr, mul2(zi, zi))));
-  const float2 Fpr = mul2(fma2(nr, ozr, mul2(ni, nzi)), inv);
-  const float2 Fpi = mul2(fma2(ni, ozr, mul2(nr, zi)), inv);
-  const float2 P2r = fma2(Qr, Fpr, mul2(nQi, Fpi)), P2i = fma2(Qr, Fpi, mul2(Qi, Fpr));
-  const float2 P3r = fma2(P2r, g.wr, mul2(P2i, g.nwi)), P3i = fma2(P2r, g.wi, mul2(P2i, g.wr));
-  const float2 s3 = fma2(vLx, P3r, mul2(vLy, P3i));
-  const float2 s3i = fma2(vLy, P3r, mul2(nvLx, P3i));
-  const float2 S13 = fma2(e.m2f, s3i, s1i);
+  // (the floor only acts at the clamped lens centre, where e^{i vphi} = 0 and G = 0)
+  const float2 dr = add2(g.wr, e.f);  // conj(w) + f = (dr, -wi)
+  const float2 inv = mul2(f2(0.5f), rcp2(max2(fma2(dr, dr, mul2(g.wi, g.wi)), 1e-30f)));
+  const float2 Hr = mul2(fma2(nr, dr, mul2(ni, g.nwi)), inv);
+  const float2 Hi = mul2(fma2(nr, g.wi, mul2(ni, dr)), inv);
+  const float2 s3 = fma2(Gr, Hr, mul2(nGi, Hi));  // v . (A e^{i vphi} F' w)
+  const float2 t3 = fma2(Gr, Hi, mul2(Gi, Hr));   // -v . (i A e^{i vphi} F' w)
+  const float2 S13 = fma2(neg2(e.m2f), t3, s1i);
   acc_add(acc[0], s1);
   acc_add(acc[1], sT);
   acc_fma(acc[1], s1, lnbR);
