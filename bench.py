@@ -60,24 +60,28 @@ def series_terms(f: float, t: float) -> int:
 
 def algorithmic_ops(theta: np.ndarray, ny: int, nx: int, s: int, k: int, n_light: int,
                     n_src: int) -> tuple:
-    """FP32 operations (an FMA counts once) and MUFU operations of one
-    log p + gradient evaluation per row, summed over rows, from the
-    formulation's operation count:
-      forward sub-pixel  34 + 2N (EPL) + 8 (shear, lens equation)
-                         + 15 per Sersic + 2 (grid) ... 3 MUFU EPL, 3 per Sersic
-      adjoint sub-pixel  38 + 4N (EPL, both series) + 8 + 31 per Sersic
-                         + 6 per source (position gradient) + 85 (EPL adjoint)
-                         + 2 (grid) ... 4 MUFU EPL, 4 per Sersic
+    """FP32 operations (an FMA counts once, per lane) and MUFU operations of
+    one log p + gradient evaluation per row, summed over rows, counted term
+    by term from the formulation the kernels evaluate (negations fold into
+    the consuming operation and are not counted; max/select are ALU work):
+      forward sub-pixel  2 (grid) + 14 (EPL frame, w) + 1 + 2N (series)
+                         + 4 (F) + 16 (deflection, shear, lens equation)
+                         + 11 per Sersic + (components - 1) (sum) + 1 (bin)
+                         ... 3 MUFU for the EPL, 3 per Sersic
+      adjoint sub-pixel  2 + 15 + 1 + 4N (both series) + 10 (E, F, dF/dt)
+                         + 16 + 26 per Sersic + 6 per source (position
+                         gradient) + 78 (EPL and shear adjoint)
+                         ... 4 MUFU for the EPL, 4 per Sersic
       per pixel          2 k^2 (PSF convolution and its adjoint) + 8
-    with N the per-row series length; a series costs 2 operations per term
-    (Clenshaw's recurrence: one FMA and one add)."""
+    with N the row's series length (Clenshaw's recurrence: two operations
+    per term)."""
     nsub = ny * nx * s * s
     npix = ny * nx
     ncomp = n_light + n_src
     f = np.hypot(theta[:, 2], theta[:, 3])
     N = np.array([series_terms(float(v), float(g) - 1.0) for v, g in zip(f, theta[:, 1])])
-    fwd = 34 + 2 * N + 8 + 15 * ncomp + 2
-    adj = 38 + 4 * N + 8 + 31 * ncomp + 6 * n_src + 85 + 2
+    fwd = 2 + 14 + 1 + 2 * N + 4 + 16 + 11 * ncomp + (ncomp - 1) + 1
+    adj = 2 + 15 + 1 + 4 * N + 10 + 16 + 26 * ncomp + 6 * n_src + 78
     ops = nsub * (fwd + adj) + npix * (2 * k * k + 8)
     mufu = nsub * (3 + 3 * ncomp + 4 + 4 * ncomp)
     return float(ops.sum()), float(mufu * theta.shape[0])
