@@ -87,9 +87,8 @@ struct EplP {
   float2 f, nf, m2f;          // f = |e|, -f, -2f
   float2 ht, CA;              // (1 - t)/2, 2 b^t / (1 + q)
   float2 t, omt, ntmt;        // t, 1 - t, -(2 - t)
-  float2 omtq, omtq2;         // (1 - t) q, (1 - t) q^2
+  float2 omtq;                // (1 - t) q
   float2 Kk;                  // kappa = Kk A / R
-  float2 a0;                  // t/(2q) - 1/(1+q)
   float2 lnb;
   float2 ndfdq;               // -d f / d q = 2/(1+q)^2
 };
@@ -240,9 +239,8 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
       E.ht = f2(0.5f * (1.f - t));
       E.CA = f2(2.f * powf(b, t) / (1.f + q));
       E.t = f2(t); E.omt = f2(1.f - t); E.ntmt = f2(t - 2.f);
-      E.omtq = f2((1.f - t) * q); E.omtq2 = f2((1.f - t) * q * q);
+      E.omtq = f2((1.f - t) * q);
       E.Kk = f2((2.f - t) * (1.f + q) * 0.25f);
-      E.a0 = f2(t / (2.f * q) - 1.f / (1.f + q));
       E.lnb = f2(logf(b));
       E.ndfdq = f2(2.f / ((1.f + q) * (1.f + q)));
       F.p0 = th[0]; F.t = t; F.n = 0.f; F.I = 0.f; F.bn = 0.f;
@@ -355,7 +353,10 @@ __device__ inline void epl_finish(const FinishC& F, const double* a, float* g,
   const float cc = fmaxf(F.c, 1e-30f);
   const float c2p = F.cs * F.cs - F.sn * F.sn, s2p = 2.f * F.cs * F.sn;  // as in sersic_finish
   const float dqdc = -2.f / ((1.f + F.c) * (1.f + F.c));
-  const float dq = (float)a[2], rot = (float)a[3];
+  // a[2] holds the q-derivative without its constant part a0 sum s1, a0 =
+  // t/(2q) - 1/(1+q) (the derivative of ln of the deflection prefactor)
+  const double a0 = (double)F.t / (2.0 * F.q) - 1.0 / (1.0 + F.q);
+  const float dq = (float)(a[2] + a0 * a[0]), rot = (float)a[3];
   g[0] = F.t / F.p0 * (float)a[0];
   g[1] = (float)a[1];
   if (rot_is_dphi) {

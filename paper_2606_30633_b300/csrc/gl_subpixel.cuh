@@ -305,10 +305,10 @@ __device__ __forceinline__ void sersic_adj2(const LightP& c, float2 X, float2 Y,
   const float2 S = mul2(c.Ip, ex2_2(mul2(c.nbl, p)));
   const float2 Sp = mul2(S, p);
   // d R^2 / d(position) vanishes where the radius is clamped
-  float2 Dh = mul2(Sp, rcp2(R2));
-  Dh.x = R2raw.x > R_MIN2 ? Dh.x : 0.f;
-  Dh.y = R2raw.y > R_MIN2 ? Dh.y : 0.f;
-  const float2 uSp = mul2(u, Sp), kD = mul2(u, Dh);
+  float2 rR2 = rcp2(R2);
+  rR2.x = R2raw.x > R_MIN2 ? rR2.x : 0.f;
+  rR2.y = R2raw.y > R_MIN2 ? rR2.y : 0.f;
+  const float2 uSp = mul2(u, Sp), kD = mul2(uSp, rR2);
   acc_fma(a[0], u, S);
   acc_add(a[1], uSp);
   acc_fma(a[2], uSp, l2p);
@@ -317,6 +317,7 @@ __device__ __forceinline__ void sersic_adj2(const LightP& c, float2 X, float2 Y,
   acc_fma(a[5], kD, us);
   acc_fma(a[6], kD, vs);
   if (grad_pos) {
+    const float2 Dh = mul2(Sp, rR2);
     gX = fma2(Dh, fma2(c.kX1, us, mul2(c.kX2, vs)), gX);
     gY = fma2(Dh, fma2(c.kY1, us, mul2(c.kY2, vs)), gY);
   }
@@ -385,8 +386,10 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
   const float2 nGi = neg2(Gi);
   const float2 lnbR = fma2(f2(-0.34657359027997264f), Lm, e.lnb);  // ln b - ln R
   const float2 xp = mul2(g.qx, e.iq);                               // x'
-  const float2 dphq = mul2(mul2(xp, g.yp), neg2(iR2));              // d vphi / d ln q
-  const float2 aq = fma2(mul2(mul2(e.omtq, xp), xp), iR2, e.a0);
+  const float2 xR = mul2(iR2, xp);
+  // acc[2] (d/dq) takes S13 d vphi/d ln q + s1 ((1-t) q x'^2/R^2 + a0) with
+  // d vphi/d ln q = -x'y'/R^2: x'/R^2 ((1-t) q x' s1 - y' S13) per sub-pixel;
+  // the constant part a0 sum s1 = a0 acc[0] is added per sample (epl_finish)
   if (TAB) {
     // table derivatives at fixed (the other) arguments: dF/dvphi, dF/dq, dF/dt
     const float2 Pr = make_float2(t0.Pr, t1.Pr), Pi = make_float2(t0.Pi, t1.Pi);
@@ -398,9 +401,9 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
     acc_add(acc[1], sT);
     acc_fma(acc[1], s1, lnbR);
     acc_add(acc[2], sQ);
-    acc_fma(acc[2], S13, dphq);
-    acc_fma(acc[2], s1, aq);
-    const float2 Dx = mul2(iR2, fma2(mul2(e.omtq2, xp), s1, mul2(mul2(e.nq, g.yp), S13)));
+    const float2 yS = mul2(g.yp, S13);
+    acc_fma(acc[2], xR, fma2(mul2(e.omtq, xp), s1, neg2(yS)));
+    const float2 Dx = mul2(iR2, fma2(mul2(e.omtq, g.qx), s1, mul2(e.nq, yS)));
     const float2 Dy = mul2(iR2, fma2(mul2(e.omt, g.yp), s1, mul2(g.qx, S13)));
     acc_add(acc[3], fma2(g.yp, Dx, fma2(neg2(xp), Dy, s1i)));  // d alpha/d phi
     acc_add(acc[4], Dx);
@@ -423,8 +426,8 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
   acc_add(acc[1], sT);
   acc_fma(acc[1], s1, lnbR);
   acc_fma(acc[2], e.ndfdq, s3);
-  acc_fma(acc[2], S13, dphq);
-  acc_fma(acc[2], s1, aq);
+  const float2 yS = mul2(g.yp, S13);
+  acc_fma(acc[2], xR, fma2(mul2(e.omtq, xp), s1, neg2(yS)));
   // rotation: d alpha'/d phi = i X with X = (2-t) alpha' - 2 kappa z' =
   // -2 kappa f (z' w E + conj(z') F), which is O(f); acc[3] = sum kappa v.(iY)
   const float2 kap = mul2(mul2(e.Kk, A), g.ir);
@@ -432,7 +435,7 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
   const float2 Yr = fma2(zwr, Er, fma2(neg2(zwi), Ei, fma2(xp, Fr, mul2(g.yp, Fi))));
   const float2 Yi = fma2(zwr, Ei, fma2(zwi, Er, fma2(xp, Fi, mul2(neg2(g.yp), Fr))));
   acc_fma(acc[3], kap, fma2(vLy, Yr, mul2(nvLx, Yi)));
-  acc_fma(acc[4], iR2, fma2(mul2(e.omtq2, xp), s1, mul2(mul2(e.nq, g.yp), S13)));
+  acc_fma(acc[4], iR2, fma2(mul2(e.omtq, g.qx), s1, mul2(e.nq, yS)));  // (1-t) q^2 x' = (1-t) q qx
   acc_fma(acc[5], iR2, fma2(mul2(e.omt, g.yp), s1, mul2(g.qx, S13)));
 }
 
