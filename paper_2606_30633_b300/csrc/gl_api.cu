@@ -360,6 +360,7 @@ static gl_status run_forward(gl_system* sys, const float* theta, int B, float* l
 
 gl_status gl_logp(gl_system* sys, const float* theta, int B, float* logp, gl_deflection defl,
                   void* stream) {
+  gl::Range nvtx_range("gl_logp");
   gl_status r = check_call(sys, theta, B, logp, defl);
   if (r != GL_OK) return r;
   if (B == 0) return GL_OK;
@@ -369,6 +370,7 @@ gl_status gl_logp(gl_system* sys, const float* theta, int B, float* logp, gl_def
 
 gl_status gl_model_image(gl_system* sys, const float* theta, int B, float* img,
                          gl_deflection defl, void* stream) {
+  gl::Range nvtx_range("gl_model_image");
   gl_status r = check_call(sys, theta, B, img, defl);
   if (r != GL_OK) return r;
   if (B == 0) return GL_OK;
@@ -378,6 +380,7 @@ gl_status gl_model_image(gl_system* sys, const float* theta, int B, float* img,
 
 gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, float* grad,
                        gl_deflection defl, void* stream) {
+  gl::Range nvtx_range("gl_logp_grad");
   gl_status r = check_call(sys, theta, B, logp, defl);
   if (r != GL_OK) return r;
   if (B > 0 && !grad) return fail(GL_EINVAL, "grad is NULL");
@@ -403,6 +406,7 @@ gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, f
 
 gl_status gl_leapfrog(gl_system* sys, float* theta, float* p, float* logp, float* grad,
                       const float* inv_mass, float eps, int n_steps, int B, void* stream) {
+  gl::Range nvtx_range("gl_leapfrog");
   if (!sys) return fail(GL_EINVAL, "system is NULL");
   if (B < 0 || n_steps < 0) return fail(GL_EINVAL, "B and n_steps must be >= 0");
   if (!std::isfinite(eps)) return fail(GL_EINVAL, "eps must be finite");
@@ -461,6 +465,7 @@ gl_status gl_leapfrog(gl_system* sys, float* theta, float* p, float* logp, float
 
 gl_status gl_logp_grad_host(gl_system* sys, const float* theta_host, int B, float* logp_host,
                             float* grad_host, gl_deflection defl, void* stream) {
+  gl::Range nvtx_range("gl_logp_grad_host");
   gl_status r = check_call(sys, theta_host, B, logp_host, defl);
   if (r != GL_OK) return r;
   if (B == 0) return GL_OK;

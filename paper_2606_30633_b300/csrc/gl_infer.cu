@@ -954,6 +954,7 @@ gl_status gl_bijector_inverse(gl_system* sys, const float* theta, int B, float* 
 
 gl_status gl_logp_grad_unconstrained(gl_system* sys, const float* u, int B, float* logp,
                                      float* grad, gl_deflection defl, void* stream) {
+  gl::Range nvtx_range("gl_logp_grad_unconstrained");
   if (!sys) return fail(GL_EINVAL, "system is NULL");
   if (B < 0) return fail(GL_EINVAL, "B < 0");
   if (B == 0) return GL_OK;
@@ -993,6 +994,7 @@ gl_status gl_logp_grad_unconstrained(gl_system* sys, const float* u, int B, floa
 gl_status gl_map_adam(gl_system* sys, float* u, float* m, float* v, int B, int n_steps, int t0,
                       float lr, float beta1, float beta2, float eps, float* logp,
                       gl_deflection defl, void* stream) {
+  gl::Range nvtx_range("gl_map_adam");
   if (!sys) return fail(GL_EINVAL, "system is NULL");
   if (B < 0 || n_steps < 0 || t0 < 0) return fail(GL_EINVAL, "B, n_steps and t0 must be >= 0");
   if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
@@ -1166,6 +1168,7 @@ gl_status gl_hmc_set_inv_mass(gl_hmc* h, const float* inv_mass, void* stream) {
 }
 
 gl_status gl_hmc_run(gl_hmc* h, int n, int flags, float* draws, float* accept, void* stream) {
+  gl::Range nvtx_range("gl_hmc_run");
   if (!h) return fail(GL_EINVAL, "sampler is NULL");
   if (n < 0) return fail(GL_EINVAL, "n must be >= 0");
   if (flags & ~(GL_HMC_ADAPT_STEP | GL_HMC_COLLECT_MOMENTS)) return fail(GL_EINVAL, "unknown flags");
@@ -1273,6 +1276,7 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
                            int t0, float lr, float beta1, float beta2, float eps,
                            unsigned long long seed, float* elbo, gl_deflection defl,
                            void* stream) {
+  gl::Range nvtx_range("gl_svi_adabelief");
   if (!sys) return fail(GL_EINVAL, "system is NULL");
   if (n_samples < 1 || n_steps < 0 || t0 < 0)
     return fail(GL_EINVAL, "need n_samples >= 1, n_steps >= 0, t0 >= 0");
@@ -1364,6 +1368,7 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
 // ------------------------------------------------ backward intensities ----
 gl_status gl_logp_grad_backward(gl_system* sys, const float* theta, int B, float* logp,
                                 float* grad, float* intensity, gl_deflection defl, void* stream) {
+  gl::Range nvtx_range("gl_logp_grad_backward");
   if (!sys) return fail(GL_EINVAL, "system is NULL");
   if (B < 0) return fail(GL_EINVAL, "B < 0");
   if (B == 0) return GL_OK;

@@ -5,9 +5,20 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 struct gl_surrogate;
 
 namespace gl {
+
+// NVTX range over one library call: named spans on an Nsight Systems
+// timeline; a no-op unless a tool is attached (NVTX3 is header-only).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 constexpr int MAX_K = 21;      // largest PSF side
 constexpr int MAX_S = 8;       // largest supersampling factor

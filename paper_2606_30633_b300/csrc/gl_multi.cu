@@ -156,6 +156,7 @@ gl_status gl_multi_create(gl_system* const* systems, int n_sys, const int* rows_
 
 gl_status gl_multi_logp_grad(gl_multi* m, const float* const* theta, float* const* logp,
                              float* const* grad, gl_deflection defl, void* stream) {
+  gl::Range nvtx_range("gl_multi_logp_grad");
   if (!m) return fail(GL_EINVAL, "multi is NULL");
   if (!theta || !logp || !grad) return fail(GL_EINVAL, "NULL pointer arrays");
   if (defl != GL_DEFL_SERIES && defl != GL_DEFL_SURROGATE && defl != GL_DEFL_TABLE)

@@ -58,6 +58,7 @@ cudaError_t scratch_address(int dev, float** out) {
 
 extern "C" gl_status gl_logp_grad_noalloc(gl_system* sys, const float* theta, int B, float* logp,
                                           float* grad, void* stream) {
+  gl::Range nvtx_range("gl_logp_grad_noalloc");
   if (!sys) return fail(GL_EINVAL, "system is NULL");
   if (B < 0) return fail(GL_EINVAL, "B < 0");
   if (B > 0 && (!theta || !logp || !grad)) return fail(GL_EINVAL, "NULL theta, logp or grad");

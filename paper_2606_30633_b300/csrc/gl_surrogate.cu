@@ -1090,6 +1090,7 @@ gl_status gl_surrogate_loss_grad(const gl_surrogate* s, const float* x, const fl
 
 gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** out,
                              float* final_loss) {
+  gl::Range nvtx_range("gl_surrogate_train");
   if (!d || !out) return fail(GL_EINVAL, "NULL argument");
   *out = nullptr;
   if (d->n_samples < TILE || d->batch < TILE || d->batch % TILE != 0 || d->epochs < 1)
