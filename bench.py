@@ -164,6 +164,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(t_ms: float, world: int, device) -> float:
+    """The job's timed total: the slowest rank's (an all-reduce MAX over the
+    process group; each rank's own total when there is one rank)."""
+    if world == 1:
+        return t_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, t_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (ranks hold equal shares of the work: weak scaling)."""
+    return world * units_per_rank / (t_ms / 1e3)
+
+
 def run_reference(args) -> dict | None:
     """The FP64 oracle (value + dual-number gradient, OpenMP over rows) on the
     host cores, on a bounded sample of the same workload."""
@@ -359,11 +377,8 @@ def run_ours(args) -> dict | None:
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * B * args.steps / (t_ms / 1e3)
+    t_ms = max_over_ranks(t_ms, world, dev)
+    value = job_rate(B * args.steps, world, t_ms)
     assert torch.isfinite(logp).all(), "non-finite log p in the benchmark batch"
 
     # end to end through the public API with host buffers
@@ -483,11 +498,8 @@ def run_leapfrog(args) -> dict | None:
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * B * L * args.steps / (t_ms / 1e3)
+    t_ms = max_over_ranks(t_ms, world, dev)
+    value = job_rate(B * L * args.steps, world, t_ms)
     u_end, lp_end, _, _ = h.state()
     h.close()
     finite = float(torch.isfinite(lp_end).float().mean())
@@ -613,11 +625,8 @@ def run_uneven(args) -> dict | None:
     h2d = sum(t.numel() * 4 for t in thetas)
     d2h = sum(t.numel() * 4 + t.shape[0] * 4 for t in thetas)
     t_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * n_rows * args.steps / (t_ms / 1e3)
+    t_ms = max_over_ranks(t_ms, world, dev)
+    value = job_rate(n_rows * args.steps, world, t_ms)
     ops = 0.0
     for W, th in zip(Ws, thetas):
         o, _ = algorithmic_ops(th.double().cpu().numpy(), W.ny, W.nx, W.supersample,
@@ -739,11 +748,8 @@ def run_pipeline(args) -> dict | None:
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * B * L * args.steps / (t_ms / 1e3)
+    t_ms = max_over_ranks(t_ms, world, dev)
+    value = job_rate(B * L * args.steps, world, t_ms)
     u_end, lp_end, _, eps = h.state()
     h.close()
     # end to end: chain starts from pinned host memory, one transition, the
