@@ -38,6 +38,18 @@ METRIC = "logp+grad evals/s (100x100 px, 3x SS) on 1 B300, learned vs plain; % r
 SM_COUNT_B300 = 148
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM_CLK = 16
+# DRAM bytes (read + write) of one k_grad launch of the ground-based workload
+# (4096 rows), from one ncu capture of this bench's own launch:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+#       -k regex:k_grad -s 3 -c 1 python bench.py --steps 5 --warmup 3 --no-cpu-baseline
+# (626,432 read + 0 written; the outputs are still in L2 when the launch ends).
+# Set to None when the kernel changes until it is captured again.
+TRAFFIC_GROUND_4096 = 626432
+# DRAM bytes of one k_grad launch of the space-telescope workload per row,
+# from one --set full capture of a 512-row launch inside the HMC leg
+# (24,538,112 read + 181,527,296 written); the traffic is the per-row scratch
+# images, so it grows in proportion to the rows. None when the kernel changes.
+TRAFFIC_SPACE_PER_ROW = (24538112 + 181527296) / 512
 
 
 # ------------------------------------------------------------ op counts ----
@@ -415,10 +427,13 @@ def run_ours(args) -> dict | None:
                        "parallelism": f"replicas x{world}"},
             "learned": learned,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": TRAFFIC_GROUND_4096 if B == 4096 else None,
+                         "algorithmic_bytes": B * (2 * W.P + 1) * 4 + 2 * W.ny * W.nx * 4,
                          "note": "FP32 lane-operations (FMA = 1) of the formulation's op "
                                  "count per evaluation / mean step time; peak = 148 SM x 128 "
-                                 "lanes x 2032 MHz",
+                                 "lanes x 2032 MHz; traffic = ncu DRAM bytes of the k_grad "
+                                 "launch (one pass, captured on this bench's launch)",
                          "mufu_ops_per_step": mufu,
                          "measured_unit_rates": rates,
                          "mufu": mufu_roof},
@@ -543,7 +558,10 @@ def run_leapfrog(args) -> dict | None:
                        "l2": "flushed (256 MB write) before every timed step",
                        "finite_chains_at_end": finite},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None},
+                         "frac": achieved / peak,
+                         "traffic": TRAFFIC_SPACE_PER_ROW * B,
+                         "traffic_note": "ncu DRAM bytes of a 512-row launch scaled to the "
+                                         "launch's rows (per-row scratch images)"},
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": B * W.P * 4,
                     "d2h_bytes_per_step": B * 4},
             "gpu_launches": (2 * L + 4) * args.steps,
