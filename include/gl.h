@@ -282,8 +282,8 @@ gl_status gl_surrogate_infer(const gl_surrogate* sur, const float* x, int N, flo
 /* The exact F = 2F1(1, t/2; 2 - t/2; -f e^{2 i vphi}) (Sec. 3 mass model,
  * the series of Tessore & Metcalf 2015), summed in FP64 on the device until
  * the terms fall below 1e-18, for N raw inputs x: device [N][4] = (q, gamma,
- * ignored, vphi) -> F: device [N][2] (Re, Im, rounded to FP32); the judge of
- * the surrogate's deflection error. Tuples outside 0.01 <= q <= 1,
+ * ignored, vphi) -> F: device [N][2] (Re, Im, rounded to FP32); the
+ * reference the surrogate's deflection error is measured against. Tuples outside 0.01 <= q <= 1,
  * 1 < gamma < 3 (or not finite) give NaN. Asynchronous on stream; GL_EINVAL for N < 0, NULL
  * pointers with N > 0, or x not 16-byte / F not 8-byte aligned. */
 gl_status gl_series_F(const float* x, int N, float* F, void* stream);

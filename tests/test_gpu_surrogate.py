@@ -88,7 +88,7 @@ def test_trained_network_against_the_exact_series(gl, trained):
                                                                     dal.max())
     assert np.sqrt(np.mean(d ** 2)) < 0.01 * np.sqrt(np.mean(base ** 2))  # the network's gain
     assert trained.final_loss < 1e-4
-    # the library's own exact series (the surrogate's judge) on the same tuples
+    # the library's own exact series (the reference the surrogate is measured against)
     Fx = g.series_F(torch.tensor(X, device="cuda")).cpu().numpy()
     np.testing.assert_allclose(Fx[:, 0] + 1j * Fx[:, 1], Fe, rtol=0, atol=3e-7)
 
