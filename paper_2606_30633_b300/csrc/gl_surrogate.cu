@@ -25,6 +25,8 @@ struct gl_surrogate {
   int device = 0;
   float* params = nullptr;        // [NPARAM] FP32 master weights
   __nv_bfloat16* wb = nullptr;    // [NBF16] packed BF16 operands
+  unsigned char* wimg = nullptr;  // [TRAIN_IMG_BYTES] the training kernel's weight operands,
+                                  // byte for byte as it lays them out in shared memory
   float final_loss = NAN;
   float q_lo = 0.5f, q_hi = 1.f, g_lo = 1.7f, g_hi = 2.3f;  // training domain
 };
@@ -122,8 +124,20 @@ __global__ void k_init_params(float* __restrict__ p, uint64_t seed) {
   p[k] = v;
 }
 
-// FP32 parameters -> BF16 operand layouts (gl_mlp.cuh).
-__global__ void k_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ wb) {
+// The training kernel's hidden-layer weight operands as it holds them in
+// shared memory: P1 [64][16], then P2..P4 and T2..T4 [64][64], each in the
+// canonical K-major core-matrix layout (8 x 16-byte core matrices, K-adjacent
+// ones 128 B apart). k_pack writes this image next to the plain operands, so
+// the training kernel stages it with coalesced 16-byte copies.
+constexpr int TRAIN_IMG_BYTES = 64 * 16 * 2 + 6 * 64 * 64 * 2;
+__device__ __forceinline__ int img_core_off(int r, int k, int K) {
+  return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// FP32 parameters -> BF16 operand layouts (gl_mlp.cuh), and the training
+// kernel's shared-memory image of P1..P4, T2..T4 (img, may be null).
+__global__ void k_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ wb,
+                       unsigned char* __restrict__ img) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= NBF16) return;
   float v = 0.f;
@@ -146,7 +160,21 @@ __global__ void k_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ 
     const int i = (k - BOFF_T5) / 16, o = (k - BOFF_T5) % 16;
     v = o < NOUT ? p[OFF_W5 + o * H + i] : 0.f;
   }
-  wb[k] = __float2bfloat16_rn(v);
+  const __nv_bfloat16 b = __float2bfloat16_rn(v);
+  wb[k] = b;
+  if (img) {
+    int off = -1;
+    if (k < BOFF_P2) {
+      off = img_core_off((k - BOFF_P1) / 16, (k - BOFF_P1) % 16, 16);
+    } else if (k < BOFF_P5) {
+      const int l = (k - BOFF_P2) / (H * H), r = (k - BOFF_P2) % (H * H);
+      off = 64 * 16 * 2 + l * H * H * 2 + img_core_off(r / H, r % H, H);
+    } else if (k >= BOFF_T2 && k < BOFF_T5) {
+      const int l = (k - BOFF_T2) / (H * H), r = (k - BOFF_T2) % (H * H);
+      off = 64 * 16 * 2 + 3 * H * H * 2 + l * H * H * 2 + img_core_off(r / H, r % H, H);
+    }
+    if (off >= 0) *reinterpret_cast<__nv_bfloat16*>(img + off) = b;
+  }
 }
 
 // Sum of the tiles' gradients and Adam (FP32 master weights); writes the
@@ -685,7 +713,8 @@ __device__ void colsum(const float (&v)[N], float* red, float* __restrict__ dst)
 }  // namespace tc
 
 __global__ void __launch_bounds__(tc::NT, 1)
-k_train_tc(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
+k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict__ wimg,
+           const float* __restrict__ params,
            const float4* __restrict__ X, const float2* __restrict__ Y, long long n_data,
            long long row0, long long stride, float inv_batch, float* __restrict__ gpart,
            float* __restrict__ lpart, int* __restrict__ timeout) {
@@ -698,13 +727,14 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ param
   float* gp = gpart + (size_t)blockIdx.x * NPARAM;
   float* red = reinterpret_cast<float*>(sm + TR_RED);
   // weights in the operand layout; zero the transposed buffers (padding rows)
-  load_operand(sm + TR_W1, wb + BOFF_P1, 64, 16, 64);
-  load_operand(sm + TR_WH, wb + BOFF_P2, 64, 64, 64);
-  load_operand(sm + TR_WH + 8192, wb + BOFF_P3, 64, 64, 64);
-  load_operand(sm + TR_WH + 16384, wb + BOFF_P4, 64, 64, 64);
-  load_operand(sm + TR_TH, wb + BOFF_T2, 64, 64, 64);
-  load_operand(sm + TR_TH + 8192, wb + BOFF_T3, 64, 64, 64);
-  load_operand(sm + TR_TH + 16384, wb + BOFF_T4, 64, 64, 64);
+  static_assert(TR_W1 == 0 && TR_WH == 64 * 16 * 2 && TR_A == TRAIN_IMG_BYTES,
+                "the packed image must match the shared-memory operand layout");
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(wimg);
+    uint4* dst = reinterpret_cast<uint4*>(sm + TR_W1);
+#pragma unroll 5
+    for (int k = t; k < TRAIN_IMG_BYTES / 16; k += NT) dst[k] = src[k];
+  }
   for (int k = t; k < (TR_AT - TR_XT) / 16; k += NT)
     reinterpret_cast<uint4*>(sm + TR_XT)[k] = make_uint4(0u, 0u, 0u, 0u);
   for (int k = t; k < (TR_RED - TR_DZT) / 16; k += NT)
@@ -967,9 +997,11 @@ gl_status sur_alloc(gl_surrogate** out) {
   gl_surrogate* s = new gl_surrogate();
   cudaGetDevice(&s->device);
   if (cudaMalloc(&s->params, NPARAM * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&s->wb, NBF16 * sizeof(__nv_bfloat16)) != cudaSuccess) {
+      cudaMalloc(&s->wb, NBF16 * sizeof(__nv_bfloat16)) != cudaSuccess ||
+      cudaMalloc(&s->wimg, TRAIN_IMG_BYTES) != cudaSuccess) {
     cudaFree(s->params);
     cudaFree(s->wb);
+    cudaFree(s->wimg);
     delete s;
     return fail(GL_ENOMEM, "surrogate allocation failed");
   }
@@ -1008,7 +1040,7 @@ gl_status gl_surrogate_create(const float* params_host, gl_surrogate** out) {
   if (r != GL_OK) return r;
   cudaError_t e = cudaMemcpy(s->params, params_host, NPARAM * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    k_pack<<<(NBF16 + 255) / 256, 256>>>(s->params, s->wb);
+    k_pack<<<(NBF16 + 255) / 256, 256>>>(s->params, s->wb, s->wimg);
     e = cudaDeviceSynchronize();
   }
   if (e != cudaSuccess) {
@@ -1031,6 +1063,7 @@ void gl_surrogate_destroy(gl_surrogate* s) {
   cudaDeviceSynchronize();
   cudaFree(s->params);
   cudaFree(s->wb);
+  cudaFree(s->wimg);
   delete s;
 }
 
@@ -1075,7 +1108,7 @@ gl_status gl_surrogate_loss_grad(const gl_surrogate* s, const float* x, const fl
   int* flag = nullptr;
   SUR_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), gl::g_table_timeout), "flag");
   gl::k_train_tc<<<ntiles, gl::tc::NT, gl::tc::TR_SMEM>>>(
-      s->wb, s->params, reinterpret_cast<const float4*>(x),
+      s->wb, s->wimg, s->params, reinterpret_cast<const float4*>(x),
       reinterpret_cast<const float2*>(target), N, 0, 1, 1.f / N, tb.gpart, tb.lpart, flag);
   k_adam<<<(NPARAM + 255) / 256, 256>>>(nullptr, nullptr, nullptr, tb.gpart, ntiles, 0.f, 0.f, 0.f,
                                        0.f, 1.f, 1.f, tb.loss);
@@ -1144,9 +1177,10 @@ gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** ou
     const float lr = (float)(d->lr_min + 0.5 * (d->lr - d->lr_min) * (1.0 + cos(3.14159265358979323846 * frac)));
     bc1 *= b1;
     bc2 *= b2;
-    k_pack<<<(NBF16 + 255) / 256, 256>>>(s->params, s->wb);
+    k_pack<<<(NBF16 + 255) / 256, 256>>>(s->params, s->wb, s->wimg);
     const long long row0 = (it * (long long)d->batch) % n;
-    gl::k_train_tc<<<ntiles, gl::tc::NT, gl::tc::TR_SMEM>>>(s->wb, s->params, tb.X, tb.Y, n, row0,
+    gl::k_train_tc<<<ntiles, gl::tc::NT, gl::tc::TR_SMEM>>>(s->wb, s->wimg, s->params, tb.X, tb.Y,
+                                                            n, row0,
                                                             stride, 1.f / d->batch, tb.gpart,
                                                             tb.lpart, flag);
     k_adam<<<(NPARAM + 255) / 256, 256>>>(s->params, tb.m, tb.v, tb.gpart, ntiles, lr, b1, b2,
@@ -1156,7 +1190,7 @@ gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** ou
       if (e != cudaSuccess) return bail(fail(GL_ECUDA, std::string("training: ") + cudaGetErrorString(e)));
     }
   }
-  k_pack<<<(NBF16 + 255) / 256, 256>>>(s->params, s->wb);
+  k_pack<<<(NBF16 + 255) / 256, 256>>>(s->params, s->wb, s->wimg);
   // final loss over the last batch's tiles
   k_sum<<<1, 256>>>(tb.lpart, ntiles, tb.loss);
   float lsum = 0.f;
