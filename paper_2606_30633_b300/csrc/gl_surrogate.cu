@@ -496,7 +496,8 @@ __device__ __forceinline__ void put8(unsigned char* base, int r, int k0, int K, 
 }  // namespace tc
 
 __global__ void __launch_bounds__(tc::NT, 1)
-k_table_tc(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
+k_table_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict__ wimg,
+           const float* __restrict__ params,
            const float* __restrict__ theta, int P, int B, float q_lo, float q_hi, float g_lo,
            float g_hi, float4* __restrict__ table, int* __restrict__ timeout) {
   using namespace tc;
@@ -504,10 +505,15 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const float* __restrict__ param
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t bar;
   const int t = threadIdx.x, w = t >> 5;
-  load_operand(sm + TB_W1, wb + BOFF_P1, 64, 16, 64);
-  load_operand(sm + TB_WH, wb + BOFF_P2, 64, 64, 64);
-  load_operand(sm + TB_WH + WH_BYTES, wb + BOFF_P3, 64, 64, 64);
-  load_operand(sm + TB_WH + 2 * WH_BYTES, wb + BOFF_P4, 64, 64, 64);
+  // P1..P4 are the first bytes of the packed training image (same layout)
+  static_assert(TB_W1 == 0 && TB_WH == 64 * 16 * 2 && TB_W5 == 64 * 16 * 2 + 3 * 64 * 64 * 2,
+                "the table kernel's P1..P4 must match the packed image");
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(wimg);
+    uint4* dst = reinterpret_cast<uint4*>(sm + TB_W1);
+#pragma unroll 4
+    for (int k = t; k < TB_W5 / 16; k += NT) dst[k] = src[k];
+  }
   load_operand(sm + TB_W5, wb + BOFF_P5, 16, 64, 8);
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
@@ -966,7 +972,7 @@ cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B
     e = cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), g_table_timeout);
     if (e != cudaSuccess) return e;
     const int grid = B < 2 * sms ? B : 2 * sms;
-    k_table_tc<<<grid, tc::NT, tc::SMEM_BYTES, st>>>(s->wb, s->params, theta, P, B, s->q_lo,
+    k_table_tc<<<grid, tc::NT, tc::SMEM_BYTES, st>>>(s->wb, s->wimg, s->params, theta, P, B, s->q_lo,
                                                      s->q_hi, s->g_lo, s->g_hi, table, flag);
   } else {
     k_table_exact<<<B, TABLE_M, 0, st>>>(theta, P, B, 1.f / 3.f, table);
