@@ -217,6 +217,59 @@ __device__ double row_pullback(const BijDev* __restrict__ bj, int P, const float
   return warp_sum(lj);
 }
 
+// theta(u) of one row like row_to_theta, and the Jacobian terms a later
+// pull-back at the same u needs, in jc[3 k .. 3 k + 2] (FP64, as computed):
+// a scalar map keeps (d theta/du, d log|J|/du); a disc pair keeps (j11, j12,
+// g1) in its first slot and (j22, g2) in its second. Returns log|J|.
+__device__ double row_to_theta_cache(const BijDev* __restrict__ bj, int P,
+                                     const float* __restrict__ u, float* __restrict__ th,
+                                     double* __restrict__ jc) {
+  const int lane = threadIdx.x & 31;
+  double lj = 0.0;
+  for (int k = lane; k < P; k += 32) {
+    const BijDev d = bj[k];
+    if (d.mode == BJ_DISC2) continue;
+    if (d.mode == BJ_DISC) {
+      const Disc q = bij_disc((double)d.rmax, (double)u[k], (double)u[k + 1]);
+      th[k] = (float)q.e1;
+      th[k + 1] = (float)q.e2;
+      jc[3 * k] = q.j11;
+      jc[3 * k + 1] = q.j12;
+      jc[3 * k + 2] = q.g1;
+      jc[3 * k + 3] = q.j22;
+      jc[3 * k + 4] = q.g2;
+      lj += q.logj;
+    } else {
+      const Scal q = bij_scalar(d, (double)u[k]);
+      th[k] = (float)q.th;
+      jc[3 * k] = q.dth;
+      jc[3 * k + 1] = q.dlogj;
+      lj += q.logj;
+    }
+  }
+  return warp_sum(lj);
+}
+
+// The pull-back gu = J^T g + grad log|J| of one row from the terms that
+// row_to_theta_cache stored at the same u (the same arithmetic as
+// row_pullback without evaluating the maps again).
+__device__ void row_pullback_cached(const BijDev* __restrict__ bj, int P,
+                                    const double* __restrict__ jc, const float* __restrict__ g,
+                                    float* gu) {
+  const int lane = threadIdx.x & 31;
+  for (int k = lane; k < P; k += 32) {
+    const BijDev d = bj[k];
+    if (d.mode == BJ_DISC2) continue;
+    if (d.mode == BJ_DISC) {
+      const double g1 = g[k], g2 = g[k + 1];
+      gu[k] = (float)(jc[3 * k] * g1 + jc[3 * k + 1] * g2 + jc[3 * k + 2]);
+      gu[k + 1] = (float)(jc[3 * k + 1] * g1 + jc[3 * k + 3] * g2 + jc[3 * k + 4]);
+    } else {
+      gu[k] = (float)(jc[3 * k] * (double)g[k] + jc[3 * k + 1]);
+    }
+  }
+}
+
 __global__ void k_to_theta(const BijDev* __restrict__ bj, int P, const float* __restrict__ u,
                            int B, float* __restrict__ th, float* __restrict__ logj) {
   const int row = blockIdx.x * RPB + (threadIdx.x >> 5);
@@ -348,6 +401,8 @@ struct HmcBufs {
   float *p, *H0, *prob;
   float *th, *lp_th, *g_th;
   float* inv_mass;
+  double* jc;   // [B][3 P] Jacobian terms of theta(u) at the current u (row_to_theta_cache)
+  double* ljc;  // [B] log|J| at the current u
 };
 
 // Momenta, the trajectory's start, H0, then the first half kick and drift and
@@ -384,7 +439,8 @@ __global__ void k_hmc_begin(const BijDev* __restrict__ bj, int P, int B,
     b.lp0[row] = lp;
     b.H0[row] = (float)(-(double)lp + 0.5 * kin);
   }
-  row_to_theta(bj, P, b.u + o, b.th + o);
+  const double lj = row_to_theta_cache(bj, P, b.u + o, b.th + o, b.jc + 3 * o);
+  if (lane == 0) b.ljc[row] = lj;
 }
 
 // After an evaluation: pull-back, then a full kick and drift (a half kick on
@@ -401,7 +457,9 @@ __global__ void k_hmc_mid(const BijDev* __restrict__ bj, int P, int B,
   bool live = isfinite(lpt);
   double lj = 0.0;
   if (live) {
-    lj = row_pullback(bj, P, b.u + o, b.g_th + o, gsh[w]);
+    // theta was evaluated at the current u, where the terms were cached
+    row_pullback_cached(bj, P, b.jc + 3 * o, b.g_th + o, gsh[w]);
+    lj = b.ljc[row];
     __syncwarp();
   }
   for (int k = lane; k < P; k += 32) {
@@ -416,7 +474,10 @@ __global__ void k_hmc_mid(const BijDev* __restrict__ bj, int P, int B,
   }
   if (lane == 0) b.lp[row] = live ? (float)((double)lpt + lj) : lpt;
   __syncwarp();
-  if (!last && live) row_to_theta(bj, P, b.u + o, b.th + o);
+  if (!last && live) {
+    const double ljn = row_to_theta_cache(bj, P, b.u + o, b.th + o, b.jc + 3 * o);
+    if (lane == 0) b.ljc[row] = ljn;
+  }
 }
 
 // Metropolis-Hastings: accept when log a < min(0, H0 - H1); a rejected chain
@@ -829,6 +890,7 @@ struct gl_hmc {
   uint64_t seed = 0;
   HmcBufs b{};
   float* pool = nullptr;
+  double* jpool = nullptr;  // Jacobian cache: [B][3 P] + [B] doubles
   HmcDev* ctl = nullptr;
   HmcDev* h_ctl = nullptr;  // pinned staging: initial control block, step-size reads
   cudaStream_t cap = nullptr;
@@ -1103,6 +1165,7 @@ gl_status gl_hmc_create(gl_system* sys, const gl_hmc_desc* d, const float* u0, g
   const size_t BP = (size_t)B * P;
   const size_t total = 7 * BP + 6 * (size_t)B + P;
   cudaError_t e = cudaMalloc(&h->pool, total * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&h->jpool, (3 * BP + (size_t)B) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->ctl, sizeof(HmcDev));
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctl, sizeof(HmcDev));
   if (e != cudaSuccess) {
@@ -1124,6 +1187,8 @@ gl_status gl_hmc_create(gl_system* sys, const gl_hmc_desc* d, const float* u0, g
   h->b.lp_th = q; q += B;
   q += B;  // spare
   h->b.inv_mass = q;
+  h->b.jc = h->jpool;
+  h->b.ljc = h->jpool + 3 * BP;
   HmcDev& c = *h->h_ctl;
   std::memset(&c, 0, sizeof c);
   c.eps = d->step_size;
@@ -1265,6 +1330,7 @@ gl_status gl_hmc_destroy(gl_hmc* h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->cap) cudaStreamDestroy(h->cap);
   cudaFree(h->pool);
+  cudaFree(h->jpool);
   cudaFree(h->ctl);
   cudaFreeHost(h->h_ctl);
   delete h;
