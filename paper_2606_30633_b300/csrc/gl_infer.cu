@@ -278,6 +278,18 @@ __global__ void k_to_theta(const BijDev* __restrict__ bj, int P, const float* __
   if (logj && (threadIdx.x & 31) == 0) logj[row] = (float)lj;
 }
 
+// theta(u) with the Jacobian terms for a later pull-back at the same u
+// (jc [B][3 P], ljc [B]; row_to_theta_cache).
+__global__ void k_to_theta_cache(const BijDev* __restrict__ bj, int P, const float* __restrict__ u,
+                                 int B, float* __restrict__ th, double* __restrict__ jc,
+                                 double* __restrict__ ljc) {
+  const int row = blockIdx.x * RPB + (threadIdx.x >> 5);
+  if (row >= B) return;
+  const size_t o = (size_t)row * P;
+  const double lj = row_to_theta_cache(bj, P, u + o, th + o, jc + 3 * o);
+  if ((threadIdx.x & 31) == 0) ljc[row] = lj;
+}
+
 __global__ void k_to_u(const BijDev* __restrict__ bj, int P, const float* __restrict__ th, int B,
                        float* __restrict__ u) {
   const int row = blockIdx.x * RPB + (threadIdx.x >> 5), lane = threadIdx.x & 31;
@@ -350,7 +362,8 @@ __global__ void k_map_update(const BijDev* __restrict__ bj, int P, int B, float*
                              float* __restrict__ m, float* __restrict__ v,
                              const float* __restrict__ lp_th, const float* __restrict__ g_th,
                              float* __restrict__ logp, const MapCtl* __restrict__ ctl, int step,
-                             float* __restrict__ th_next) {
+                             float* __restrict__ th_next, double* __restrict__ jc,
+                             double* __restrict__ ljc) {
   __shared__ float gsh[RPB][gl::MAX_P];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * RPB + w;
@@ -358,7 +371,9 @@ __global__ void k_map_update(const BijDev* __restrict__ bj, int P, int B, float*
   const size_t o = (size_t)row * P;
   const float lp = lp_th[row];
   if (isfinite(lp)) {
-    const double lj = row_pullback(bj, P, u + o, g_th + o, gsh[w]);
+    // theta was evaluated at the current u, where its Jacobian terms were cached
+    row_pullback_cached(bj, P, jc + 3 * o, g_th + o, gsh[w]);
+    const double lj = ljc[row];
     __syncwarp();
     if (lane == 0) logp[row] = (float)((double)lp + lj);
     const MapCtl c = *ctl;
@@ -376,7 +391,8 @@ __global__ void k_map_update(const BijDev* __restrict__ bj, int P, int B, float*
   } else if (lane == 0) {
     logp[row] = lp;
   }
-  row_to_theta(bj, P, u + o, th_next + o);
+  const double ljn = row_to_theta_cache(bj, P, u + o, th_next + o, jc + 3 * o);
+  if (lane == 0) ljc[row] = ljn;
 }
 
 // ------------------------------------------------------------------ HMC ----
@@ -915,6 +931,7 @@ struct InferState {
   } map_key{};
   float* map_buf = nullptr;  // theta, logp, grad [B(2P + 1)]
   size_t map_buf_floats = 0;
+  double* map_jc = nullptr;  // Jacobian terms of theta(u) [B][3 P], then log|J| [B]
   MapCtl* map_ctl = nullptr;
   // SVI
   cudaGraphExec_t svi_exec = nullptr;
@@ -943,6 +960,7 @@ void infer_release(gl_system* s) {
   if (f->cap) cudaStreamDestroy(f->cap);
   cudaFree(f->bij);
   cudaFree(f->map_buf);
+  cudaFree(f->map_jc);
   cudaFree(f->map_ctl);
   cudaFree(f->svi_buf);
   cudaFree(f->svi_sums);
@@ -1036,9 +1054,12 @@ gl_status gl_logp_grad_unconstrained(gl_system* sys, const float* u, int B, floa
       f->map_exec = nullptr;
     }
     cudaFree(f->map_buf);
+    cudaFree(f->map_jc);
     f->map_buf = nullptr;
+    f->map_jc = nullptr;
     f->map_buf_floats = 0;
     GI_CUDA(cudaMalloc(&f->map_buf, need * sizeof(float)), "buffer allocation");
+    GI_CUDA(cudaMalloc(&f->map_jc, (size_t)B * (3 * P + 1) * sizeof(double)), "buffer allocation");
     f->map_buf_floats = need;
   }
   float* th = f->map_buf;
@@ -1079,9 +1100,12 @@ gl_status gl_map_adam(gl_system* sys, float* u, float* m, float* v, int B, int n
       f->map_exec = nullptr;
     }
     cudaFree(f->map_buf);
+    cudaFree(f->map_jc);
     f->map_buf = nullptr;
+    f->map_jc = nullptr;
     f->map_buf_floats = 0;
     GI_CUDA(cudaMalloc(&f->map_buf, need * sizeof(float)), "buffer allocation");
+    GI_CUDA(cudaMalloc(&f->map_jc, (size_t)B * (3 * P + 1) * sizeof(double)), "buffer allocation");
     f->map_buf_floats = need;
   }
   if (!f->map_ctl) GI_CUDA(cudaMalloc(&f->map_ctl, sizeof(MapCtl)), "control allocation");
@@ -1107,13 +1131,15 @@ gl_status gl_map_adam(gl_system* sys, float* u, float* m, float* v, int B, int n
     if (!f->cap) GI_CUDA(cudaStreamCreateWithFlags(&f->cap, cudaStreamNonBlocking), "stream");
     GI_CUDA(cudaStreamBeginCapture(f->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t e = cudaSuccess;
-    k_to_theta<<<grid_rows(B), 256, 0, f->cap>>>(f->bij, P, u, B, th, nullptr);
+    double* jc = f->map_jc;
+    double* ljc = jc + (size_t)B * 3 * P;
+    k_to_theta_cache<<<grid_rows(B), 256, 0, f->cap>>>(f->bij, P, u, B, th, jc, ljc);
     e = cudaGetLastError();
     for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
       e = gl::eval_launch(sys, sp, dyn, th, B, lpth, gth, defl, f->cap);
       if (e != cudaSuccess) break;
       k_map_update<<<grid_rows(B), 256, 0, f->cap>>>(f->bij, P, B, u, m, v, lpth, gth, logp,
-                                                     f->map_ctl, k, th);
+                                                     f->map_ctl, k, th, jc, ljc);
       e = cudaGetLastError();
     }
     cudaGraph_t g = nullptr;
