@@ -635,39 +635,61 @@ __global__ void k_svi_draw(const BijDev* __restrict__ bj, int P, int n,
                            float* __restrict__ u, float* __restrict__ th,
                            float* __restrict__ logj) {
   __shared__ float zs[RPB][gl::MAX_P];
+  __shared__ double Ls[gl::MAX_P][gl::MAX_P];   // L (strict lower part used)
+  __shared__ double Li[gl::MAX_P][gl::MAX_P];   // L^{-1} (lower triangular)
+  __shared__ double dg[gl::MAX_P];               // exp(log L_kk)
+  __shared__ double ldsum;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * RPB + w;
-  if (i >= n) return;
   const float* mu = phi;
   const float* L = phi + P;  // row-major, diagonal stored as log
+  // L is the same for every sample: stage it, its diagonal and its inverse
+  // once per block (warp 0 solves L x = e_c for column c in lane c by forward
+  // substitution), then each warp's sample needs only products with them.
+  for (int k = threadIdx.x; k < P * P; k += blockDim.x) Ls[k / P][k % P] = (double)L[k];
+  __syncthreads();
+  if (w == 0) {
+    double ld = 0.0;
+    for (int k = lane; k < P; k += 32) {
+      dg[k] = exp(Ls[k][k]);
+      ld += Ls[k][k];
+    }
+    ld = warp_sum(ld);
+    if (lane == 0) ldsum = ld;
+    __syncwarp();
+    for (int c = lane; c < P; c += 32) {
+      for (int i = 0; i < c; ++i) Li[i][c] = 0.0;
+      for (int i = c; i < P; ++i) {
+        double s = i == c ? 1.0 : 0.0;
+        for (int j = c; j < i; ++j) s -= Ls[i][j] * Li[j][c];
+        Li[i][c] = s / dg[i];
+      }
+    }
+  }
+  __syncthreads();
+  const int i = blockIdx.x * RPB + w;
+  if (i >= n) return;
   const size_t o = (size_t)i * P;
   const uint64_t base = (ctl->step * (uint64_t)n + (uint64_t)i) * (uint64_t)(2 * P);
-  double zz = 0.0, ld = 0.0;
+  double zz = 0.0;
   for (int k = lane; k < P; k += 32) {
     const float zk = normal_bm(seed, base + 2 * k);
     zs[w][k] = zk;
     z[o + k] = zk;
     zz += (double)zk * zk;
-    ld += (double)L[k * P + k];
   }
   __syncwarp();
   zz = warp_sum(zz);
-  ld = warp_sum(ld);
   for (int k = lane; k < P; k += 32) {
+    // u = mu + L z, and a = L^{-T} z (the score of log q w.r.t. mu)
     double s = mu[k];
-    for (int j = 0; j < k; ++j) s += (double)L[k * P + j] * zs[w][j];
-    s += exp((double)L[k * P + k]) * zs[w][k];
+    for (int j = 0; j < k; ++j) s += Ls[k][j] * zs[w][j];
+    s += dg[k] * zs[w][k];
     u[o + k] = (float)s;
+    double t = 0.0;
+    for (int j = k; j < P; ++j) t += Li[j][k] * zs[w][j];
+    a[o + k] = (float)t;
   }
-  if (lane == 0) {
-    // L^T a = z by back substitution
-    for (int k = P - 1; k >= 0; --k) {
-      double s = zs[w][k];
-      for (int j = k + 1; j < P; ++j) s -= (double)L[j * P + k] * a[o + j];
-      a[o + k] = (float)(s / exp((double)L[k * P + k]));
-    }
-    logq[i] = (float)(-0.5 * zz - ld - 0.5 * P * LOG_2PI);
-  }
+  if (lane == 0) logq[i] = (float)(-0.5 * zz - ldsum - 0.5 * P * LOG_2PI);
   __syncwarp();
   const double lj = row_to_theta(bj, P, u + o, th + o);
   if (lane == 0) logj[i] = (float)lj;
