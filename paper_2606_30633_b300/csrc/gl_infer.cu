@@ -812,26 +812,38 @@ __global__ void k_bwd_solve(const float* __restrict__ img, const float* __restri
   __shared__ double red[8][NS];
   const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, wp = t >> 5;
   constexpr int nA = K * (K + 1) / 2, ns = NS;
-  double acc[NS];
+  // Per-thread sums of the products in FP32 with Kahan compensation (the FP64
+  // pipe of this GPU is too slow for ~5 FP64 products per pixel and row); the
+  // cross-thread reduction and the solve are FP64.
+  float acc[NS], cmp[NS];
 #pragma unroll
-  for (int q = 0; q < NS; ++q) acc[q] = 0.0;
+  for (int q = 0; q < NS; ++q) acc[q] = cmp[q] = 0.f;
+  auto kahan = [&](int q, float x) {
+    const float y = x - cmp[q];
+    const float tt = acc[q] + y;
+    cmp[q] = (tt - acc[q]) - y;
+    acc[q] = tt;
+  };
   const float* M = img + (size_t)b * K * npix;
   for (int p = t; p < npix; p += blockDim.x) {
-    const double wp_ = w[p], dp = data[p];
-    double m[K];
+    const float wp_ = w[p], dp = data[p];
+    float m[K], wm[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) m[k] = M[(size_t)k * npix + p];
+    for (int k = 0; k < K; ++k) {
+      m[k] = M[(size_t)k * npix + p];
+      wm[k] = wp_ * m[k];
+    }
     int q = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int l = 0; l <= k; ++l) acc[q++] += wp_ * m[k] * m[l];
+      for (int l = 0; l <= k; ++l) kahan(q++, wm[k] * m[l]);
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[nA + k] += wp_ * m[k] * dp;
+    for (int k = 0; k < K; ++k) kahan(nA + k, wm[k] * dp);
   }
 #pragma unroll
   for (int q = 0; q < ns; ++q) {
-    double v = acc[q];
+    double v = (double)acc[q] - (double)cmp[q];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[wp][q] = v;
   }
