@@ -21,6 +21,15 @@ cudaError_t launch_forward(const SysParams& sp, const float* theta, int B, float
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_component_images(const SysParams& sp, const float* theta, int B, float* img,
+                                    size_t dyn, cudaStream_t st) {
+  if (sp.table)
+    k_component_images<true><<<B, THREADS, dyn, st>>>(sp, theta, B, img);
+  else
+    k_component_images<false><<<B, THREADS, dyn, st>>>(sp, theta, B, img);
+  return cudaGetLastError();
+}
+
 size_t static_smem_bytes(bool multi) {
   // SmemStatic + the table (+ k_grad_multi's work index and parameter
   // block), with alignment slack
@@ -38,6 +47,12 @@ cudaError_t set_smem_limits_fwd(size_t block_max) {
   GL_SET(1, 1) GL_SET(1, 2) GL_SET(1, 3)
   GL_SET(2, 1) GL_SET(2, 2) GL_SET(2, 3)
 #undef GL_SET
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_component_images<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_component_images<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
   return e;
 }
 

@@ -799,7 +799,8 @@ __global__ void k_bwd_rows(const float* __restrict__ th, int B, int P, int K,
   rows[i] = v;
 }
 
-// One block per row: A = M^T W M and r = M^T W d over the pixels (FP64),
+// One block per row: A = M^T W M and r = M^T W d over the pixels (compensated
+// FP32 per thread, FP64 across threads),
 // then A I = r by Cholesky on thread 0; theta* = theta with I. A solve that
 // fails (a component with no light in the image) sets every intensity to 0.
 template <int K>
@@ -1539,7 +1540,7 @@ gl_status gl_logp_grad_backward(gl_system* sys, const float* theta, int B, float
     GI_CUDA(gl::launch_table(defl == GL_DEFL_TABLE ? nullptr : sys->sur, rows, P, B * K,
                              const_cast<float4*>(sf.table), st),
             "table launch");
-  GI_CUDA(gl::launch_forward(sf, rows, B * K, nullptr, imgs, df, st), "image launch");
+  GI_CUDA(gl::launch_component_images(sf, rows, B * K, imgs, df, st), "image launch");
   switch (K) {
 #define GL_BWD(k)                                                                          \
   case k:                                                                                  \

@@ -79,6 +79,9 @@ struct MultiItem {
 // sp.table != nullptr selects the surrogate instantiations.
 cudaError_t launch_forward(const SysParams& sp, const float* theta, int B, float* logp,
                            float* img, size_t dyn_smem, cudaStream_t st);
+// Images of single light components (k_component_images): one row per image.
+cudaError_t launch_component_images(const SysParams& sp, const float* theta, int B, float* img,
+                                    size_t dyn, cudaStream_t st);
 cudaError_t launch_grad(const SysParams& sp, const float* theta, int B, float* logp, float* grad,
                         size_t dyn_smem, cudaStream_t st);
 cudaError_t launch_leapfrog_block(const SysParams& sp, size_t dyn, float* theta, float* p,

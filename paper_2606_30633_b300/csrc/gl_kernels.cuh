@@ -232,6 +232,71 @@ __device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& s
   }
 }
 
+// Phase 1 for the image of one light component c (a source when source is
+// set): the loop of bin_pixels with only that component evaluated.
+template <bool TAB>
+__device__ __forceinline__ void bin_component(const SysParams& sp, const SampleC& sc,
+                                              const float4* tab, float* A, int c, bool source) {
+  const int s = sp.s, npix = sp.ny * sp.nx, Wp = sp.Wp, cy = sp.cy, cx = sp.cx;
+  const float2 D = f2(sp.D), scale = f2(sp.scale);
+  PixelWalk w0(sp.nx);
+  int p = threadIdx.x;
+  for (; p + 3 * THREADS < npix; p += 4 * THREADS) {
+    PixelWalk w1 = w0;
+    w1.next();
+    PixelWalk w2 = w1;
+    w2.next();
+    PixelWalk w3 = w2;
+    w3.next();
+    const float2 xj0 = make_float2((float)w0.j + sp.xg0, (float)w1.j + sp.xg0);
+    const float2 yi0 = make_float2((float)w0.i + sp.yg0, (float)w1.i + sp.yg0);
+    const float2 xj1 = make_float2((float)w2.j + sp.xg0, (float)w3.j + sp.xg0);
+    const float2 yi1 = make_float2((float)w2.i + sp.yg0, (float)w3.i + sp.yg0);
+    float2 acc0 = f2(0.f), acc1 = f2(0.f);
+    for (int k = 0; k < s; ++k) {
+      const float2 ok = f2(sp.off[k]);
+      const float2 y0 = mul2(add2(yi0, ok), D), y1 = mul2(add2(yi1, ok), D);
+      for (int l = 0; l < s; ++l) {
+        const float2 ol = f2(sp.off[l]);
+        const float2 x0 = mul2(add2(xj0, ol), D), x1 = mul2(add2(xj1, ol), D);
+        float2 sb0, sb1;
+        component_brightness4<TAB>(reload(sc), tab, c, source, x0, y0, x1, y1, sb0, sb1);
+        acc0 = add2(acc0, sb0);
+        acc1 = add2(acc1, sb1);
+      }
+    }
+    acc0 = mul2(acc0, scale);
+    acc1 = mul2(acc1, scale);
+    A[(size_t)(w0.i + cy) * Wp + w0.j + cx] = acc0.x;
+    A[(size_t)(w1.i + cy) * Wp + w1.j + cx] = acc0.y;
+    A[(size_t)(w2.i + cy) * Wp + w2.j + cx] = acc1.x;
+    A[(size_t)(w3.i + cy) * Wp + w3.j + cx] = acc1.y;
+    w0 = w3;
+    w0.next();
+  }
+  for (; p < npix; p += 2 * THREADS) {
+    PixelWalk w1 = w0;
+    w1.next();
+    const bool v1 = p + THREADS < npix;
+    const int i1 = v1 ? w1.i : w0.i, j1 = v1 ? w1.j : w0.j;
+    const float2 xj = make_float2((float)w0.j + sp.xg0, (float)j1 + sp.xg0);
+    const float2 yi = make_float2((float)w0.i + sp.yg0, (float)i1 + sp.yg0);
+    float2 acc = f2(0.f);
+    for (int k = 0; k < s; ++k) {
+      const float2 y = mul2(add2(yi, f2(sp.off[k])), D);
+      for (int l = 0; l < s; ++l) {
+        const float2 x = mul2(add2(xj, f2(sp.off[l])), D);
+        acc = add2(acc, component_brightness2<TAB>(reload(sc), tab, c, source, x, y));
+      }
+    }
+    acc = mul2(acc, scale);
+    A[(size_t)(w0.i + cy) * Wp + w0.j + cx] = acc.x;
+    if (v1) A[(size_t)(w1.i + cy) * Wp + w1.j + cx] = acc.y;
+    w0 = w1;
+    w0.next();
+  }
+}
+
 // Phase 4: sub-pixel adjoint over pixel pairs (p, p + T) in float2 lanes (a
 // missing second pixel repeats the first with u = 0). Per-lane FP32 sums are
 // flushed into the per-warp sums redP every FLUSH_IT pairs, which bounds the
@@ -371,6 +436,49 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
   if (want_img) return;
   const double chi2 = block_sum_double((double)csum - (double)ccomp, st.red);
   if (threadIdx.x == 0) logp[b] = (float)(-0.5 * chi2 + sc.logprior);
+}
+
+// Model images of single light components (the linear intensity solve):
+// each row has one component with non-zero intensity, and only that one is
+// evaluated (a lens-light row needs no deflection). A row with none gives a
+// zero image; a row outside the model domain or with a NaN gives NaN.
+template <bool SURR>
+__global__ void __launch_bounds__(THREADS, 2)
+k_component_images(const __grid_constant__ SysParams sp, const float* __restrict__ theta, int B,
+                   float* __restrict__ img) {
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ SmemStatic st;
+  __shared__ float4 tab[SURR ? TABLE_ROW : 1];
+  SampleC& sc = st.sc;
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  float *A, *Bf;
+  buffers(sp, dsm, false, A, Bf, blockIdx.x);
+  if (threadIdx.x < 32)
+    stage_warp(sp, theta + (size_t)b * sp.P, sc, st.fin, false);
+  else
+    zero_halo(sp, A, 32);
+  __syncthreads();
+  const int npix = sp.ny * sp.nx;
+  float* out = img + (size_t)b * npix;
+  if (sc.status != 0) {
+    for (int p = threadIdx.x; p < npix; p += THREADS) out[p] = __int_as_float(0x7fc00000);
+    return;
+  }
+  int c = 0;
+  for (int k = 0; k < sp.nL + sp.nS; ++k)
+    if (sc.light[k].Ip.x != 0.f) {
+      c = k;
+      break;
+    }
+  const bool source = c >= sp.nL;
+  load_table<SURR>(sp.table + (size_t)blockIdx.x * TABLE_ROW, sc, tab);
+  if (SURR && sc.use_table && source)
+    bin_component<true>(sp, sc, tab, A, c, source);
+  else
+    bin_component<false>(sp, sc, tab, A, c, source);
+  __syncthreads();
+  correlate<true>(sp, A, [&](int i, int j, float m) { out[i * sp.nx + j] = m; });
 }
 
 // Forward + adjoint of one row (all threads of the CTA): log p and

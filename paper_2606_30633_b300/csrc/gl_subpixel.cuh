@@ -271,6 +271,51 @@ __device__ __forceinline__ void surface_brightness4(const SampleC& sc, const flo
   sb1 = light_sum2<NL, NS>(sc, x1, y1, bx, by);
 }
 
+// One light component at four points (two pairs): a lens-light component on
+// the image plane, a source component at the lensed position (the only
+// case that needs the deflection).
+template <bool TAB>
+__device__ __forceinline__ void component_brightness4(const SampleC& sc, const float4* tab, int c,
+                                                      bool source, float2 x0, float2 y0, float2 x1,
+                                                      float2 y1, float2& sb0, float2& sb1) {
+  const LightP& L = sc.light[c];
+  if (!source) {
+    sb0 = sersic_fwd2(L, x0, y0);
+    sb1 = sersic_fwd2(L, x1, y1);
+    return;
+  }
+  const Geo2 g0 = epl_geometry2(sc.epl, x0, y0);
+  const Geo2 g1 = epl_geometry2(sc.epl, x1, y1);
+  float2 Fr0, Fi0, Fr1, Fi1;
+  if (TAB) {
+    deflection_F<true>(sc, tab, g0, Fr0, Fi0);
+    deflection_F<true>(sc, tab, g1, Fr1, Fi1);
+  } else {
+    Clen2 s0, s1;
+    clenshaw2(sc.cE, sc.n2, g0, g1, s0, s1);
+    series_F(sc.epl, g0, s0, Fr0, Fi0);
+    series_F(sc.epl, g1, s1, Fr1, Fi1);
+  }
+  float2 bx, by;
+  lens_equation2(sc, g0, x0, y0, Fr0, Fi0, bx, by);
+  sb0 = sersic_fwd2(L, bx, by);
+  lens_equation2(sc, g1, x1, y1, Fr1, Fi1, bx, by);
+  sb1 = sersic_fwd2(L, bx, by);
+}
+
+// The same at two points.
+template <bool TAB>
+__device__ __forceinline__ float2 component_brightness2(const SampleC& sc, const float4* tab, int c,
+                                                        bool source, float2 x, float2 y) {
+  const LightP& L = sc.light[c];
+  if (!source) return sersic_fwd2(L, x, y);
+  const Geo2 g = epl_geometry2(sc.epl, x, y);
+  float2 Fr, Fi, bx, by;
+  deflection_F<TAB>(sc, tab, g, Fr, Fi);
+  lens_equation2(sc, g, x, y, Fr, Fi, bx, by);
+  return sersic_fwd2(L, bx, by);
+}
+
 // ------------------------------------------------------ adjoint pieces ----
 // Per-thread adjoint sums: a float2 (one sum per lane, added at the flush)
 // where the registers allow, else a float that takes both lanes at once.

@@ -53,3 +53,21 @@ def test_backward_matches_oracle(torch, case):
     bound[:, idx] = 0.0
     err = np.abs(g - g_o)
     assert np.all(err <= bound), float(np.max(err / np.where(bound > 0, bound, 1)))
+
+
+def test_backward_with_tables_follows_the_series(torch, case):
+    """The same solve with the exact series tabulated per row (GL_DEFL_TABLE):
+    the component images of source rows read the tables, lens-light rows need
+    no deflection; intensities and log p follow the series path to the tables'
+    interpolation error."""
+    import paper_2606_30633_b300 as gl
+    W = case.W
+    s = case.gpu_system()
+    th = f32(synth.jitter(case.truth, W.prior(), 6, 5, rel=0.003))
+    th[0] = case.truth
+    t = torch.tensor(th, dtype=torch.float32, device="cuda")
+    lps, _, Is = s.logp_grad_backward(t)
+    lpt, _, It = s.logp_grad_backward(t, defl=gl.GL_DEFL_TABLE)
+    lps, Is, lpt, It = lps.cpu().numpy(), Is.cpu().numpy(), lpt.cpu().numpy(), It.cpu().numpy()
+    assert np.all(np.abs(It - Is) <= 1e-4 * np.abs(Is) + 1e-6), np.abs((It - Is) / Is).max()
+    assert np.all(np.abs(lpt - lps) <= 2e-6 * np.abs(lps) + 2e-3), np.abs(lpt - lps).max()
