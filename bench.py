@@ -169,6 +169,16 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- arms ----
+def host_cores() -> int:
+    """The host cores this process may run on: the oracle's thread count is
+    set from them explicitly, since launchers such as torchrun set
+    OMP_NUM_THREADS=1 for every rank."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -203,7 +213,7 @@ def run_reference(args) -> dict | None:
         return None
     W = synth.ground_100()
     spec = W.prior()
-    cores = oracle.max_threads()
+    cores = host_cores()
     S0 = oracle.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
                        np.ones((W.ny, W.nx)), W.psf, 1, 1, spec)
     m = S0.model_image(W.truth())[0]
@@ -315,7 +325,7 @@ def cpu_baseline_leg(budget_s: float = 12.0) -> dict:
     import oracle
     W = synth.ground_100()
     spec = W.prior()
-    cores = oracle.max_threads()
+    cores = host_cores()
     S0 = oracle.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
                        np.ones((W.ny, W.nx)), W.psf, 1, 1, spec)
     m = S0.model_image(W.truth())[0]
