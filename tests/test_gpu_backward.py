@@ -1,6 +1,7 @@
 """GPU parity of backward intensity modelling (gl_logp_grad_backward)
 against the FP64 oracle (oracle/backward.py): solved intensities, profile
-log p and the envelope-theorem gradient, near the mode and at prior draws."""
+log p and the envelope-theorem gradient, near the mode and at prior draws, for
+no lens light, one or two sources, and the most components (2 + 3)."""
 import numpy as np
 import pytest
 
@@ -19,7 +20,7 @@ def torch():
     return torch
 
 
-@pytest.fixture(scope="module", params=[(1, 1), (1, 2)])
+@pytest.fixture(scope="module", params=[(1, 1), (1, 2), (0, 1), (2, 3)])
 def case(request):
     nl, ns = request.param
     return make_case(small_workload(40, 40, 2, 11, nl, ns, seed=1401 + ns))
