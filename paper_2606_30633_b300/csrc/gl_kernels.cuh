@@ -169,9 +169,10 @@ __device__ __forceinline__ void buffers(const SysParams& sp, float* dsm, bool tw
 // Pixels go in the lanes of float2 pairs: four pixels per thread (p, p + T,
 // p + 2T, p + 3T; two interleaved pairs) while all four exist, then pairs,
 // where a missing second pixel repeats the first and is not written.
-template <int NL, int NS, bool TAB>
-__device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& sc,
-                                           const float4* tab, float* A) {
+// eval4(x0, y0, x1, y1, sb0, sb1) and eval2(x, y) give the brightness at two
+// pairs and at one pair of sub-pixel centres.
+template <class Eval4, class Eval2>
+__device__ __forceinline__ void bin_loop(const SysParams& sp, float* A, Eval4 eval4, Eval2 eval2) {
   const int s = sp.s, npix = sp.ny * sp.nx, Wp = sp.Wp, cy = sp.cy, cx = sp.cx;
   const float2 D = f2(sp.D), scale = f2(sp.scale);
   PixelWalk w0(sp.nx);
@@ -195,7 +196,7 @@ __device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& s
         const float2 ol = f2(sp.off[l]);
         const float2 x0 = mul2(add2(xj0, ol), D), x1 = mul2(add2(xj1, ol), D);
         float2 sb0, sb1;
-        surface_brightness4<NL, NS, TAB>(reload(sc), tab, x0, y0, x1, y1, sb0, sb1);
+        eval4(x0, y0, x1, y1, sb0, sb1);
         acc0 = add2(acc0, sb0);
         acc1 = add2(acc1, sb1);
       }
@@ -221,7 +222,7 @@ __device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& s
       const float2 y = mul2(add2(yi, f2(sp.off[k])), D);
       for (int l = 0; l < s; ++l) {
         const float2 x = mul2(add2(xj, f2(sp.off[l])), D);
-        acc = add2(acc, surface_brightness2<NL, NS, TAB>(reload(sc), tab, x, y));
+        acc = add2(acc, eval2(x, y));
       }
     }
     acc = mul2(acc, scale);
@@ -232,69 +233,30 @@ __device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& s
   }
 }
 
+template <int NL, int NS, bool TAB>
+__device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& sc,
+                                           const float4* tab, float* A) {
+  bin_loop(
+      sp, A,
+      [&](float2 x0, float2 y0, float2 x1, float2 y1, float2& sb0, float2& sb1) {
+        surface_brightness4<NL, NS, TAB>(reload(sc), tab, x0, y0, x1, y1, sb0, sb1);
+      },
+      [&](float2 x, float2 y) { return surface_brightness2<NL, NS, TAB>(reload(sc), tab, x, y); });
+}
+
 // Phase 1 for the image of one light component c (a source when source is
-// set): the loop of bin_pixels with only that component evaluated.
+// set): the same walk with only that component evaluated.
 template <bool TAB>
 __device__ __forceinline__ void bin_component(const SysParams& sp, const SampleC& sc,
                                               const float4* tab, float* A, int c, bool source) {
-  const int s = sp.s, npix = sp.ny * sp.nx, Wp = sp.Wp, cy = sp.cy, cx = sp.cx;
-  const float2 D = f2(sp.D), scale = f2(sp.scale);
-  PixelWalk w0(sp.nx);
-  int p = threadIdx.x;
-  for (; p + 3 * THREADS < npix; p += 4 * THREADS) {
-    PixelWalk w1 = w0;
-    w1.next();
-    PixelWalk w2 = w1;
-    w2.next();
-    PixelWalk w3 = w2;
-    w3.next();
-    const float2 xj0 = make_float2((float)w0.j + sp.xg0, (float)w1.j + sp.xg0);
-    const float2 yi0 = make_float2((float)w0.i + sp.yg0, (float)w1.i + sp.yg0);
-    const float2 xj1 = make_float2((float)w2.j + sp.xg0, (float)w3.j + sp.xg0);
-    const float2 yi1 = make_float2((float)w2.i + sp.yg0, (float)w3.i + sp.yg0);
-    float2 acc0 = f2(0.f), acc1 = f2(0.f);
-    for (int k = 0; k < s; ++k) {
-      const float2 ok = f2(sp.off[k]);
-      const float2 y0 = mul2(add2(yi0, ok), D), y1 = mul2(add2(yi1, ok), D);
-      for (int l = 0; l < s; ++l) {
-        const float2 ol = f2(sp.off[l]);
-        const float2 x0 = mul2(add2(xj0, ol), D), x1 = mul2(add2(xj1, ol), D);
-        float2 sb0, sb1;
+  bin_loop(
+      sp, A,
+      [&](float2 x0, float2 y0, float2 x1, float2 y1, float2& sb0, float2& sb1) {
         component_brightness4<TAB>(reload(sc), tab, c, source, x0, y0, x1, y1, sb0, sb1);
-        acc0 = add2(acc0, sb0);
-        acc1 = add2(acc1, sb1);
-      }
-    }
-    acc0 = mul2(acc0, scale);
-    acc1 = mul2(acc1, scale);
-    A[(size_t)(w0.i + cy) * Wp + w0.j + cx] = acc0.x;
-    A[(size_t)(w1.i + cy) * Wp + w1.j + cx] = acc0.y;
-    A[(size_t)(w2.i + cy) * Wp + w2.j + cx] = acc1.x;
-    A[(size_t)(w3.i + cy) * Wp + w3.j + cx] = acc1.y;
-    w0 = w3;
-    w0.next();
-  }
-  for (; p < npix; p += 2 * THREADS) {
-    PixelWalk w1 = w0;
-    w1.next();
-    const bool v1 = p + THREADS < npix;
-    const int i1 = v1 ? w1.i : w0.i, j1 = v1 ? w1.j : w0.j;
-    const float2 xj = make_float2((float)w0.j + sp.xg0, (float)j1 + sp.xg0);
-    const float2 yi = make_float2((float)w0.i + sp.yg0, (float)i1 + sp.yg0);
-    float2 acc = f2(0.f);
-    for (int k = 0; k < s; ++k) {
-      const float2 y = mul2(add2(yi, f2(sp.off[k])), D);
-      for (int l = 0; l < s; ++l) {
-        const float2 x = mul2(add2(xj, f2(sp.off[l])), D);
-        acc = add2(acc, component_brightness2<TAB>(reload(sc), tab, c, source, x, y));
-      }
-    }
-    acc = mul2(acc, scale);
-    A[(size_t)(w0.i + cy) * Wp + w0.j + cx] = acc.x;
-    if (v1) A[(size_t)(w1.i + cy) * Wp + w1.j + cx] = acc.y;
-    w0 = w1;
-    w0.next();
-  }
+      },
+      [&](float2 x, float2 y) {
+        return component_brightness2<TAB>(reload(sc), tab, c, source, x, y);
+      });
 }
 
 // Phase 4: sub-pixel adjoint over pixel pairs (p, p + T) in float2 lanes (a
