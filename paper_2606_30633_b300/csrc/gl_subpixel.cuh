@@ -236,22 +236,23 @@ __device__ __forceinline__ void deflection_F(const SampleC& sc, const float4* ta
   }
 }
 
-// Surface brightness at two points.
-template <int NL, int NS, bool TAB>
-__device__ __forceinline__ float2 surface_brightness2(const SampleC& sc, const float4* tab, float2 x,
-                                                      float2 y) {
+// Brightness at two points whose light light(x, y, bx, by) depends on the
+// image-plane position (x, y) and the lensed position (bx, by).
+template <bool TAB, class Light>
+__device__ __forceinline__ float2 lensed_brightness2(const SampleC& sc, const float4* tab, float2 x,
+                                                     float2 y, Light light) {
   const Geo2 g = epl_geometry2(sc.epl, x, y);
   float2 Fr, Fi, bx, by;
   deflection_F<TAB>(sc, tab, g, Fr, Fi);
   lens_equation2(sc, g, x, y, Fr, Fi, bx, by);
-  return light_sum2<NL, NS>(sc, x, y, bx, by);
+  return light(x, y, bx, by);
 }
 
-// Surface brightness at four points (two pairs; the series sums interleaved).
-template <int NL, int NS, bool TAB>
-__device__ __forceinline__ void surface_brightness4(const SampleC& sc, const float4* tab, float2 x0,
-                                                    float2 y0, float2 x1, float2 y1, float2& sb0,
-                                                    float2& sb1) {
+// The same at four points (two pairs; the series sums interleaved).
+template <bool TAB, class Light>
+__device__ __forceinline__ void lensed_brightness4(const SampleC& sc, const float4* tab, float2 x0,
+                                                   float2 y0, float2 x1, float2 y1, float2& sb0,
+                                                   float2& sb1, Light light) {
   const Geo2 g0 = epl_geometry2(sc.epl, x0, y0);
   const Geo2 g1 = epl_geometry2(sc.epl, x1, y1);
   float2 Fr0, Fi0, Fr1, Fi1;
@@ -266,9 +267,29 @@ __device__ __forceinline__ void surface_brightness4(const SampleC& sc, const flo
   }
   float2 bx, by;
   lens_equation2(sc, g0, x0, y0, Fr0, Fi0, bx, by);
-  sb0 = light_sum2<NL, NS>(sc, x0, y0, bx, by);
+  sb0 = light(x0, y0, bx, by);
   lens_equation2(sc, g1, x1, y1, Fr1, Fi1, bx, by);
-  sb1 = light_sum2<NL, NS>(sc, x1, y1, bx, by);
+  sb1 = light(x1, y1, bx, by);
+}
+
+// Surface brightness (lens light and sources) at two points.
+template <int NL, int NS, bool TAB>
+__device__ __forceinline__ float2 surface_brightness2(const SampleC& sc, const float4* tab, float2 x,
+                                                      float2 y) {
+  return lensed_brightness2<TAB>(sc, tab, x, y, [&](float2 px, float2 py, float2 bx, float2 by) {
+    return light_sum2<NL, NS>(sc, px, py, bx, by);
+  });
+}
+
+// The same at four points.
+template <int NL, int NS, bool TAB>
+__device__ __forceinline__ void surface_brightness4(const SampleC& sc, const float4* tab, float2 x0,
+                                                    float2 y0, float2 x1, float2 y1, float2& sb0,
+                                                    float2& sb1) {
+  lensed_brightness4<TAB>(sc, tab, x0, y0, x1, y1, sb0, sb1,
+                          [&](float2 px, float2 py, float2 bx, float2 by) {
+                            return light_sum2<NL, NS>(sc, px, py, bx, by);
+                          });
 }
 
 // One light component at four points (two pairs): a lens-light component on
@@ -284,23 +305,8 @@ __device__ __forceinline__ void component_brightness4(const SampleC& sc, const f
     sb1 = sersic_fwd2(L, x1, y1);
     return;
   }
-  const Geo2 g0 = epl_geometry2(sc.epl, x0, y0);
-  const Geo2 g1 = epl_geometry2(sc.epl, x1, y1);
-  float2 Fr0, Fi0, Fr1, Fi1;
-  if (TAB) {
-    deflection_F<true>(sc, tab, g0, Fr0, Fi0);
-    deflection_F<true>(sc, tab, g1, Fr1, Fi1);
-  } else {
-    Clen2 s0, s1;
-    clenshaw2(sc.cE, sc.n2, g0, g1, s0, s1);
-    series_F(sc.epl, g0, s0, Fr0, Fi0);
-    series_F(sc.epl, g1, s1, Fr1, Fi1);
-  }
-  float2 bx, by;
-  lens_equation2(sc, g0, x0, y0, Fr0, Fi0, bx, by);
-  sb0 = sersic_fwd2(L, bx, by);
-  lens_equation2(sc, g1, x1, y1, Fr1, Fi1, bx, by);
-  sb1 = sersic_fwd2(L, bx, by);
+  lensed_brightness4<TAB>(sc, tab, x0, y0, x1, y1, sb0, sb1,
+                          [&](float2, float2, float2 bx, float2 by) { return sersic_fwd2(L, bx, by); });
 }
 
 // The same at two points.
@@ -309,11 +315,9 @@ __device__ __forceinline__ float2 component_brightness2(const SampleC& sc, const
                                                         bool source, float2 x, float2 y) {
   const LightP& L = sc.light[c];
   if (!source) return sersic_fwd2(L, x, y);
-  const Geo2 g = epl_geometry2(sc.epl, x, y);
-  float2 Fr, Fi, bx, by;
-  deflection_F<TAB>(sc, tab, g, Fr, Fi);
-  lens_equation2(sc, g, x, y, Fr, Fi, bx, by);
-  return sersic_fwd2(L, bx, by);
+  return lensed_brightness2<TAB>(sc, tab, x, y, [&](float2, float2, float2 bx, float2 by) {
+    return sersic_fwd2(L, bx, by);
+  });
 }
 
 // ------------------------------------------------------ adjoint pieces ----
