@@ -266,7 +266,7 @@ def timed_steps(fn, steps, warmup, stream, flush):
 
 def learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world) -> dict:
     """The learned deflection surrogate on the same workload: trained here with
-    the library's kernels (1e7 exact-series tuples, 60 epochs), then the same
+    the library's kernels (1e7 exact-series tuples, 120 epochs), then the same
     timed steps with GL_DEFL_SURROGATE (per-row angular tables from the network,
     interpolated per sub-pixel; rows outside its q/gamma domain use the series).
     |d log p| is measured against the exact-series path of the same kernels,
@@ -274,7 +274,7 @@ def learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world) -
     import torch
     import paper_2606_30633_b300 as gl
     t0 = time.perf_counter()
-    sur = gl.Surrogate.train(n_samples=10_000_000, epochs=60, batch=16384, lr=2e-3, lr_min=1e-5,
+    sur = gl.Surrogate.train(n_samples=10_000_000, epochs=120, batch=16384, lr=2e-3, lr_min=1e-5,
                              seed_data=401, seed_init=402)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
@@ -624,7 +624,7 @@ def run_uneven(args) -> dict | None:
     with ClockSampler(local) as clk:
         ms = timed_steps(lambda: plan.logp_grad(thetas, logps, grads, stream=stream), args.steps,
                          args.warmup, stream, flush)
-    sur = gl.Surrogate.train(n_samples=10_000_000, epochs=60, batch=16384, lr=2e-3, lr_min=1e-5,
+    sur = gl.Surrogate.train(n_samples=10_000_000, epochs=120, batch=16384, lr=2e-3, lr_min=1e-5,
                              seed_data=401, seed_init=402)
     for s_ in systems:
         s_.set_surrogate(sur)

@@ -504,7 +504,7 @@ class Surrogate:
         return int(load().gl_surrogate_num_params())
 
     @classmethod
-    def train(cls, n_samples=10_000_000, epochs=60, batch=16384, lr=2e-3, lr_min=1e-5,
+    def train(cls, n_samples=10_000_000, epochs=120, batch=16384, lr=2e-3, lr_min=1e-5,
               seed_data=401, seed_init=402, q=(0.5, 1.0), gamma=(1.7, 2.3), r=(0.05, 5.0)):
         lib = load()
         d = gl_surrogate_train_desc(n_samples, epochs, batch, lr, lr_min, seed_data, seed_init,

@@ -33,8 +33,8 @@ def gl():
 @pytest.fixture(scope="module")
 def trained(gl):
     torch, g = gl
-    # the benchmark's training run: 1e7 exact-series tuples, 60 epochs
-    return g.Surrogate.train(n_samples=10_000_000, epochs=60, batch=16384, lr=2e-3, lr_min=1e-5,
+    # the benchmark's training run: 1e7 exact-series tuples, 120 epochs
+    return g.Surrogate.train(n_samples=10_000_000, epochs=120, batch=16384, lr=2e-3, lr_min=1e-5,
                              seed_data=401, seed_init=402)
 
 
