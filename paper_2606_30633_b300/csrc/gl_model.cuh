@@ -88,7 +88,6 @@ struct EplP {
   float2 ht, CA;              // (1 - t)/2, 2 b^t / (1 + q)
   float2 t, omt, ntmt;        // t, 1 - t, -(2 - t)
   float2 omtq;                // (1 - t) q
-  float2 Kk;                  // kappa = Kk A / R
   float2 lnb;
   float2 ndfdq;               // -d f / d q = 2/(1+q)^2
 };
@@ -240,7 +239,6 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
       E.CA = f2(2.f * powf(b, t) / (1.f + q));
       E.t = f2(t); E.omt = f2(1.f - t); E.ntmt = f2(t - 2.f);
       E.omtq = f2((1.f - t) * q);
-      E.Kk = f2((2.f - t) * (1.f + q) * 0.25f);
       E.lnb = f2(logf(b));
       E.ndfdq = f2(2.f / ((1.f + q) * (1.f + q)));
       F.p0 = th[0]; F.t = t; F.n = 0.f; F.I = 0.f; F.bn = 0.f;
@@ -341,8 +339,9 @@ __device__ inline void sersic_finish(const FinishC& F, const double* a, float* g
 }
 
 // EPL + shear native accumulators:
-// [0] sum s1 (theta_E), [1] d/dt, [2] d/dq, [3] sum kappa v.(iY) with
-// d/dphi = -2 f [3] (exact series) or d/dphi itself (surrogate table),
+// [0] sum s1 (theta_E), [1] d/dt, [2] d/dq, [3] sum (kappa/Kk) v.(iY) with
+// d/dphi = -2 f Kk [3] (exact series; Kk = (2 - t)(1 + q)/4 is applied here)
+// or d/dphi itself (surrogate table),
 // [4] sum v.d alpha/dx', [5] sum v.d alpha/dy' (lens frame; the centre
 // gradient is minus these), [6] d/dg1, [7] d/dg2.
 // With f = |e| and d phi/d e = (-e2, e1)/(2 f^2) the rotation part of d/de is
@@ -356,7 +355,9 @@ __device__ inline void epl_finish(const FinishC& F, const double* a, float* g,
   // a[2] holds the q-derivative without its constant part a0 sum s1, a0 =
   // t/(2q) - 1/(1+q) (the derivative of ln of the deflection prefactor)
   const double a0 = (double)F.t / (2.0 * F.q) - 1.0 / (1.0 + F.q);
-  const float dq = (float)(a[2] + a0 * a[0]), rot = (float)a[3];
+  // the series path sums kappa/Kk v.(iY) in a[3]; Kk = (2 - t)(1 + q)/4 per sample
+  const double Kk = (2.0 - (double)F.t) * (1.0 + (double)F.q) * 0.25;
+  const float dq = (float)(a[2] + a0 * a[0]), rot = (float)(rot_is_dphi ? a[3] : Kk * a[3]);
   g[0] = F.t / F.p0 * (float)a[0];
   g[1] = (float)a[1];
   if (rot_is_dphi) {

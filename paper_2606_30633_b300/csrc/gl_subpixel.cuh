@@ -478,8 +478,8 @@ __device__ __forceinline__ void subpixel_adjoint2(const SampleC& sc, const float
   const float2 yS = mul2(g.yp, S13);
   acc_fma(acc[2], xR, fma2(mul2(e.omtq, xp), s1, neg2(yS)));
   // rotation: d alpha'/d phi = i X with X = (2-t) alpha' - 2 kappa z' =
-  // -2 kappa f (z' w E + conj(z') F), which is O(f); acc[3] = sum kappa v.(iY)
-  const float2 kap = mul2(mul2(e.Kk, A), g.ir);
+  // -2 kappa f (z' w E + conj(z') F), which is O(f); acc[3] = sum (kappa/Kk) v.(iY)
+  const float2 kap = mul2(A, g.ir);  // kappa / Kk, Kk = (2 - t)(1 + q)/4 applied per sample
   const float2 zwr = fma2(xp, g.wr, mul2(g.yp, g.nwi)), zwi = fma2(xp, g.wi, mul2(g.yp, g.wr));
   const float2 Yr = fma2(zwr, Er, fma2(neg2(zwi), Ei, fma2(xp, Fr, mul2(g.yp, Fi))));
   const float2 Yi = fma2(zwr, Ei, fma2(zwi, Er, fma2(xp, Fi, mul2(neg2(g.yp), Fr))));
