@@ -81,8 +81,8 @@ def algorithmic_ops(theta: np.ndarray, ny: int, nx: int, s: int, k: int, n_light
                          + 11 per Sersic + (components - 1) (sum) + 1 (bin)
                          ... 3 MUFU for the EPL, 3 per Sersic
       adjoint sub-pixel  2 + 15 + 1 + 4N (both series) + 10 (E, F, dF/dt)
-                         + 16 + 25 per Sersic + 7 per source (position
-                         gradient) + 74 (EPL and shear adjoint)
+                         + 16 + 24 per Sersic + 8 per source (amplitude and
+                         position gradient) + 74 (EPL and shear adjoint)
                          ... 4 MUFU for the EPL, 4 per Sersic
       per pixel          2 k^2 (PSF convolution and its adjoint) + 8
     with N the row's series length (Clenshaw's recurrence: two operations
@@ -93,7 +93,7 @@ def algorithmic_ops(theta: np.ndarray, ny: int, nx: int, s: int, k: int, n_light
     f = np.hypot(theta[:, 2], theta[:, 3])
     N = np.array([series_terms(float(v), float(g) - 1.0) for v, g in zip(f, theta[:, 1])])
     fwd = 2 + 14 + 1 + 2 * N + 4 + 16 + 11 * ncomp + (ncomp - 1) + 1
-    adj = 2 + 15 + 1 + 4 * N + 10 + 16 + 25 * ncomp + 7 * n_src + 74
+    adj = 2 + 15 + 1 + 4 * N + 10 + 16 + 24 * ncomp + 8 * n_src + 74
     ops = nsub * (fwd + adj) + npix * (2 * k * k + 8)
     mufu = nsub * (3 + 3 * ncomp + 4 + 4 * ncomp)
     return float(ops.sum()), float(mufu * theta.shape[0])

@@ -524,7 +524,7 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
       for (int k = 0; k < 8; ++k) grad_out[k] = g[k] + sc.dprior[k];
     } else {
       const int o = 8 + 7 * (c - 1);
-      sersic_finish(st.fin[c], st.adj.gsum + o, g);
+      sersic_finish(st.fin[c], st.adj.gsum + o, g, c - 1 < NL);
 #pragma unroll
       for (int k = 0; k < 7; ++k) grad_out[o + k] = g[k] + sc.dprior[o + k];
     }

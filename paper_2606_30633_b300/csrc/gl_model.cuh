@@ -312,13 +312,20 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
 
 // Converts a Sersic component's native accumulators a[0..6] to gradients
 // w.r.t. [R_e, n, e1, e2, x, y, I_e] (one lane per component).
-__device__ inline void sersic_finish(const FinishC& F, const double* a, float* g) {
+// amp_deferred: a lens-light component, whose sums a[1..6] were taken without
+// the amplitude I_e e^{b_n} (a[0] sums u S / (I_e e^{b_n}) for every component).
+__device__ inline void sersic_finish(const FinishC& F, const double* a, float* g,
+                                     bool amp_deferred) {
   const float m = -F.bn / F.n;
+  const double eb = (double)expf(F.bn);
+  const double amp = (double)(F.I * expf(F.bn));  // the staged I_e e^{b_n}
+  const double s16 = amp_deferred ? amp : 1.0;
   // a[3], a[5], a[6] hold sums over u^2 - v^2, u, v (u = sqrt(q) x', v = y'/sqrt(q));
   // A3, A5, A6 are the same sums over x'^2 - y'^2/q^2, x', y'
   const float rq = sqrtf(F.q);
-  const float A0 = (float)a[0], A1 = (float)a[1], A2 = (float)a[2], A3 = (float)a[3] / F.q;
-  const float A4 = (float)a[4], A5 = (float)a[5] / rq, A6 = (float)a[6] * rq;
+  const float A0 = (float)(amp * a[0]), A1 = (float)(s16 * a[1]), A2 = (float)(s16 * a[2]);
+  const float A3 = (float)(s16 * a[3]) / F.q;
+  const float A4 = (float)(s16 * a[4]), A5 = (float)(s16 * a[5]) / rq, A6 = (float)(s16 * a[6]) * rq;
   // d/dphi = m (q - 1/q) A4 with q - 1/q = -4c/(1-c^2); d phi/d e = (-e2, e1)/(2c^2),
   // so the rotation part of d/de is 2 m A4 (sin 2phi, -cos 2phi)/(1-c^2) (no 1/c)
   const float dq = 0.5f * m * A3;
@@ -335,7 +342,7 @@ __device__ inline void sersic_finish(const FinishC& F, const double* a, float* g
   g[3] = dq * dqdc * s2p - rot * c2p;
   g[4] = -(F.cs * Sx - F.sn * Sy);
   g[5] = -(F.sn * Sx + F.cs * Sy);
-  g[6] = A0 / F.I;
+  g[6] = (float)(eb * a[0]);  // d S / d I_e = e^{b_n} Se: finite at I_e = 0
 }
 
 // EPL + shear native accumulators:

@@ -337,9 +337,10 @@ template <> __device__ __forceinline__ float acc_zero<float>() { return 0.f; }
 
 // Native accumulators of a Sersic component (converted to parameter
 // gradients once per sample), in the scaled frame us = sqrt(q) x',
-// vs = y'/sqrt(q): [0] sum uS, [1] sum uSp, [2] sum uSp log2 p,
+// vs = y'/sqrt(q): [0] sum u Se (Se = S / (I_e e^{b_n})), [1] sum uSp, [2] sum uSp log2 p,
 // [3] sum uSp/R^2 (us^2 - vs^2), [4] sum uSp/R^2 us vs,
-// [5] sum uSp/R^2 us, [6] sum uSp/R^2 vs (one sum per lane).
+// [5] sum uSp/R^2 us, [6] sum uSp/R^2 vs (one sum per lane); for a lens-light
+// component [1..6] also hold S / (I_e e^{b_n}) in place of S.
 // If grad_pos, adds dS/dX, dS/dY (without u) to gX, gY.
 template <bool grad_pos, class AccT>
 __device__ __forceinline__ void sersic_adj2(const LightP& c, float2 X, float2 Y, float2 u,
@@ -351,14 +352,19 @@ __device__ __forceinline__ void sersic_adj2(const LightP& c, float2 X, float2 Y,
   const float2 R2 = max2(R2raw, R_MIN2);
   const float2 l2p = fma2(c.c1, lg2_2(R2), c.c0);
   const float2 p = ex2_2(l2p);
-  const float2 S = mul2(c.Ip, ex2_2(mul2(c.nbl, p)));
+  // Se: the profile without its amplitude I_e e^{b_n}. A lens-light component
+  // (no position gradient) accumulates everything without the amplitude, which
+  // sersic_finish applies per sample; a source keeps it, since its position
+  // gradient feeds the deflection's adjoint. a[0] always sums u Se.
+  const float2 Se = ex2_2(mul2(c.nbl, p));
+  const float2 S = grad_pos ? mul2(c.Ip, Se) : Se;
   const float2 Sp = mul2(S, p);
   // d R^2 / d(position) vanishes where the radius is clamped
   float2 rR2 = rcp2(R2);
   rR2.x = R2raw.x > R_MIN2 ? rR2.x : 0.f;
   rR2.y = R2raw.y > R_MIN2 ? rR2.y : 0.f;
   const float2 uSp = mul2(u, Sp), kD = mul2(uSp, rR2);
-  acc_fma(a[0], u, S);
+  acc_fma(a[0], u, Se);
   acc_add(a[1], uSp);
   acc_fma(a[2], uSp, l2p);
   acc_fma(a[3], kD, fma2(us, us, mul2(neg2(vs), vs)));

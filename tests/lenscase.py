@@ -124,7 +124,9 @@ def grad_bound(case: "Case", th: np.ndarray, rel=1e-3, eps=EPS_MODEL,
 def grad_close_bound(got, ref, bound):
     """(ok, worst ratio err/bound and where: (row, parameter index, got, ref))."""
     err = np.abs(np.asarray(got, np.float64) - ref)
-    r = np.atleast_2d(err / bound)
+    # an exact zero bound (an entry that is exactly 0 on both sides) counts as ratio 0
+    # unless the error is non-zero
+    r = np.atleast_2d(np.divide(err, bound, out=np.where(err > 0, np.inf, 0.0), where=bound > 0))
     b, k = np.unravel_index(int(np.argmax(r)), r.shape)
     g2, r2 = np.atleast_2d(got), np.atleast_2d(ref)
     return bool(np.all(err <= bound)), (float(r[b, k]), int(b), int(k), float(g2[b, k]),

@@ -214,6 +214,41 @@ def test_degenerate_lenses(torch):
     assert lpt[0].item() == lp[0] and np.array_equal(gt[0].cpu().numpy(), g[0].astype(np.float32))
 
 
+def test_zero_intensity_components(torch):
+    """Components with intensity exactly 0 under flat intensity priors (the
+    backward solve's setting): log p and the whole gradient, including
+    d log p / d I_e, finite and equal to the oracle's."""
+    import dataclasses
+
+    import oracle
+    import paper_2606_30633_b300 as gl
+    from lenscase import round_spec
+    c = make_case(small_workload(20, 20, 2, 5, 1, 1, seed=37))
+    ps = list(c.spec.params)
+    ps[14] = synth.Prior("flat", 0.0, 1.0, -np.inf, np.inf)  # lens-light intensity
+    ps[21] = synth.Prior("flat", 0.0, 1.0, -np.inf, np.inf)  # source intensity
+    spec = round_spec(synth.PriorSpec(ps, c.spec.emax))
+    W = c.W
+    orc = oracle.System(W.ny, W.nx, W.pixel_scale, W.supersample, c.data, c.sigma, c.psf, 1, 1,
+                        spec)
+    cf = dataclasses.replace(c, spec=spec, oracle=orc)
+    s = gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, c.data, c.sigma, c.psf, 1, 1, spec)
+    th = np.repeat(c.truth[None], 3, 0)
+    th[0, 14] = 0.0
+    th[1, 21] = 0.0
+    th[2, [14, 21]] = 0.0
+    th = np.asarray(np.asarray(th, np.float32), np.float64)
+    lp, g = s.logp_grad(torch.tensor(th, dtype=torch.float32, device="cuda"))
+    lp, g = lp.cpu().numpy(), g.cpu().numpy().astype(np.float64)
+    assert np.isfinite(lp).all() and np.isfinite(g).all()
+    lref, gref = orc.logp_grad(th)
+    ok, worst = _lp_close(lp, lref)
+    assert ok, worst
+    ok, worst = grad_close_bound(g, gref, grad_bound(cf, th))
+    assert ok, worst
+    s.close()
+
+
 def test_tiny_image_single_pixel(torch):
     c = make_case(small_workload(1, 1, 3, 1, 1, 1, seed=3))
     th = c.theta(4)
