@@ -42,14 +42,14 @@ MUFU_PER_SM_CLK = 16
 # (4096 rows), from one ncu capture of this bench's own launch:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
 #       -k regex:k_grad -s 3 -c 1 python bench.py --steps 5 --warmup 3 --no-cpu-baseline
-# (626,432 read + 0 written; the outputs are still in L2 when the launch ends).
+# (700,160 read + 0 written; the outputs are still in L2 when the launch ends).
 # Set to None when the kernel changes until it is captured again.
-TRAFFIC_GROUND_4096 = 626432
+TRAFFIC_GROUND_4096 = 700160
 # DRAM bytes of one k_grad launch of the space-telescope workload per row,
-# from one --set full capture of a 512-row launch inside the HMC leg
-# (24,538,112 read + 181,527,296 written); the traffic is the per-row scratch
+# from one capture of a 512-row launch inside the HMC leg
+# (24,968,704 read + 181,744,384 written); the traffic is the per-row scratch
 # images, so it grows in proportion to the rows. None when the kernel changes.
-TRAFFIC_SPACE_PER_ROW = (24538112 + 181527296) / 512
+TRAFFIC_SPACE_PER_ROW = (24968704 + 181744384) / 512
 
 
 # ------------------------------------------------------------ op counts ----
