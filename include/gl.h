@@ -441,7 +441,8 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
  * linear inversion instead of sampled). The model image is linear in the
  * Sersic intensities, m = sum_k I_k M_k, so per row the intensities that
  * maximise the likelihood solve (M^T W M) I = M^T W d, W = diag(sigma^-2)
- * (FP64 sums over the pixels, Cholesky). The paper gives no formula; this
+ * (compensated FP32 sums per thread, FP64 across threads, Cholesky in FP64).
+ * The paper gives no formula; this
  * library takes:
  *   theta      [B][P]; its intensity entries (index 8 + 7c + 6 of light
  *              component c, lens lights first) are ignored;
