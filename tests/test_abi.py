@@ -116,3 +116,30 @@ def test_inference_entry_points_reject_bad_arguments(lib):
     assert lib.gl_hmc_state(None, None, None, None, None, None) == gl.GL_EINVAL
     assert lib.gl_hmc_destroy(None) == gl.GL_OK
     assert "NULL" in gl.last_error() or "sampler" in gl.last_error()
+
+
+def _ground_system_args():
+    W = synth.ground_60()
+    return (W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
+            np.ones((W.ny, W.nx)), W.psf, 1, 1, W.prior())
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    """No libgl.so: the binding raises ImportError instead of computing anything."""
+    monkeypatch.setattr(gl, "_LIB", None)
+    monkeypatch.setattr(gl, "LIB_PATH", str(tmp_path / "libgl.so"))
+    with pytest.raises(ImportError, match="missing"):
+        gl.load()
+    with pytest.raises(ImportError):
+        gl.System(*_ground_system_args())
+
+
+def test_no_cpu_fallback_without_a_device(lib):
+    """Without a CUDA device, creating a system fails with GL_ECUDA (there is no
+    host code path to fall back to)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(gl.GLError) as e:
+        gl.System(*_ground_system_args())
+    assert e.value.status == gl.GL_ECUDA
