@@ -258,6 +258,39 @@ def test_tiny_image_single_pixel(torch):
     assert grad_close_bound(g.cpu().numpy(), gref, grad_bound(c, th))[0]
 
 
+def test_maximum_image_size(torch):
+    """The largest image the library accepts, 2048 x 2048 with a 21 x 21 PSF
+    (per-row images in global scratch): model image and log p of the truth, a
+    row a small step from it and a prior draw. The gradient is checked at the
+    maximum width on a 2048-pixel-wide strip, where the oracle's Jacobian
+    for the tolerance stays cheap."""
+    c = make_case(small_workload(2048, 2048, 1, 21, 1, 1, pixel_scale=0.005, seed=7))
+    th = np.concatenate([_near_mode(c, 2), c.theta(1)])
+    sysg = c.gpu_system()
+    t = torch.tensor(th, dtype=torch.float32, device="cuda")
+    img = sysg.model_image(t).cpu().numpy().astype(np.float64)
+    ref = c.oracle.model_image(th)
+    for b in range(th.shape[0]):
+        ok, worst = image_close(img[b], ref[b])
+        assert ok, (b, worst)
+    lp, _ = sysg.logp_grad(t)
+    lp = lp.cpu().numpy()
+    ok, worst = _mode_close(c, th[:2], lp[:2])
+    assert ok, worst
+    ok, worst = _lp_close(lp[2:], c.oracle.logp(th[2:]))
+    assert ok, worst
+    np.testing.assert_array_equal(sysg.logp(t).cpu().numpy(), lp)
+    sysg.close()
+
+    c = make_case(small_workload(160, 2048, 1, 21, 1, 1, pixel_scale=0.01, seed=8))
+    th = np.concatenate([_near_mode(c, 1), c.theta(1)])
+    lp, g = c.gpu_system().logp_grad(torch.tensor(th, dtype=torch.float32, device="cuda"))
+    lref, gref = c.oracle.logp_grad(th)
+    assert _mode_close(c, th[:1], lp.cpu().numpy()[:1])[0]
+    ok, worst = grad_close_bound(g.cpu().numpy(), gref, grad_bound(c, th))
+    assert ok, worst
+
+
 def test_host_buffer_entry_point(torch):
     c = make_case(small_workload(32, 32, 2, 11, 1, 1, seed=9))
     sysg = c.gpu_system()
