@@ -141,3 +141,27 @@ def test_shear_and_lens_equation():
     sb = S.surface_brightness(th, x, y)
     ref = oracle.sersic(src, x - ax, y - ay)
     np.testing.assert_allclose(sb, ref, rtol=1e-8)
+
+
+def test_sis_images_of_an_offset_source():
+    """Singular isothermal sphere (gamma = 2, e = 0) with Einstein radius
+    theta_E and a round source at (beta0, 0), beta0 < theta_E: the lens equation
+    beta = theta - theta_E theta/|theta| has the two images theta = beta0 +
+    theta_E and beta0 - theta_E on the x axis (Schneider, Ehlers & Falco 1992,
+    Sec. 8.1). There the lensed surface brightness equals the source's central
+    brightness, and it falls off on both sides along the axis."""
+    thetaE, beta0 = 1.2, 0.3
+    S = _system(4, 4, 0.1, 1, np.ones((1, 1)))
+    th = np.zeros(22)
+    th[:8] = [thetaE, 2.0, 0, 0, 0, 0, 0, 0]
+    th[8:15] = [0.2, 1.0, 0, 0, 0, 0, 0.0]     # no lens light
+    src = [0.15, 0.5, 0.0, 0.0, beta0, 0.0, 1.0]
+    th[15:22] = src
+    peak = oracle.sersic(src, np.array([beta0]), np.array([0.0]))[0]
+    for x_img in (beta0 + thetaE, beta0 - thetaE):
+        sb = S.surface_brightness(th, np.array([x_img]), np.array([0.0]))[0]
+        assert abs(sb / peak - 1) < 1e-9, (x_img, sb, peak)
+        side = S.surface_brightness(th, np.array([x_img - 0.02, x_img + 0.02]), np.zeros(2))
+        assert np.all(side < 0.99 * peak)
+    # the unlensed position of the source is not an image: the brightness there is tiny
+    assert S.surface_brightness(th, np.array([beta0]), np.array([0.0]))[0] < 1e-3 * peak

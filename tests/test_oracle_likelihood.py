@@ -75,6 +75,21 @@ def test_support_domain_and_nan():
     assert np.isnan(S.logp(t)[0])
 
 
+def test_model_domain_of_the_slope():
+    """The EPL exists for 1 < gamma < 3 (t = gamma - 1 in (0, 2)): with a prior
+    that does not bound gamma, log p is -inf outside that range and finite
+    inside it."""
+    S, th0, spec, m, sig = _small(8, 8, 1)
+    ps = list(spec.params)
+    ps[1] = synth.Prior("normal", 2.0, 1.0)
+    wide = synth.PriorSpec(ps, spec.emax)
+    S2 = oracle.System(8, 8, 0.262, 1, S.data, S.sigma, S.psf, 1, 1, wide)
+    rows = np.repeat(th0[None], 4, 0)
+    rows[:, 1] = [0.95, 1.05, 2.95, 3.05]
+    lp = S2.logp(rows)
+    assert np.isneginf(lp[[0, 3]]).all() and np.isfinite(lp[[1, 2]]).all()
+
+
 @pytest.mark.parametrize("which", ["truth", "draw0", "draw1"])
 def test_dual_gradient_matches_central_differences(which):
     """Forward-mode dual-number gradient against FP64 central differences,
