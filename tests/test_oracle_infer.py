@@ -133,12 +133,24 @@ def test_leapfrog_on_the_harmonic_oscillator_is_the_known_linear_map():
     # five steps = A^5
     u5, p5, _, _ = I.leapfrog(u0, p0, lp, g, np.ones(1), eps, 5, lg)
     assert np.allclose([u5[0, 0], p5[0, 0]], np.linalg.matrix_power(A, 5) @ [0.7, -0.4])
+    # inverse mass c (H = u^2/2 + c p^2/2): the half kicks are unchanged and the
+    # drift moves u by e c p, so one step is
+    # [u, p] -> [(1 - c e^2/2) u + c e p, -e (1 - c e^2/4) u + (1 - c e^2/2) p]
+    c = 2.5
+    uc, pc, _, _ = I.leapfrog(u0, p0, lp, g, np.full(1, c), eps, 1, lg)
+    Ac = np.array([[1 - c * eps ** 2 / 2, c * eps],
+                   [-eps * (1 - c * eps ** 2 / 4), 1 - c * eps ** 2 / 2]])
+    assert np.allclose([uc[0, 0], pc[0, 0]], Ac @ [0.7, -0.4], atol=1e-14)
+    assert abs(np.linalg.det(Ac) - 1) < 1e-14  # leapfrog is volume preserving
 
 
-def test_hmc_leaves_a_gaussian_invariant():
+@pytest.mark.parametrize("inv_mass", [(1.0, 1.0), (0.3, 5.0)])
+def test_hmc_leaves_a_gaussian_invariant(inv_mass):
     # target N(0, diag(1, 4)); 4000 chains started from the target; the
     # Metropolis-Hastings correction keeps it invariant even at a step with
-    # large energy errors
+    # large energy errors, for any (here deliberately mismatched) mass matrix,
+    # provided the momenta are drawn from N(0, M)
+    inv_mass = np.array(inv_mass)
     sd = np.array([1.0, 2.0])
     lg = lambda u: (-0.5 * ((u / sd) ** 2).sum(1), -u / sd ** 2)
     rng = np.random.default_rng(11)
@@ -148,7 +160,7 @@ def test_hmc_leaves_a_gaussian_invariant():
     rates = []
     for step in range(60):
         z, a = I.hmc_draws(5, step, B, 2)
-        u, lp, g, acc_p, acc = I.hmc_transition(u, lp, g, np.ones(2), 1.6, 3, z, a, lg)
+        u, lp, g, acc_p, acc = I.hmc_transition(u, lp, g, inv_mass, 1.6, 3, z, a, lg)
         rates.append(acc.mean())
     assert 0.2 < np.mean(rates) < 0.95
     assert np.allclose(u.mean(0), 0.0, atol=0.1)

@@ -78,11 +78,77 @@ MUTANTS = [
      "return chain(a, std::log(a.v), a.v);"),
 ]
 
+# (module, name, original text, mutated text, pin files) for the Python parts
+PY_PINS = {"infer": ["tests/test_oracle_infer.py"], "backward": ["tests/test_oracle_backward.py"],
+           "mlp": ["tests/test_oracle_mlp.py"]}
+PY_MUTANTS = [
+    ("infer", "interval log-det width", "logj += math.log(w) - np.abs(x)", "logj += -np.abs(x)"),
+    ("infer", "exp log-det", "th[:, k] = np.exp(x)\n                logj += x",
+     "th[:, k] = np.exp(x)\n                logj += 2.0 * x"),
+    ("infer", "disc log-det term", " + np.log(_tanh_over(rho))", ""),
+    ("infer", "interval Jacobian", "* s * (1.0 - s)", "* s"),
+    ("infer", "disc Jacobian outer term", "(g if a == b else 0.0) + gp_over * v[:, a] * v[:, b]",
+     "(g if a == b else 0.0)"),
+    ("infer", "interval log-det gradient", "G[:, k] = 1.0 - 2.0 / (1.0 + np.exp(-x))",
+     "G[:, k] = 1.0 - 1.0 / (1.0 + np.exp(-x))"),
+    ("infer", "unconstrained gradient drops the log-det",
+     'gu = np.einsum("bij,bi->bj", J, g) + bij.grad_logj(u)', 'gu = np.einsum("bij,bi->bj", J, g)'),
+    ("infer", "disc inverse radius", "rho = np.arctanh(r / R)", "rho = np.arctanh(r)"),
+    ("infer", "SplitMix64 shift", "z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9)",
+     "z = ((z ^ (z >> 31)) * 0xBF58476D1CE4E5B9)"),
+    ("infer", "uniform grid offset", "return ((z >> 40) + 0.5)", "return ((z >> 40) + 1.0)"),
+    ("infer", "drift without the mass", "u = u + eps * inv_mass * p", "u = u + eps * p"),
+    ("infer", "kinetic energy factor", "H0 = -lp + 0.5 * np.sum(inv_mass * p0 * p0, axis=1)",
+     "H0 = -lp + np.sum(inv_mass * p0 * p0, axis=1)"),
+    ("infer", "momentum scale", "p0 = z / np.sqrt(inv_mass)", "p0 = z * np.sqrt(inv_mass)"),
+    ("infer", "acceptance sign", "dH = H0 - H1", "dH = H1 - H0"),
+    ("infer", "burn-in fraction", "0.9 * n", "0.5 * n"),
+    ("infer", "Adam bias correction", "mh = m / (1 - b1 ** t)\n        vh",
+     "mh = m\n        vh"),
+    ("infer", "AdaBelief belief term", "d = g - m", "d = g"),
+    ("infer", "SVI L-gradient diagonal", "g_L = np.tril(g_L) - np.diag(w.mean() / np.diag(L))",
+     "g_L = np.tril(g_L)"),
+    ("infer", "SVI score transposed", "a = np.linalg.solve(L.T, z.T).T", "a = np.linalg.solve(L, z.T).T"),
+    ("infer", "R-hat between-chain variance",
+     "B = N / (M - 1) * ((cm - cm.mean(axis=0)) ** 2).sum(axis=0)",
+     "B = 1.0 / (M - 1) * ((cm - cm.mean(axis=0)) ** 2).sum(axis=0)"),
+    ("infer", "ESS lag-0 term", "tau = -1.0 + 2.0 * tau_sum", "tau = 2.0 * tau_sum"),
+    ("backward", "normal equations weights", "w = (1.0 / system.sigma ** 2).ravel()",
+     "w = (1.0 / system.sigma).ravel()"),
+    ("backward", "intensity index", "return [8 + 7 * c + 6 for c", "return [8 + 7 * c + 5 for c"),
+    ("mlp", "BF16 rounding ties", "(b + 0x7FFF + ((b >> 16) & 1))", "(b + 0x8000)"),
+    ("mlp", "SiLU derivative", "sps.append(bf16r(s * (1 + z * (1 - s))))",
+     "sps.append(bf16r(s * (1 + z * s)))"),
+    ("mlp", "weight gradient input", 'g[f"W{l}"] = bf16(dz).T @ cache[l - 1]',
+     'g[f"W{l}"] = bf16(dz).T @ cache[l]'),
+    ("mlp", "second series coefficient", "c2 = c1 * (2 + t) / (6 - t)", "c2 = c1 * (2 + t) / (4 - t)"),
+    ("mlp", "tail factor power", "return base_F(X) + z ** 3 *", "return base_F(X) + z ** 2 *"),
+]
+
 # the pins import the oracle, whose loader builds liboracle.so; the subprocess
 # points that build step at the mutant library instead
 RUNNER = ("import sys; sys.path[:0] = [{root!r}, {tests!r}]; import oracle.build as b; "
           "b.build = lambda force=False: {lib!r}; import pytest; "
           "sys.exit(pytest.main(['-x', '-q', '-p', 'no:cacheprovider', *{pins!r}]))")
+
+PY_RUNNER = ("import sys, types; sys.path[:0] = [{root!r}, {tests!r}]; import oracle; "
+             "path = {path!r}; src = open(path).read(); "
+             "m = types.ModuleType('oracle.' + {mod!r}); m.__file__ = path; "
+             "m.__package__ = 'oracle'; sys.modules['oracle.' + {mod!r}] = m; "
+             "setattr(oracle, {mod!r}, m); "
+             "exec(compile(src.replace({old!r}, {new!r}), path, 'exec'), m.__dict__); "
+             "import pytest; "
+             "sys.exit(pytest.main(['-x', '-q', '-p', 'no:cacheprovider', *{pins!r}]))")
+
+
+def _pin_python(mod: str, old: str, new: str):
+    code = PY_RUNNER.format(root=ROOT, tests=os.path.join(ROOT, "tests"),
+                            path=os.path.join(ROOT, "oracle", mod + ".py"), mod=mod, old=old,
+                            new=new, pins=PY_PINS[mod])
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=600)
+    return r.returncode, r.stdout[-3000:]
 
 
 def _build_and_pin(tag: str, text: str):
@@ -112,6 +178,12 @@ def results():
     workers = max(1, min(8, os.cpu_count() or 1))
     with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
         futs = {tag: ex.submit(_build_and_pin, tag, text) for tag, text in jobs.items()}
+        futs["py-original"] = ex.submit(_pin_python, "infer", "", "")
+        for mod in ("backward", "mlp"):
+            futs[f"py-original-{mod}"] = ex.submit(_pin_python, mod, "", "")
+        for k, (mod, name, old, new) in enumerate(PY_MUTANTS):
+            assert open(os.path.join(ROOT, "oracle", mod + ".py")).read().count(old) == 1, name
+            futs[f"p{k:02d}"] = ex.submit(_pin_python, mod, old, new)
         return {tag: f.result() for tag, f in futs.items()}
 
 
@@ -124,3 +196,15 @@ def test_unmodified_oracle_passes_the_pins(results):
 def test_planted_mistake_fails_a_pin(results, k):
     rc, out = results[f"m{k:02d}"]
     assert rc == 1, (MUTANTS[k][0], rc, out)
+
+
+def test_unmodified_python_oracle_passes_the_pins(results):
+    for tag in ("py-original", "py-original-backward", "py-original-mlp"):
+        rc, out = results[tag]
+        assert rc == 0, (tag, out)
+
+
+@pytest.mark.parametrize("k", range(len(PY_MUTANTS)), ids=[m[1] for m in PY_MUTANTS])
+def test_planted_mistake_in_python_fails_a_pin(results, k):
+    rc, out = results[f"p{k:02d}"]
+    assert rc == 1, (PY_MUTANTS[k][1], rc, out)
