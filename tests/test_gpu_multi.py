@@ -68,3 +68,26 @@ def test_autotuner_returns_the_fastest_policy(env):
     assert set(times) == {"global", "two_ctas", "one_cta"}
     assert times[min(times, key=times.get)] == min(times.values())
     assert best.smem_policy == autotune.POLICIES[min(times, key=times.get)]
+
+
+@pytest.mark.parametrize("defl", ["series", "table"])
+def test_systems_without_rows(env, defl):
+    """Systems with zero rows are skipped, including a whole component-count
+    group without rows; the others still match their own gl_logp_grad bit for
+    bit. A plan in which no system has rows launches nothing and succeeds."""
+    torch, gl, cases, systems, thetas = env
+    d = gl.GL_DEFL_SERIES if defl == "series" else gl.GL_DEFL_TABLE
+    th = [t if k % 2 == 0 else t[:0] for k, t in enumerate(thetas)]
+    plan = gl.Multi(systems, [t.shape[0] for t in th], gl.GL_MULTI_SMEM_TWO_CTAS)
+    lps, gs = plan.logp_grad(th, defl=d)
+    torch.cuda.synchronize()
+    for s, t, lp, g in zip(systems, th, lps, gs):
+        assert lp.shape[0] == t.shape[0] and g.shape == t.shape
+        if t.shape[0]:
+            rl, rg = s.logp_grad(t, defl=d)
+            np.testing.assert_array_equal(lp.cpu().numpy(), rl.cpu().numpy())
+            np.testing.assert_array_equal(g.cpu().numpy(), rg.cpu().numpy())
+    none = gl.Multi(systems, [0] * len(systems), gl.GL_MULTI_SMEM_GLOBAL)
+    lps, gs = none.logp_grad([t[:0] for t in thetas], defl=d)
+    torch.cuda.synchronize()
+    assert all(lp.numel() == 0 for lp in lps) and all(g.numel() == 0 for g in gs)
