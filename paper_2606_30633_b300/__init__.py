@@ -167,6 +167,19 @@ def _ptr(t) -> Optional[int]:
     return None if t is None else int(t.data_ptr())
 
 
+def _need(t, shape, name: str):
+    """t must be a contiguous CUDA float32 tensor of exactly this shape: the
+    library reads or writes through its raw pointer, so a short buffer would
+    be accessed out of bounds."""
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA float32 tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, not {tuple(t.shape)}")
+    return t
+
+
 def prior_array(prior_spec) -> ctypes.Array:
     arr = (gl_prior * len(prior_spec.params))()
     for k, p in enumerate(prior_spec.params):
@@ -229,7 +242,8 @@ class System:
         torch = _torch()
         theta = self._theta(theta)
         B = theta.shape[0]
-        out = torch.empty(B, device=theta.device, dtype=torch.float32) if out is None else out
+        out = (torch.empty(B, device=theta.device, dtype=torch.float32) if out is None
+               else _need(out, (B,), "out"))
         _check(self._lib.gl_logp(self._h, _ptr(theta), B, _ptr(out), defl, _stream_ptr(stream)))
         return out
 
@@ -237,8 +251,9 @@ class System:
         torch = _torch()
         theta = self._theta(theta)
         B = theta.shape[0]
-        out = torch.empty(B, device=theta.device, dtype=torch.float32) if out is None else out
-        grad = torch.empty_like(theta) if grad is None else grad
+        out = (torch.empty(B, device=theta.device, dtype=torch.float32) if out is None
+               else _need(out, (B,), "out"))
+        grad = torch.empty_like(theta) if grad is None else _need(grad, (B, self.P), "grad")
         _check(self._lib.gl_logp_grad(self._h, _ptr(theta), B, _ptr(out), _ptr(grad), defl,
                                       _stream_ptr(stream)))
         return out, grad
@@ -306,12 +321,11 @@ class System:
         are the Adam moments (zeros for a fresh start). Returns log p~ at the
         last point evaluated."""
         torch = _torch()
-        for t in (u, m, v):
-            self._rows(t)
-            if not t.is_contiguous():
-                raise ValueError("u, m and v must be contiguous")
-        B = u.shape[0]
-        logp = torch.empty(B, device=u.device, dtype=torch.float32) if logp is None else logp
+        B = u.shape[0] if isinstance(u, torch.Tensor) and u.dim() == 2 else -1
+        for t, name in ((u, "u"), (m, "m"), (v, "v")):
+            _need(t, (B, self.P), name)
+        logp = (torch.empty(B, device=u.device, dtype=torch.float32) if logp is None
+                else _need(logp, (B,), "logp"))
         _check(self._lib.gl_map_adam(self._h, _ptr(u), _ptr(m), _ptr(v), B, int(n_steps),
                                      int(t0), float(lr), float(beta1), float(beta2), float(eps),
                                      _ptr(logp), defl, _stream_ptr(stream)))
@@ -358,8 +372,9 @@ class System:
         torch = _torch()
         theta = self._theta(theta)
         B = theta.shape[0]
-        out = torch.empty(B, device=theta.device, dtype=torch.float32) if out is None else out
-        grad = torch.empty_like(theta) if grad is None else grad
+        out = (torch.empty(B, device=theta.device, dtype=torch.float32) if out is None
+               else _need(out, (B,), "out"))
+        grad = torch.empty_like(theta) if grad is None else _need(grad, (B, self.P), "grad")
         _check(self._lib.gl_logp_grad_noalloc(self._h, _ptr(theta), B, _ptr(out), _ptr(grad),
                                               _stream_ptr(stream)))
         return out, grad
@@ -368,6 +383,8 @@ class System:
                        stream=None):
         """Host arrays in and out (the copies happen inside the call)."""
         th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+        if th.ndim != 2 or th.shape[1] != self.P:
+            raise ValueError(f"theta must be [B, {self.P}]")
         B = th.shape[0]
         lp = np.empty(B, dtype=np.float32)
         g = np.empty_like(th) if want_grad else None
@@ -381,7 +398,7 @@ class System:
         theta = self._theta(theta)
         B = theta.shape[0]
         out = (torch.empty((B, self.ny, self.nx), device=theta.device, dtype=torch.float32)
-               if out is None else out)
+               if out is None else _need(out, (B, self.ny, self.nx), "out"))
         _check(self._lib.gl_model_image(self._h, _ptr(theta), B, _ptr(out), defl,
                                         _stream_ptr(stream)))
         return out
@@ -407,6 +424,7 @@ class Hmc:
         self._h = h
 
     def set_inv_mass(self, inv_mass, stream=None):
+        _need(inv_mass.contiguous(), (self.P,), "inv_mass")
         _check(self._lib.gl_hmc_set_inv_mass(self._h, _ptr(inv_mass.contiguous()),
                                              _stream_ptr(stream)))
 
@@ -456,6 +474,8 @@ class Multi:
         self._lib = load()
         self.systems = list(systems)
         self.rows = [int(r) for r in rows]
+        if len(self.rows) != len(self.systems):
+            raise ValueError("one row count per system")
         hs = (_VP * len(self.systems))(*[s.handle for s in self.systems])
         rs = (ctypes.c_int * len(self.rows))(*self.rows)
         h = _VP()
@@ -468,11 +488,19 @@ class Multi:
         """thetas: list of CUDA float32 [rows_k, P_k]; returns lists of logp, grad."""
         torch = _torch()
         n = len(self.systems)
-        thetas = [t.contiguous() for t in thetas]
+        if len(thetas) != n:
+            raise ValueError(f"need one theta per system ({n})")
+        thetas = [_need(t.contiguous(), (r, s.P), f"thetas[{k}]")
+                  for k, (t, r, s) in enumerate(zip(thetas, self.rows, self.systems))]
         if logps is None:
             logps = [torch.empty(t.shape[0], device=t.device, dtype=torch.float32) for t in thetas]
         if grads is None:
             grads = [torch.empty_like(t) for t in thetas]
+        if len(logps) != n or len(grads) != n:
+            raise ValueError(f"need one logp and one grad buffer per system ({n})")
+        for k, (t, lp_k, g_k) in enumerate(zip(thetas, logps, grads)):
+            _need(lp_k, (t.shape[0],), f"logps[{k}]")
+            _need(g_k, tuple(t.shape), f"grads[{k}]")
         tp = (_VP * n)(*[_ptr(t) for t in thetas])
         lp = (_VP * n)(*[_ptr(t) for t in logps])
         gp = (_VP * n)(*[_ptr(t) for t in grads])

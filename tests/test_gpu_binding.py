@@ -1,0 +1,73 @@
+"""The binding rejects buffers that the library would access out of bounds:
+a wrong shape, dtype or device raises before anything is launched, and valid
+caller-provided buffers give the same results as the allocating calls."""
+import numpy as np
+import pytest
+
+from lenscase import make_case, small_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_2606_30633_b300 import build
+    build.build()
+    import paper_2606_30633_b300 as gl
+    c = make_case(small_workload(16, 16, 2, 5, 1, 1, seed=31))
+    S = c.gpu_system()
+    th = torch.tensor(c.theta(4), dtype=torch.float32, device="cuda")
+    return torch, gl, S, th
+
+
+def test_wrong_buffers_are_rejected(env):
+    torch, gl, S, th = env
+    B, P = th.shape
+    dev = "cuda"
+    short = torch.empty(B - 1, device=dev)
+    with pytest.raises(ValueError):
+        S.logp(th, out=short)
+    with pytest.raises(ValueError):
+        S.logp_grad(th, out=short)
+    with pytest.raises(ValueError):
+        S.logp_grad(th, grad=torch.empty(B, P - 1, device=dev))
+    with pytest.raises(ValueError):
+        S.logp_grad_noalloc(th, grad=torch.empty(B - 1, P, device=dev))
+    with pytest.raises(ValueError):
+        S.model_image(th, out=torch.empty(B, 16, 15, device=dev))
+    with pytest.raises(TypeError):
+        S.logp(th, out=torch.empty(B, device=dev, dtype=torch.float64))
+    with pytest.raises(TypeError):
+        S.logp(th, out=torch.empty(B))  # host memory
+    with pytest.raises(ValueError):
+        S.logp_grad_host(np.zeros((B, P + 1), np.float32))
+    u = S.bijector_inverse(th)
+    with pytest.raises(ValueError):
+        S.map_adam(u, torch.zeros(B - 1, P, device=dev), torch.zeros_like(u), 1)
+    hmc = gl.Hmc(S, u, 2, 1e-3)
+    with pytest.raises(ValueError):
+        hmc.set_inv_mass(torch.ones(P - 1, device=dev))
+    hmc.close()
+    out, grad = torch.empty(B, device=dev), torch.empty_like(th)
+    S.logp_grad(th, out=out, grad=grad)
+    lp, g = S.logp_grad(th)
+    assert torch.equal(out, lp) and torch.equal(grad, g)
+
+
+def test_multi_rejects_mismatched_buffers(env):
+    torch, gl, S, th = env
+    with pytest.raises(ValueError):
+        gl.Multi([S, S], [4])
+    plan = gl.Multi([S, S], [4, 2])
+    with pytest.raises(ValueError):
+        plan.logp_grad([th])
+    with pytest.raises(ValueError):
+        plan.logp_grad([th, th[:1]])
+    with pytest.raises(ValueError):
+        plan.logp_grad([th, th[:2]], logps=[torch.empty(3, device="cuda"),
+                                            torch.empty(2, device="cuda")])
+    lps, gs = plan.logp_grad([th, th[:2]])
+    lp, g = S.logp_grad(th)
+    assert torch.equal(lps[0], lp) and torch.equal(gs[0], g)
+    assert torch.equal(lps[1], lp[:2]) and torch.equal(gs[1], g[:2])
