@@ -547,7 +547,8 @@ class Surrogate:
     @classmethod
     def from_params(cls, params):
         p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
-        assert p.size == cls.num_params()
+        if p.size != cls.num_params():
+            raise ValueError(f"the surrogate has {cls.num_params()} parameters, not {p.size}")
         h = _VP()
         _check(load().gl_surrogate_create(p.ctypes.data, ctypes.byref(h)))
         return cls(h)
@@ -569,7 +570,7 @@ class Surrogate:
     def infer(self, x, stream=None):
         """x: CUDA float32 [N, 4] raw (q, gamma, log R/theta_E, vphi) -> F [N, 2]."""
         torch = _torch()
-        x = x.contiguous()
+        x = _need(x.contiguous(), (x.shape[0], 4) if x.dim() == 2 else (-1, 4), "x")
         y = torch.empty((x.shape[0], 2), device=x.device, dtype=torch.float32)
         _check(self._lib.gl_surrogate_infer(self._h, _ptr(x), x.shape[0], _ptr(y),
                                             _stream_ptr(stream)))
@@ -578,7 +579,9 @@ class Surrogate:
     def loss_grad(self, x, target):
         """Mean squared loss and its parameter gradient (x [N, 4], target [N, 2]
         CUDA float32; N a multiple of 128)."""
-        x, target = x.contiguous(), target.contiguous()
+        N = x.shape[0] if x.dim() == 2 else -1
+        x = _need(x.contiguous(), (N, 4), "x")
+        target = _need(target.contiguous(), (N, 2), "target")
         loss = np.empty(1, dtype=np.float32)
         grad = np.empty(self.num_params(), dtype=np.float32)
         _check(self._lib.gl_surrogate_loss_grad(self._h, _ptr(x), _ptr(target), x.shape[0],
@@ -601,7 +604,7 @@ def series_F(x, stream=None):
     """The exact F of the EPL series in FP64 on the device (gl_series_F):
     x CUDA float32 [N, 4] raw (q, gamma, ., vphi) -> F [N, 2] (Re, Im)."""
     torch = _torch()
-    x = x.contiguous()
+    x = _need(x.contiguous(), (x.shape[0], 4) if x.dim() == 2 else (-1, 4), "x")
     F = torch.empty((x.shape[0], 2), device=x.device, dtype=torch.float32)
     _check(load().gl_series_F(_ptr(x), x.shape[0], _ptr(F), _stream_ptr(stream)))
     return F

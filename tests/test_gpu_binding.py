@@ -71,3 +71,20 @@ def test_multi_rejects_mismatched_buffers(env):
     lp, g = S.logp_grad(th)
     assert torch.equal(lps[0], lp) and torch.equal(gs[0], g)
     assert torch.equal(lps[1], lp[:2]) and torch.equal(gs[1], g[:2])
+
+
+def test_network_calls_reject_wrong_shapes(env):
+    torch, gl, S, th = env
+    x = torch.rand(256, 3, device="cuda")
+    with pytest.raises(ValueError):
+        gl.series_F(x)
+    with pytest.raises(ValueError):
+        gl.Surrogate.from_params(np.zeros(7, np.float32))
+    sur = gl.Surrogate.from_params(np.zeros(gl.Surrogate.num_params(), np.float32))
+    with pytest.raises(ValueError):
+        sur.infer(x)
+    with pytest.raises(ValueError):
+        sur.loss_grad(torch.rand(256, 4, device="cuda"), torch.rand(255, 2, device="cuda"))
+    y = sur.infer(torch.rand(256, 4, device="cuda") + 0.5)
+    assert y.shape == (256, 2) and bool(torch.isfinite(y).all())
+    sur.close()
