@@ -832,22 +832,127 @@ def run_pipeline(args) -> dict | None:
     return out
 
 
+def run_fit(args) -> dict | None:
+    """The whole inference pipeline of Sec. 3 with the hyperparameter table of
+    the hundred simulated systems (Sec. 4.2) on the ground-based system
+    (100x100 px, s = 3): multi-start MAP from 2000 prior draws for 1000 Adam
+    steps, SVI with 1000 draws for 5000 AdaBelief steps, then HMC with 64
+    chains (500 burn-in transitions with step-size and mass adaptation, the
+    step-size retune, 1500 samples, 10 leapfrogs each). A step is one whole
+    fit (infer.fit); warm-up steps are fits with 1 % of the iterations. The
+    value is whole-job fits per hour; each rank fits its own copy."""
+    import torch
+    import paper_2606_30633_b300 as gl
+    from paper_2606_30633_b300 import build as glbuild, infer
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    glbuild.build()
+    dev = torch.device("cuda", local)
+    W = synth.ground_100()
+    spec = W.prior()
+    blank = gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
+                      np.ones((W.ny, W.nx)), W.psf, 1, 1, spec)
+    truth = W.truth()
+    m = blank.model_image(torch.tensor(truth[None], dtype=torch.float32, device=dev))[0]
+    blank.close()
+    d, sig = synth.noisy_data(m.double().cpu().numpy(), W.noise())
+    S = gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, d, sig, W.psf, 1, 1, spec)
+    n_map = 2000
+    starts_np = synth.draw(spec, n_map, W.seed_samples, 1, 1).astype(np.float32)
+    starts = torch.tensor(starts_np, device=dev)
+    hp = dict(map_steps=1000, n_vi=1000, svi_steps=5000, n_chains=64, n_burnin=500,
+              n_samples=1500, n_leapfrog=10)
+    small = dict(map_steps=10, n_vi=1000, svi_steps=50, n_chains=64, n_burnin=5,
+                 n_samples=15, n_leapfrog=10)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for k in range(args.warmup):
+        infer.fit(S, starts, seed=100 + k, **small)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    secs, stages, results = [], [], []
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = infer.fit(S, starts, seed=k, **hp)
+            torch.cuda.synchronize()
+            secs.append(time.perf_counter() - t0)
+            stages.append(r.seconds)
+            results.append(r)
+    t_s = max_over_ranks(sum(secs) * 1e3, world, dev) / 1e3
+    value = world * args.steps / t_s * 3600.0
+    # end to end: the starts from pinned host memory, the draws back to host memory
+    h_starts = starts.cpu().pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r_e = infer.fit(S, h_starts.to(dev, non_blocking=True), seed=999, **hp)
+    draws_host = r_e.hmc.draws.cpu()
+    e2e_s = time.perf_counter() - t0
+    last = results[-1]
+    th_mean = last.hmc.draws.double().mean((0, 1)).cpu().numpy()
+    th_sd = last.hmc.draws.double().std((0, 1)).cpu().numpy()
+    evals = {"map": n_map * hp["map_steps"], "svi": hp["n_vi"] * hp["svi_steps"],
+             "hmc": hp["n_chains"] * hp["n_leapfrog"]
+             * (hp["n_burnin"] + hp["n_burnin"] // 2 + hp["n_samples"])}
+    mean_stage = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
+    out = None
+    if rank == 0:
+        out = {
+            "metric": "whole fits per hour (MAP 2000 starts x 1000 steps, SVI 1000 draws x "
+                      "5000 steps, HMC 64 chains x (500 + 250 retune + 1500) transitions of 10 "
+                      "leapfrogs; 100x100 px, 3x SS) on 1 B300",
+            "value": value, "unit": "fits/h", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded priors, library-rendered truth, seeded noise)",
+            "config": {"workload": "fit-" + W.name, **hp, "n_map": n_map,
+                       "l2": "flushed (256 MB write) before every timed fit"},
+            "stages_s": mean_stage,
+            "stage_evals_per_s": {k: evals[k] / mean_stage[k] for k in evals},
+            "map_best_logp": last.map_logp,
+            "hmc": {"rhat_max": float(np.max(last.hmc.rhat)),
+                    "ess_min": float(np.min(last.hmc.ess)),
+                    "mean_accept": float(np.mean(last.hmc.accept)),
+                    "step_size": last.hmc.step_size,
+                    "truth_within_sd": float(np.max(np.abs(th_mean - truth) / th_sd))},
+            "e2e": {"value": 3600.0 / e2e_s * world, "unit": "fits/h",
+                    "h2d_bytes_per_step": n_map * W.P * 4,
+                    "d2h_bytes_per_step": int(draws_host.numel() * 4)},
+            "gpu_launches": args.steps * (2 * hp["map_steps"] + 4 * hp["svi_steps"]
+                                          + (2 * hp["n_leapfrog"] + 4)
+                                          * (hp["n_burnin"] + hp["n_burnin"] // 2
+                                             + hp["n_samples"])),
+            "clocks": clk.summary(),
+        }
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default 50; 20 for space200-leapfrog, about 40 s)")
+                    help="timed steps (default 50; 20 for space200-leapfrog, about 40 s; "
+                         "1 whole fit for fit)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=None,
                     help="rows per step (rows per system for uneven; default: the "
                          "workload's); for profiling runs")
-    ap.add_argument("--workload", choices=["ground100", "space200-leapfrog", "uneven", "pipeline"],
+    ap.add_argument("--workload", choices=["ground100", "space200-leapfrog", "uneven", "pipeline",
+                                           "fit"],
                     default="ground100")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 20 if args.workload == "space200-leapfrog" else 50
+        args.steps = {"space200-leapfrog": 20, "fit": 1}.get(args.workload, 50)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -858,6 +963,8 @@ def main():
         res = run_uneven(args)
     elif args.workload == "pipeline":
         res = run_pipeline(args)
+    elif args.workload == "fit":
+        res = run_fit(args)
     else:
         res = run_ours(args)
     if res is not None:

@@ -406,6 +406,25 @@ def svi_grad(mu, L, z, logp_u: Callable):
     return w.mean(), g_mu, g_L
 
 
+def svi_grad_pathwise(mu, L, z, logp_grad_u: Callable):
+    """ELBO estimate and its reparameterisation (pathwise) gradient, the
+    gradient that automatic differentiation of the sampled ELBO gives
+    (Sec. 3.2 states the gradient is taken that way). With u_i = mu + L z_i,
+    log q(u_i) = -|z_i|^2/2 - sum log L_jj - const does not depend on mu, so
+      grad_mu ELBO = -mean_i g_i,   grad_L ELBO = -tril(mean_i g_i z_i^T) - diag(1/L_jj),
+    g_i = grad_u log p~(u_i). Both estimators have the same expectation."""
+    u = mu[None, :] + z @ L.T
+    P = mu.size
+    lp, g = logp_grad_u(u)
+    logq = (-0.5 * np.sum(z * z, axis=1) - np.sum(np.log(np.abs(np.diag(L))))
+            - 0.5 * P * math.log(2.0 * math.pi))
+    w = logq - lp
+    n = z.shape[0]
+    g_mu = -g.sum(0) / n
+    g_L = -np.tril(g.T @ z / n) - np.diag(1.0 / np.diag(L))
+    return w.mean(), g_mu, g_L
+
+
 # ----------------------------------------------------------- diagnostics --
 def rhat(samples: np.ndarray) -> np.ndarray:
     """Potential scale reduction factor (Gelman et al. 2014, BDA3 Sec. 11.4,

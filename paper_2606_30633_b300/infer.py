@@ -9,7 +9,8 @@ gl_hmc_*); this module chooses the phases and moves the draws to the host.
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass
+import time
+from dataclasses import dataclass, field
 from typing import Optional
 
 import numpy as np
@@ -104,6 +105,25 @@ def svi_unpack(system: System, phi):
     return mu, L
 
 
+def svi_fit(system: System, mu0, n_samples: int, n_steps: int, lr: float = 1e-4,
+            scale: float = 1e-3, seed: int = 0, defl: int = GL_DEFL_SERIES, chunk: int = 100):
+    """SVI (Sec. 3.2) from q = N(mu0, scale^2 I): n_steps AdaBelief steps with
+    the paper's defaults (lr 1e-4, b1 0.95, b2 0.99), n_samples draws each, in
+    graph-captured chunks. Returns (mu [P], L [P, P], per-step ELBO estimates)."""
+    torch = _torch()
+    phi, opt = svi_init(system, mu0, scale)
+    elbo = []
+    done = 0
+    while done < n_steps:
+        k = min(chunk, n_steps - done)
+        elbo.append(system.svi_adabelief(phi, opt, n_samples, k, t0=done, lr=lr, seed=seed,
+                                         defl=defl))
+        done += k
+    mu, L = svi_unpack(system, phi)
+    e = torch.cat(elbo).cpu().numpy() if elbo else np.zeros(0)
+    return mu.clone(), L, e
+
+
 @dataclass
 class HmcResult:
     draws: "object"          # device tensor [n_samples, B, P] (theta)
@@ -152,3 +172,60 @@ def hmc_sample(system: System, u0, n_burnin: int, n_samples: int, n_leapfrog: in
         h.close()
     d = draws.double().cpu().numpy()
     return HmcResult(draws, acc.cpu().numpy(), eps, im.cpu().numpy(), rhat(d), ess(d))
+
+
+@dataclass
+class FitResult:
+    map_u: "object"                  # best MAP point, device [P] (unconstrained)
+    map_logp: float                  # its log p~
+    svi_mu: "object"                 # device [P]
+    svi_L: "object"                  # device [P, P], lower triangular
+    svi_elbo: np.ndarray             # per-step estimates of E_q[log q - log p~]
+    hmc: HmcResult
+    seconds: dict = field(default_factory=dict)   # wall-clock per stage
+
+
+def fit(system: System, theta_starts, map_steps: int = 1000, map_lr: float = 1e-2,
+        n_vi: int = 1000, svi_steps: int = 5000, svi_lr: float = 1e-4, svi_scale: float = 1e-3,
+        n_chains: int = 64, n_burnin: int = 500, n_samples: int = 1500, n_leapfrog: int = 10,
+        step_size: float = 0.1, seed: int = 0, defl: int = GL_DEFL_SERIES) -> FitResult:
+    """The pipeline of Sec. 3, stage after stage. The defaults are the
+    hyperparameter table of the hundred simulated systems (Sec. 4.2; n_MAP is
+    the number of rows of theta_starts, 2000 there):
+      1. multi-start MAP: Adam from every row of theta_starts (device [n_MAP, P],
+         e.g. prior draws) for map_steps; the row with the highest log p~ wins;
+      2. SVI: AdaBelief on a full-covariance Gaussian q started at the MAP point,
+         n_vi draws per step for svi_steps;
+      3. HMC: n_chains chains started from draws of q, with q's marginal
+         variances as the first inverse mass, burn-in with step-size and mass
+         adaptation (hmc_sample), then n_samples transitions, R-hat and ESS.
+    Every step runs in libgl; this function only orders them. The chains'
+    start draws u0 = mu + L z use torch's generator (seeded)."""
+    torch = _torch()
+    sec = {}
+
+    def now():
+        torch.cuda.synchronize()
+        return time.perf_counter()
+
+    t0 = now()
+    u_map, lp_map = map_fit(system, system.bijector_inverse(theta_starts), map_steps, map_lr,
+                            defl)
+    lp = lp_map.cpu().numpy().astype(np.float64)
+    lp[~np.isfinite(lp)] = -np.inf
+    best = int(np.argmax(lp))
+    t1 = now()
+    sec["map"] = t1 - t0
+    mu, L, elbo = svi_fit(system, u_map[best].contiguous(), n_vi, svi_steps, svi_lr, svi_scale,
+                          seed, defl)
+    t2 = now()
+    sec["svi"] = t2 - t1
+    g = torch.Generator(device=mu.device)
+    g.manual_seed(seed)
+    z = torch.randn(n_chains, system.P, device=mu.device, generator=g)
+    u0 = (mu[None, :] + z @ L.T).contiguous()
+    inv_mass = (L * L).sum(1).contiguous()
+    res = hmc_sample(system, u0, n_burnin, n_samples, n_leapfrog, step_size, seed=seed + 1,
+                     defl=defl, inv_mass=inv_mass)
+    sec["hmc"] = now() - t2
+    return FitResult(u_map[best].clone(), float(lp[best]), mu, L, elbo, res, sec)

@@ -109,6 +109,9 @@ PY_MUTANTS = [
     ("infer", "SVI L-gradient diagonal", "g_L = np.tril(g_L) - np.diag(w.mean() / np.diag(L))",
      "g_L = np.tril(g_L)"),
     ("infer", "SVI score transposed", "a = np.linalg.solve(L.T, z.T).T", "a = np.linalg.solve(L, z.T).T"),
+    ("infer", "pathwise mu-gradient sign", "g_mu = -g.sum(0) / n", "g_mu = g.sum(0) / n"),
+    ("infer", "pathwise entropy term", "g_L = -np.tril(g.T @ z / n) - np.diag(1.0 / np.diag(L))",
+     "g_L = -np.tril(g.T @ z / n)"),
     ("infer", "R-hat between-chain variance",
      "B = N / (M - 1) * ((cm - cm.mean(axis=0)) ** 2).sum(axis=0)",
      "B = 1.0 / (M - 1) * ((cm - cm.mean(axis=0)) ** 2).sum(axis=0)"),
