@@ -924,7 +924,7 @@ def run_fit(args) -> dict | None:
             "e2e": {"value": 3600.0 / e2e_s * world, "unit": "fits/h",
                     "h2d_bytes_per_step": n_map * W.P * 4,
                     "d2h_bytes_per_step": int(draws_host.numel() * 4)},
-            "gpu_launches": args.steps * (2 * hp["map_steps"] + 4 * hp["svi_steps"]
+            "gpu_launches": args.steps * (2 * hp["map_steps"] + 5 * hp["svi_steps"]
                                           + (2 * hp["n_leapfrog"] + 4)
                                           * (hp["n_burnin"] + hp["n_burnin"] // 2
                                              + hp["n_samples"])),

@@ -103,9 +103,14 @@ SIGNATURES = {
                                         ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_float, ctypes.c_ulonglong, _VP, ctypes.c_int,
                                         _VP]),
+    "gl_svi_adabelief_ex": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                           ctypes.c_float, ctypes.c_float, ctypes.c_ulonglong,
+                                           _VP, ctypes.c_int, ctypes.c_int, _VP]),
 }
 
 GL_HMC_ADAPT_STEP, GL_HMC_COLLECT_MOMENTS = 1, 2
+GL_SVI_SCORE, GL_SVI_PATHWISE = 0, 1
 
 
 class gl_hmc_desc(ctypes.Structure):
@@ -334,10 +339,12 @@ class System:
     def svi_adabelief(self, phi, opt, n_samples: int, n_steps: int, t0: int = 0,
                       lr: float = 1e-4, beta1: float = 0.95, beta2: float = 0.99,
                       eps: float = 1e-16, seed: int = 0, defl: int = GL_DEFL_SERIES,
-                      stream=None):
+                      stream=None, estimator: int = GL_SVI_SCORE):
         """n_steps of SVI (AdaBelief on phi = (mu, L with log diagonal)) in
-        place; opt is AdaBelief's state [2 (P + P^2)]. Returns the per-step
-        ELBO estimates [n_steps]."""
+        place; opt is AdaBelief's state [2 (P + P^2)]. estimator:
+        GL_SVI_SCORE (the printed score-function gradient) or GL_SVI_PATHWISE
+        (the reparameterisation gradient; see gl_svi_adabelief_ex). Returns the
+        per-step ELBO estimates [n_steps]."""
         torch = _torch()
         P = self.P
         if phi.shape != (P + P * P,) or opt.shape != (2 * (P + P * P),):
@@ -346,10 +353,10 @@ class System:
             if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
                 raise TypeError("phi and opt must be contiguous CUDA float32 tensors")
         elbo = torch.empty(max(int(n_steps), 1), device=phi.device, dtype=torch.float32)
-        _check(self._lib.gl_svi_adabelief(self._h, _ptr(phi), _ptr(opt), int(n_samples),
-                                          int(n_steps), int(t0), float(lr), float(beta1),
-                                          float(beta2), float(eps), int(seed), _ptr(elbo), defl,
-                                          _stream_ptr(stream)))
+        _check(self._lib.gl_svi_adabelief_ex(self._h, _ptr(phi), _ptr(opt), int(n_samples),
+                                             int(n_steps), int(t0), float(lr), float(beta1),
+                                             float(beta2), float(eps), int(seed), _ptr(elbo),
+                                             defl, int(estimator), _stream_ptr(stream)))
         return elbo[:int(n_steps)]
 
     def logp_grad_backward(self, theta, defl: int = GL_DEFL_SERIES, stream=None):

@@ -739,10 +739,58 @@ __global__ void k_svi_sums(int P, int n, const float* __restrict__ a, const floa
   }
 }
 
+// The same outputs for the reparameterisation (pathwise) gradient: k < P
+// gives sum_i g_ik, then the lower triangle (j, c) sum_i g_ij z_ic, then
+// sum_i w_i and the count, with g_i = grad_u log p~(u_i) and
+// w_i = log q_i - log p~_i; samples with a non-finite w_i are left out.
+__global__ void k_svi_sums_rep(int P, int n, const float* __restrict__ g,
+                               const float* __restrict__ z, const float* __restrict__ logq,
+                               const float* __restrict__ lpu, double* __restrict__ sums) {
+  __shared__ double red[8], redc[8];
+  const int out = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int nL = P * (P + 1) / 2;
+  int mode, j = 0, c = 0;
+  if (out < P) {
+    mode = 0;
+    j = out;
+  } else if (out < P + nL) {
+    mode = 1;
+    int r = out - P;
+    j = 0;
+    while (r > j) { r -= j + 1; ++j; }
+    c = r;
+  } else {
+    mode = 2;
+  }
+  double s = 0.0, cnt = 0.0;
+  for (int i = t; i < n; i += blockDim.x) {
+    const double wi = (double)logq[i] - (double)lpu[i];
+    if (!isfinite(wi)) continue;
+    const size_t o = (size_t)i * P;
+    if (mode == 0) s += (double)g[o + j];
+    else if (mode == 1) s += (double)g[o + j] * z[o + c];
+    else { s += wi; cnt += 1.0; }
+  }
+  s = warp_sum(s);
+  cnt = warp_sum(cnt);
+  if (lane == 0) { red[w] = s; redc[w] = cnt; }
+  __syncthreads();
+  if (t == 0) {
+    double a1 = 0.0, a2 = 0.0;
+    for (int q = 0; q < 8; ++q) { a1 += red[q]; a2 += redc[q]; }
+    sums[out] = a1;
+    if (mode == 2) sums[out + 1] = a2;
+  }
+}
+
 // One AdaBelief step (Zhuang et al. 2020) on phi = (mu, L with log diagonal),
 // minimising the ELBO loss, from the sums; records the ELBO estimate.
+// rep = 0: score-function sums (k_svi_sums), gradients
+//   mu: S_k/n, L_jc: S_jc/n, log L_jj: L_jj S_jj/n - W/n;
+// rep = 1: pathwise sums (k_svi_sums_rep), gradients
+//   mu: -S_k/n, L_jc: -S_jc/n, log L_jj: -L_jj S_jj/n - 1.
 __global__ void k_svi_update(int P, float* __restrict__ phi, float* __restrict__ opt,
-                             const double* __restrict__ sums, SviCtl* __restrict__ ctl) {
+                             const double* __restrict__ sums, SviCtl* __restrict__ ctl, int rep) {
   const int nL = P * (P + 1) / 2;
   const double W = sums[P + nL], cnt = sums[P + nL + 1];
   const int np = P + P * P;
@@ -752,15 +800,16 @@ __global__ void k_svi_update(int P, float* __restrict__ phi, float* __restrict__
   const double t = (double)c.step + 1.0;
   const double bc1 = 1.0 - pow((double)c.b1, t), bc2 = 1.0 - pow((double)c.b2, t);
   for (int idx = threadIdx.x; idx < np; idx += blockDim.x) {
+    const double sgn = rep ? -1.0 : 1.0;
     double g;
     if (idx < P) {
-      g = sums[idx] / cnt;
+      g = sgn * sums[idx] / cnt;
     } else {
       const int q = idx - P, j = q / P, k = q - j * P;
       if (k > j) continue;  // upper triangle: not a parameter
       const int tri = j * (j + 1) / 2 + k;
-      g = sums[P + tri] / cnt;
-      if (k == j) g = g * exp((double)phi[idx]) - W / cnt;  // d/d log L_jj
+      g = sgn * sums[P + tri] / cnt;
+      if (k == j) g = g * exp((double)phi[idx]) - (rep ? 1.0 : W / cnt);  // d/d log L_jj
     }
     if (!(cnt > 0.0) || !isfinite(g)) continue;
     const double mk = (double)c.b1 * m[idx] + (1.0 - c.b1) * g;
@@ -974,7 +1023,7 @@ struct InferState {
     float *phi, *opt;
     void *scratch, *table;
     const void* sur;
-    int n, defl;
+    int n, defl, est;
     unsigned long long seed;
   } svi_key{};
   float* svi_buf = nullptr;
@@ -1403,6 +1452,14 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
                            int t0, float lr, float beta1, float beta2, float eps,
                            unsigned long long seed, float* elbo, gl_deflection defl,
                            void* stream) {
+  return gl_svi_adabelief_ex(sys, phi, opt, n_samples, n_steps, t0, lr, beta1, beta2, eps, seed,
+                             elbo, defl, GL_SVI_SCORE, stream);
+}
+
+gl_status gl_svi_adabelief_ex(gl_system* sys, float* phi, float* opt, int n_samples, int n_steps,
+                              int t0, float lr, float beta1, float beta2, float eps,
+                              unsigned long long seed, float* elbo, gl_deflection defl,
+                              int estimator, void* stream) {
   gl::Range nvtx_range("gl_svi_adabelief");
   if (!sys) return fail(GL_EINVAL, "system is NULL");
   if (n_samples < 1 || n_steps < 0 || t0 < 0)
@@ -1411,7 +1468,10 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
       !(eps > 0.f))
     return fail(GL_EINVAL, "need lr > 0, 0 <= beta < 1, eps > 0");
   if (!phi || !opt) return fail(GL_EINVAL, "NULL phi or opt");
+  if (estimator != GL_SVI_SCORE && estimator != GL_SVI_PATHWISE)
+    return fail(GL_EINVAL, "unknown SVI gradient estimator");
   if (n_steps == 0) return GL_OK;
+  const bool rep = estimator == GL_SVI_PATHWISE;
   gl_status r = set_dev(sys);
   if (r != GL_OK) return r;
   gl::InferState* f;
@@ -1419,9 +1479,9 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
   SysParams sp;
   size_t dyn;
   const int n = n_samples, P = sys->sp.P;
-  if ((r = gl::eval_prepare(sys, n, defl, false, &sp, &dyn)) != GL_OK) return r;
+  if ((r = gl::eval_prepare(sys, n, defl, rep, &sp, &dyn)) != GL_OK) return r;
   const size_t nP = (size_t)n * P;
-  const size_t need = 4 * nP + 3 * (size_t)n;
+  const size_t need = 6 * nP + 4 * (size_t)n;
   if (need > f->svi_buf_floats) {
     if (f->svi_exec) {
       cudaGraphExecDestroy(f->svi_exec);
@@ -1444,16 +1504,19 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
   float* a = z + nP;
   float* u = a + nP;
   float* th = u + nP;
-  float* logq = th + nP;
+  float* gth = th + nP;   // pathwise: d log p / d theta
+  float* gu = gth + nP;   // pathwise: d log p~ / d u
+  float* logq = gu + nP;
   float* lp = logq + n;
   float* lj = lp + n;
+  float* lpu = lj + n;    // pathwise: log p~(u)
   gl::InferState::SviKey key;
   std::memset(&key, 0, sizeof key);
   key.phi = phi; key.opt = opt;
   key.scratch = sp.scratch;
   key.table = const_cast<float4*>(sp.table);
   key.sur = sys->sur;
-  key.n = n; key.defl = (int)defl; key.seed = seed;
+  key.n = n; key.defl = (int)defl; key.seed = seed; key.est = estimator;
   if (!f->svi_exec || std::memcmp(&key, &f->svi_key, sizeof key) != 0) {
     if (f->svi_exec) {
       cudaGraphExecDestroy(f->svi_exec);
@@ -1464,13 +1527,21 @@ gl_status gl_svi_adabelief(gl_system* sys, float* phi, float* opt, int n_samples
     k_svi_draw<<<grid_rows(n), 256, 0, f->cap>>>(f->bij, P, n, f->svi_ctl, seed, phi, z, a, logq,
                                                   u, th, lj);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = gl::eval_launch(sys, sp, dyn, th, n, lp, nullptr, defl, f->cap);
-    if (e == cudaSuccess) {
-      k_svi_sums<<<nsums - 1, 256, 0, f->cap>>>(P, n, a, z, logq, lp, lj, f->svi_sums);
+    if (e == cudaSuccess)
+      e = gl::eval_launch(sys, sp, dyn, th, n, lp, rep ? gth : nullptr, defl, f->cap);
+    if (e == cudaSuccess && rep) {
+      k_pullback<<<grid_rows(n), 256, 0, f->cap>>>(f->bij, P, u, n, lp, gth, lpu, gu);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-      k_svi_update<<<1, 256, 0, f->cap>>>(P, phi, opt, f->svi_sums, f->svi_ctl);
+      if (rep)
+        k_svi_sums_rep<<<nsums - 1, 256, 0, f->cap>>>(P, n, gu, z, logq, lpu, f->svi_sums);
+      else
+        k_svi_sums<<<nsums - 1, 256, 0, f->cap>>>(P, n, a, z, logq, lp, lj, f->svi_sums);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      k_svi_update<<<1, 256, 0, f->cap>>>(P, phi, opt, f->svi_sums, f->svi_ctl, rep ? 1 : 0);
       e = cudaGetLastError();
     }
     cudaGraph_t g = nullptr;

@@ -15,8 +15,8 @@ from typing import Optional
 
 import numpy as np
 
-from . import (GL_DEFL_SERIES, GL_HMC_ADAPT_STEP, GL_HMC_COLLECT_MOMENTS, Hmc, System,
-               _torch)
+from . import (GL_DEFL_SERIES, GL_HMC_ADAPT_STEP, GL_HMC_COLLECT_MOMENTS, GL_SVI_PATHWISE, Hmc,
+               System, _torch)
 
 
 # ----------------------------------------------------------- diagnostics --
@@ -106,10 +106,13 @@ def svi_unpack(system: System, phi):
 
 
 def svi_fit(system: System, mu0, n_samples: int, n_steps: int, lr: float = 1e-4,
-            scale: float = 1e-3, seed: int = 0, defl: int = GL_DEFL_SERIES, chunk: int = 100):
+            scale: float = 1e-3, seed: int = 0, defl: int = GL_DEFL_SERIES, chunk: int = 100,
+            estimator: int = GL_SVI_PATHWISE):
     """SVI (Sec. 3.2) from q = N(mu0, scale^2 I): n_steps AdaBelief steps with
     the paper's defaults (lr 1e-4, b1 0.95, b2 0.99), n_samples draws each, in
-    graph-captured chunks. Returns (mu [P], L [P, P], per-step ELBO estimates)."""
+    graph-captured chunks, with the reparameterisation gradient by default
+    (the gradient automatic differentiation of the sampled ELBO gives).
+    Returns (mu [P], L [P, P], per-step ELBO estimates)."""
     torch = _torch()
     phi, opt = svi_init(system, mu0, scale)
     elbo = []
@@ -117,7 +120,7 @@ def svi_fit(system: System, mu0, n_samples: int, n_steps: int, lr: float = 1e-4,
     while done < n_steps:
         k = min(chunk, n_steps - done)
         elbo.append(system.svi_adabelief(phi, opt, n_samples, k, t0=done, lr=lr, seed=seed,
-                                         defl=defl))
+                                         defl=defl, estimator=estimator))
         done += k
     mu, L = svi_unpack(system, phi)
     e = torch.cat(elbo).cpu().numpy() if elbo else np.zeros(0)
@@ -188,14 +191,17 @@ class FitResult:
 def fit(system: System, theta_starts, map_steps: int = 1000, map_lr: float = 1e-2,
         n_vi: int = 1000, svi_steps: int = 5000, svi_lr: float = 1e-4, svi_scale: float = 1e-3,
         n_chains: int = 64, n_burnin: int = 500, n_samples: int = 1500, n_leapfrog: int = 10,
-        step_size: float = 0.1, seed: int = 0, defl: int = GL_DEFL_SERIES) -> FitResult:
+        step_size: float = 0.1, seed: int = 0, defl: int = GL_DEFL_SERIES,
+        svi_estimator: int = GL_SVI_PATHWISE) -> FitResult:
     """The pipeline of Sec. 3, stage after stage. The defaults are the
     hyperparameter table of the hundred simulated systems (Sec. 4.2; n_MAP is
     the number of rows of theta_starts, 2000 there):
       1. multi-start MAP: Adam from every row of theta_starts (device [n_MAP, P],
          e.g. prior draws) for map_steps; the row with the highest log p~ wins;
       2. SVI: AdaBelief on a full-covariance Gaussian q started at the MAP point,
-         n_vi draws per step for svi_steps;
+         n_vi draws per step for svi_steps (reparameterisation gradient by
+         default; GL_SVI_SCORE gives the printed score-function form, which is
+         mostly noise on narrow lensing posteriors);
       3. HMC: n_chains chains started from draws of q, with q's marginal
          variances as the first inverse mass, burn-in with step-size and mass
          adaptation (hmc_sample), then n_samples transitions, R-hat and ESS.
@@ -217,7 +223,7 @@ def fit(system: System, theta_starts, map_steps: int = 1000, map_lr: float = 1e-
     t1 = now()
     sec["map"] = t1 - t0
     mu, L, elbo = svi_fit(system, u_map[best].contiguous(), n_vi, svi_steps, svi_lr, svi_scale,
-                          seed, defl)
+                          seed, defl, estimator=svi_estimator)
     t2 = now()
     sec["svi"] = t2 - t1
     g = torch.Generator(device=mu.device)
