@@ -29,7 +29,8 @@ def rhat(draws) -> np.ndarray:
     means = x.mean(axis=0)
     within = x.var(axis=0, ddof=1).mean(axis=0)
     between_over_n = means.var(axis=0, ddof=1)
-    return np.sqrt(((N - 1) / N * within + between_over_n) / within)
+    with np.errstate(divide="ignore", invalid="ignore"):  # chains that never moved: inf / nan
+        return np.sqrt(((N - 1) / N * within + between_over_n) / within)
 
 
 def _autocov(c: np.ndarray) -> np.ndarray:
@@ -57,13 +58,17 @@ def ess(draws) -> np.ndarray:
         s2 = ac[0] * N / (N - 1)
         W = s2.mean()
         var_plus = (N - 1) / N * W + (xs.mean(axis=0).var(ddof=1) if M > 1 else 0.0)
-        rho = 1.0 - (W - (s2 * (ac / ac[0])).mean(axis=1)) / var_plus
+        # s2_m rho_{t,m} = s2_m ac_{t,m} / ac_{0,m} = ac_{t,m} N / (N - 1), also for a
+        # chain that never moved (ac = 0); all chains constant gives var+ = 0: nan
+        with np.errstate(divide="ignore", invalid="ignore"):
+            rho = 1.0 - (W - (ac * (N / (N - 1))).mean(axis=1)) / var_plus
         pairs = rho[0:N - 1:2] + rho[1:N:2]
         pos = np.flatnonzero(pairs <= 0)
         pairs = pairs[:pos[0]] if pos.size else pairs
         pairs = np.minimum.accumulate(pairs)
         tau = -1.0 + 2.0 * pairs.sum()
-        out[k] = N * M / tau
+        with np.errstate(divide="ignore", invalid="ignore"):
+            out[k] = N * M / tau
     return out.reshape(tail)
 
 
