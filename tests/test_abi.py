@@ -106,6 +106,8 @@ def test_inference_entry_points_reject_bad_arguments(lib):
                            None) == gl.GL_EINVAL
     assert lib.gl_svi_adabelief(None, None, None, 1, 1, 0, 1e-4, 0.95, 0.99, 1e-16, 0, None, 0,
                                 None) == gl.GL_EINVAL
+    assert lib.gl_svi_adabelief_ex(None, None, None, 1, 1, 0, 1e-4, 0.95, 0.99, 1e-16, 0, None,
+                                   0, gl.GL_SVI_PATHWISE, None) == gl.GL_EINVAL
     h = P()
     assert lib.gl_hmc_create(None, None, None, ctypes.byref(h), None) == gl.GL_EINVAL
     assert h.value is None

@@ -88,3 +88,14 @@ def test_network_calls_reject_wrong_shapes(env):
     y = sur.infer(torch.rand(256, 4, device="cuda") + 0.5)
     assert y.shape == (256, 2) and bool(torch.isfinite(y).all())
     sur.close()
+
+
+def test_unknown_svi_estimator_is_rejected(env):
+    torch, gl, S, th = env
+    from paper_2606_30633_b300 import infer
+    phi, opt = infer.svi_init(S, S.bijector_inverse(th)[0])
+    before = phi.clone()
+    with pytest.raises(gl.GLError) as e:
+        S.svi_adabelief(phi, opt, 8, 1, estimator=7)
+    assert e.value.status == gl.GL_EINVAL
+    assert torch.equal(phi, before)
