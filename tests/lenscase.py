@@ -1,9 +1,12 @@
 """Shared set-up of parity cases: one seeded synthetic lens system handed to
 both the FP64 oracle and the CUDA library with identical (float32-rounded)
-inputs. The noiseless truth is rendered by the oracle only."""
+inputs: parameters, priors, data, noise map, PSF and pixel scale. The
+noiseless truth is rendered by the oracle only."""
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
+import os
 
 import numpy as np
 
@@ -45,6 +48,8 @@ class Case:
 
 
 def make_case(W: synth.Workload, nthreads: int = 0) -> Case:
+    # the library takes the pixel scale as a float: both sides get that value
+    W = dataclasses.replace(W, pixel_scale=float(np.float32(W.pixel_scale)))
     spec = round_spec(W.prior())
     psf = f32(W.psf)
     truth = f32(W.truth())
@@ -113,12 +118,32 @@ def grad_bound(case: "Case", th: np.ndarray, rel=1e-3, eps=EPS_MODEL,
     ty[:, ys] += pos_delta
     _, gx = case.oracle.logp_grad(tx)
     _, gy = case.oracle.logp_grad(ty)
-    for b in range(th.shape[0]):
+    def model_term(b):
         m, J = case.oracle.model_jacobian(th[b])
         wt = w * (np.abs(m) + np.abs(case.data - m))
-        out[b] = (rel * np.abs(gref[b]) + eps * np.einsum("ij,ijk->k", wt, np.abs(J))
+        return eps * np.einsum("ij,ijk->k", wt, np.abs(J))
+
+    # the oracle's Jacobian is serial per row; ctypes releases the GIL, so rows run in parallel
+    with concurrent.futures.ThreadPoolExecutor(max(1, min(th.shape[0], os.cpu_count() or 1))) as ex:
+        terms = list(ex.map(model_term, range(th.shape[0])))
+    for b in range(th.shape[0]):
+        out[b] = (rel * np.abs(gref[b]) + terms[b]
                   + np.abs(gx[b] - gref[b]) + np.abs(gy[b] - gref[b]))
     return out
+
+
+def central_differences(case: "Case", th: np.ndarray) -> np.ndarray:
+    """FP64 central differences of the oracle's log p, h = 1e-6 max(|theta_k|, 1),
+    for every row and parameter (all 2 P shifted rows of a row in one call)."""
+    th = np.atleast_2d(np.asarray(th, np.float64))
+    B, P = th.shape
+    h = 1e-6 * np.maximum(np.abs(th), 1.0)
+    shifted = np.repeat(th, 2 * P, axis=0).reshape(B, 2 * P, P)
+    for k in range(P):
+        shifted[:, 2 * k, k] += h[:, k]
+        shifted[:, 2 * k + 1, k] -= h[:, k]
+    lp = case.oracle.logp(shifted.reshape(-1, P)).reshape(B, P, 2)
+    return (lp[:, :, 0] - lp[:, :, 1]) / (2 * h)
 
 
 def grad_close_bound(got, ref, bound):
