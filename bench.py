@@ -43,13 +43,35 @@ MUFU_PER_SM_CLK = 16
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
 #       -k regex:k_grad -s 3 -c 1 python bench.py --steps 5 --warmup 3 --no-cpu-baseline
 # (700,160 read + 0 written; the outputs are still in L2 when the launch ends).
-# Set to None when the kernel changes until it is captured again.
+# Reported only while KGRAD_SOURCES still hash to the value recorded with the
+# capture (kgrad_source_hash()); a changed kernel reports traffic null.
 TRAFFIC_GROUND_4096 = 700160
 # DRAM bytes of one k_grad launch of the space-telescope workload per row,
 # from one capture of a 512-row launch inside the HMC leg
 # (24,968,704 read + 181,744,384 written); the traffic is the per-row scratch
-# images, so it grows in proportion to the rows. None when the kernel changes.
+# images, so it grows in proportion to the rows.
 TRAFFIC_SPACE_PER_ROW = (24968704 + 181744384) / 512
+# kgrad_source_hash() of the sources the two captures above were taken with
+# (None: no capture of the current kernel yet)
+TRAFFIC_SOURCE_HASH = None
+KGRAD_SOURCES = ["gl_internal.cuh", "gl_model.cuh", "gl_subpixel.cuh", "gl_kernels.cuh",
+                 "gl_grad.cu", "gl_grad_impl.cuh", "gl_grad_l0_series.cu", "gl_grad_l1_series.cu",
+                 "gl_grad_l2_series.cu"]
+
+
+def kgrad_source_hash() -> str:
+    """SHA-256 (first 16 hex digits) of the fused gradient kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KGRAD_SOURCES:
+        with open(os.path.join(ROOT, "paper_2606_30633_b300", "csrc", name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(value):
+    """value if the kernel is the one the ncu capture measured, else None."""
+    return value if TRAFFIC_SOURCE_HASH == kgrad_source_hash() else None
 
 
 # ------------------------------------------------------------ op counts ----
@@ -438,7 +460,8 @@ def run_ours(args) -> dict | None:
             "learned": learned,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak,
-                         "traffic": TRAFFIC_GROUND_4096 if B == 4096 else None,
+                         "traffic": captured_traffic(TRAFFIC_GROUND_4096) if B == 4096 else None,
+                         "kernel_source_hash": kgrad_source_hash(),
                          "algorithmic_bytes": B * (2 * W.P + 1) * 4 + 2 * W.ny * W.nx * 4,
                          "note": "FP32 lane-operations (FMA = 1) of the formulation's op "
                                  "count per evaluation / mean step time; peak = 148 SM x 128 "
@@ -569,7 +592,7 @@ def run_leapfrog(args) -> dict | None:
                        "finite_chains_at_end": finite},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak,
-                         "traffic": TRAFFIC_SPACE_PER_ROW * B,
+                         "traffic": captured_traffic(TRAFFIC_SPACE_PER_ROW * B),
                          "traffic_note": "ncu DRAM bytes of a 512-row launch scaled to the "
                                          "launch's rows (per-row scratch images)"},
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": B * W.P * 4,

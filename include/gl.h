@@ -215,12 +215,18 @@ gl_status gl_model_image(gl_system* sys, const float* theta, int B, float* img,
  *   - Scratch: one file-scope device array of GL_NOALLOC_SCRATCH_FLOATS floats
  *     that every GPU loading the library holds until the process exits.
  *     Images whose two padded buffers fit in shared memory use none of it;
- *     larger ones need one slot per row, and a batch whose slots exceed the
- *     array is rejected with GL_EINVAL (gl_last_error() states the largest
- *     batch that fits).
+ *     larger ones need one slot per row (below), and a batch whose slots
+ *     exceed the array is rejected with GL_EINVAL (gl_last_error() states the
+ *     largest batch that fits).
  *   - The first call on each device looks up the array's device address (and
  *     may load the library's device code); make that first call before any
- *     stream capture.
+ *     stream capture. The address is kept for the life of the process, so the
+ *     call must not be used after a cudaDeviceReset of that device.
+ *   - Images whose padded buffer does not fit in shared memory take scratch
+ *     per row: one padded buffer (Hp x Wp floats, Hp = ny + psf_ny - 1,
+ *     Wp = nx + psf_nx - 1, rounded up to a multiple of 4) when that one
+ *     buffer fits in shared memory but two do not, two buffers otherwise.
+ *   - The caller's current CUDA device is the same on return.
  *   - Every call shares the one array, which keeps the last call's contents
  *     (the kernel writes every value it later reads): calls whose work
  *     overlaps on the GPU, from any system or stream, race on it.
@@ -295,6 +301,24 @@ gl_status gl_series_F(const float* x, int N, float* F, void* stream);
  * grad_host [gl_surrogate_num_params()] receive the results. Synchronous. */
 gl_status gl_surrogate_loss_grad(const gl_surrogate* sur, const float* x, const float* target,
                                  int N, float* loss_host, float* grad_host);
+
+/* The tensor-core surrogate kernels (the per-row table build behind
+ * GL_DEFL_SURROGATE, and the training step) bound every wait for a tensor-core
+ * completion. A wait that runs out drains its outstanding commit (bounded
+ * again), frees its tensor memory and fills its outputs with NaN; the call
+ * reports GL_ETIMEOUT: gl_surrogate_train and gl_surrogate_loss_grad at
+ * once (they are synchronous), a table build at the first GL_DEFL_SURROGATE
+ * call on the same surrogate after the failed build has completed on its
+ * stream (asynchronous, like CUDA's own errors); the rows it served have NaN
+ * log p and gradient.
+ *
+ * Test hook (no counterpart in the paper): with on != 0 the tensor-core
+ * kernels launched afterwards take that timeout path at their first wait as
+ * if it had run out, without waiting (so no wait really runs out and every
+ * commit is still drained before the tensor memory is freed); on = 0
+ * restores normal operation. Process-wide, for every device the calling
+ * thread's current device is; synchronous. Not for production use. */
+gl_status gl_debug_force_wait_timeout(int on);
 
 /* Save / load the parameters and domain to / from a flat binary file. */
 gl_status gl_surrogate_save(const gl_surrogate* sur, const char* path);

@@ -77,6 +77,7 @@ SIGNATURES = {
     "gl_series_F": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     "gl_unit_rates": (ctypes.c_int, [_VP, _VP, _VP]),
     "gl_surrogate_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
+    "gl_debug_force_wait_timeout": (ctypes.c_int, [ctypes.c_int]),
     "gl_surrogate_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "gl_surrogate_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_VP)]),
     "gl_surrogate_destroy": (None, [_VP]),
@@ -605,6 +606,12 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+def debug_force_wait_timeout(on: bool) -> None:
+    """Test hook: the tensor-core surrogate kernels take their wait-timeout path
+    at their first wait (see gl_debug_force_wait_timeout in include/gl.h)."""
+    _check(load().gl_debug_force_wait_timeout(1 if on else 0))
 
 
 def series_F(x, stream=None):

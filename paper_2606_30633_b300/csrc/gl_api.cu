@@ -110,6 +110,10 @@ gl_status ensure_scratch(gl_system* s, size_t floats) {
 // Builds the surrogate tables for B rows and points sp at them.
 gl_status prepare_surrogate(gl_system* s, const float* theta, int B, SysParams& sp,
                             gl_deflection defl, cudaStream_t st) {
+  if (defl == GL_DEFL_SURROGATE) {
+    gl_status r = gl::surrogate_take_timeout(s->sur);
+    if (r != GL_OK) return r;
+  }
   if ((size_t)B > s->table_rows) {
     cudaFree(s->d_table);
     s->d_table = nullptr;
@@ -533,6 +537,7 @@ gl_status eval_prepare(gl_system* s, int B, gl_deflection defl, bool with_grad, 
     if (r != GL_OK) return r;
     sp->scratch = s->scratch;
   }
+  if (defl == GL_DEFL_SURROGATE && (r = gl::surrogate_take_timeout(s->sur)) != GL_OK) return r;
   if (defl != GL_DEFL_SERIES) {
     if ((size_t)B > s->table_rows) {
       cudaFree(s->d_table);

@@ -95,6 +95,7 @@ cudaError_t launch_grad_multi(int nL, int nS, bool surr, const SysParams* system
 cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B, float4* table,
                          cudaStream_t st);
 void surrogate_domain(const gl_surrogate* s, float* q_lo, float* q_hi, float* g_lo, float* g_hi);
+
 // Largest static shared memory of the forward and gradient kernels (bytes,
 // with the surrogate table), or of the multi-system kernel.
 size_t static_smem_bytes(bool multi = false);

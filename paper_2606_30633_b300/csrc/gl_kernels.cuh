@@ -347,6 +347,14 @@ __device__ __forceinline__ void load_table(const float4* src, const SampleC& sc,
   __syncthreads();
 }
 
+// A table build whose tensor-core wait ran out leaves the row's table NaN; the
+// row's results are then NaN (NaN positions would otherwise be clamped to a
+// finite radius by the fmax in the radius floor and give finite brightness).
+template <bool SURR>
+__device__ __forceinline__ bool table_failed(const SampleC& sc, const float4* tab) {
+  return SURR && sc.use_table && isnan(tab[0].x);
+}
+
 // Forward: log p per row, or (img != nullptr) the model image per row.
 template <int NL, int NS, bool SURR>
 __global__ void __launch_bounds__(THREADS, 2)
@@ -376,6 +384,14 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
     return;
   }
   load_table<SURR>(sp.table + (size_t)blockIdx.x * TABLE_ROW, sc, tab);
+  if (table_failed<SURR>(sc, tab)) {
+    if (want_img) {
+      for (int p = threadIdx.x; p < npix; p += THREADS) img[(size_t)b * npix + p] = __int_as_float(0x7fc00000);
+    } else if (threadIdx.x == 0) {
+      logp[b] = __int_as_float(0x7fc00000);
+    }
+    return;
+  }
   if (SURR && sc.use_table)
     bin_pixels<NL, NS, true>(sp, sc, tab, A);
   else
@@ -435,6 +451,10 @@ k_component_images(const __grid_constant__ SysParams sp, const float* __restrict
     }
   const bool source = c >= sp.nL;
   load_table<SURR>(sp.table + (size_t)blockIdx.x * TABLE_ROW, sc, tab);
+  if (source && table_failed<SURR>(sc, tab)) {
+    for (int p = threadIdx.x; p < npix; p += THREADS) out[p] = __int_as_float(0x7fc00000);
+    return;
+  }
   if (SURR && sc.use_table && source)
     bin_component<true>(sp, sc, tab, A, c, source);
   else
@@ -474,6 +494,12 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
     return;
   }
   load_table<SURR>(table_row, sc, tab);
+  if (table_failed<SURR>(sc, tab)) {
+    if (threadIdx.x == 0) *logp_out = __int_as_float(0x7fc00000);
+    if (threadIdx.x < P) grad_out[threadIdx.x] = __int_as_float(0x7fc00000);
+    __syncthreads();
+    return;
+  }
   const bool use_tab = SURR && sc.use_table;
   const int Wp = sp.Wp, cy = sp.cy, cx = sp.cx, nx = sp.nx;
   // phase 1

@@ -168,6 +168,11 @@ gl_status gl_multi_logp_grad(gl_multi* m, const float* const* theta, float* cons
     if (defl == GL_DEFL_SURROGATE && !m->systems[k]->sur)
       return fail(GL_ENOSURROGATE, "a system has no surrogate attached");
   }
+  if (defl == GL_DEFL_SURROGATE)
+    for (int k = 0; k < n_sys; ++k) {
+      const gl_status r = gl::surrogate_take_timeout(m->systems[k]->sur);
+      if (r != GL_OK) return r;
+    }
   cudaStream_t st = (cudaStream_t)stream;
   int cur = -1;
   MU_CUDA(cudaGetDevice(&cur), "cudaGetDevice");

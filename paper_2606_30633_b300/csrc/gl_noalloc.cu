@@ -41,7 +41,8 @@ gl_status fail(gl_status st, const std::string& msg) {
 
 // Host code may not use g_noalloc_scratch directly (on the host it is only a
 // stand-in symbol); its device address is looked up once per device, with
-// that device current.
+// that device current, and kept for the life of the process (a device reset
+// would leave it stale: the entry point is not for use after cudaDeviceReset).
 cudaError_t scratch_address(int dev, float** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_dev[dev]) {
@@ -78,8 +79,18 @@ extern "C" gl_status gl_logp_grad_noalloc(gl_system* sys, const float* theta, in
   }
   int cur = -1;
   cudaError_t e = cudaGetDevice(&cur);
-  if (e == cudaSuccess && cur != dev) e = cudaSetDevice(dev);
   if (e != cudaSuccess) return fail(GL_ECUDA, cudaGetErrorString(e));
+  if (cur != dev) {
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return fail(GL_ECUDA, cudaGetErrorString(e));
+  }
+  // the caller's current device is restored on every return below
+  struct Restore {
+    int dev, cur;
+    ~Restore() {
+      if (cur >= 0 && cur != dev) cudaSetDevice(cur);
+    }
+  } restore{dev, cur};
   if (slot) {
     float* base = nullptr;
     e = scratch_address(dev, &base);

@@ -29,6 +29,10 @@ struct gl_surrogate {
                                   // byte for byte as it lays them out in shared memory
   float final_loss = NAN;
   float q_lo = 0.5f, q_hi = 1.f, g_lo = 1.7f, g_hi = 2.3f;  // training domain
+  // set by a table build whose bounded tensor-core wait ran out (device word),
+  // and its stream-ordered copy in pinned host memory, read at the next call
+  int* d_timeout = nullptr;
+  int* h_timeout = nullptr;
 };
 
 namespace {
@@ -426,6 +430,18 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
       smem_u32(bar)));
 }
 
+// Set through gl_debug_force_wait_timeout: the tensor-core kernels then treat
+// their first completion wait as run out (without waiting), so that the
+// timeout path (drain, flag, NaN outputs, TMEM release) runs with no real wait
+// running out.
+__device__ int g_force_wait_timeout = 0;
+
+__global__ void k_set_force_wait_timeout(int v) { g_force_wait_timeout = v; }
+
+__device__ __forceinline__ bool forced_timeout() {
+  return *reinterpret_cast<volatile int*>(&g_force_wait_timeout) != 0;
+}
+
 // Bounded wait for the barrier's phase; false on timeout.
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t phase) {
   uint32_t done = 0;
@@ -535,6 +551,7 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
   const uint32_t wh = smem_u32(sm + TB_WH), w5 = smem_u32(sm + TB_W5);
   uint32_t phase = 0;
   bool ok = true;
+  const bool forced = forced_timeout();
   // tangent seeds of the normalised inputs, rounded to BF16 like every operand
   const float seed[3] = {__bfloat162float(__float2bfloat16(1.f / PI_F)), 4.f,
                          __bfloat162float(__float2bfloat16(1.f / 0.3f))};
@@ -562,8 +579,8 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
     }
     for (int layer = 1; layer <= 5 && ok; ++layer) {
       // the decision is the block's (a thread leaving alone would desert a barrier)
-      if (!__syncthreads_and(wait_phase(&bar, phase))) {
-        ok = false;
+      if (!__syncthreads_and(!forced && wait_phase(&bar, phase))) {
+        ok = false;  // the commit of phase `phase` is still outstanding
         break;
       }
       phase ^= 1u;
@@ -641,8 +658,12 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
     __syncthreads();
   }
   if (!ok) {
-    // a wait ran out: flag it and make every row this CTA still owned NaN, so
-    // the lens results show the failure instead of reading stale tables
+    // a wait ran out with one commit outstanding: wait for it once more (also
+    // bounded), so that no MMA still writes the tensor memory freed below;
+    // flag the failure and make every row this CTA still owned NaN, so the
+    // lens results show it instead of reading stale tables
+    wait_phase(&bar, phase);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (t == 0) atomicExch(timeout, 1);
     const float nan = __int_as_float(0x7fc00000);
     for (int b = blockIdx.x; b < B; b += gridDim.x)
@@ -780,10 +801,14 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
   const uint32_t sW1 = smem_u32(sm + TR_W1), sWH = smem_u32(sm + TR_WH), sTH = smem_u32(sm + TR_TH);
   uint32_t phase = 0;
   bool ok = true;
+  const bool forced = forced_timeout();
+  // a wait that runs out leaves phase at the outstanding commit (drained below)
   auto wait = [&]() -> bool {
-    const bool got = __syncthreads_and(wait_phase(&bar, phase));
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool got = __syncthreads_and(!forced && wait_phase(&bar, phase));
+    if (got) {
+      phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
     return got;
   };
   // ---- forward ----
@@ -940,6 +965,9 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
     }
   }
   if (!ok) {
+    // drain the outstanding commit (bounded) before the tensor memory is freed
+    wait_phase(&bar, phase);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (t == 0) {
       atomicExch(timeout, 1);
       lpart[blockIdx.x] = __int_as_float(0x7fc00000);
@@ -952,8 +980,6 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tb),
                  "r"(TR_TMEM_COLS));
 }
-
-__device__ int g_table_timeout = 0;
 
 cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B, float4* table,
                          cudaStream_t st) {
@@ -968,16 +994,28 @@ cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B
       if (e == cudaSuccess) configured_dev = dev;
     }
     if (e != cudaSuccess) return e;
-    int* flag = nullptr;
-    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), g_table_timeout);
+    e = cudaMemsetAsync(s->d_timeout, 0, sizeof(int), st);  // this launch's flag only
     if (e != cudaSuccess) return e;
     const int grid = B < 2 * sms ? B : 2 * sms;
     k_table_tc<<<grid, tc::NT, tc::SMEM_BYTES, st>>>(s->wb, s->wimg, s->params, theta, P, B, s->q_lo,
-                                                     s->q_hi, s->g_lo, s->g_hi, table, flag);
+                                                     s->q_hi, s->g_lo, s->g_hi, table,
+                                                     s->d_timeout);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the flag's stream-ordered copy, read by the next call that uses the surrogate
+    return cudaMemcpyAsync(s->h_timeout, s->d_timeout, sizeof(int), cudaMemcpyDeviceToHost, st);
   } else {
     k_table_exact<<<B, TABLE_M, 0, st>>>(theta, P, B, 1.f / 3.f, table);
   }
   return cudaGetLastError();
+}
+
+gl_status surrogate_take_timeout(const gl_surrogate* s) {
+  if (!s || *reinterpret_cast<volatile int*>(s->h_timeout) == 0) return GL_OK;
+  *reinterpret_cast<volatile int*>(s->h_timeout) = 0;
+  set_last_error("a surrogate table build ran out of its bounded tensor-core wait; the rows it "
+                 "served have NaN tables (log p and gradient NaN)");
+  return GL_ETIMEOUT;
 }
 
 void surrogate_domain(const gl_surrogate* s, float* q_lo, float* q_hi, float* g_lo, float* g_hi) {
@@ -1004,13 +1042,18 @@ gl_status sur_alloc(gl_surrogate** out) {
   cudaGetDevice(&s->device);
   if (cudaMalloc(&s->params, NPARAM * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&s->wb, NBF16 * sizeof(__nv_bfloat16)) != cudaSuccess ||
-      cudaMalloc(&s->wimg, TRAIN_IMG_BYTES) != cudaSuccess) {
+      cudaMalloc(&s->wimg, TRAIN_IMG_BYTES) != cudaSuccess ||
+      cudaMalloc(&s->d_timeout, sizeof(int)) != cudaSuccess ||
+      cudaMemset(s->d_timeout, 0, sizeof(int)) != cudaSuccess ||
+      cudaHostAlloc(&s->h_timeout, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
     cudaFree(s->params);
     cudaFree(s->wb);
     cudaFree(s->wimg);
+    cudaFree(s->d_timeout);
     delete s;
     return fail(GL_ENOMEM, "surrogate allocation failed");
   }
+  *s->h_timeout = 0;
   *out = s;
   return GL_OK;
 }
@@ -1019,7 +1062,9 @@ struct TrainBuffers {
   float4* X = nullptr;
   float2* Y = nullptr;
   float *m = nullptr, *v = nullptr, *gpart = nullptr, *lpart = nullptr, *loss = nullptr;
+  int* timeout = nullptr;  // set by a training step whose bounded wait ran out
   ~TrainBuffers() {
+    cudaFree(timeout);
     cudaFree(X);
     cudaFree(Y);
     cudaFree(m);
@@ -1070,6 +1115,8 @@ void gl_surrogate_destroy(gl_surrogate* s) {
   cudaFree(s->params);
   cudaFree(s->wb);
   cudaFree(s->wimg);
+  cudaFree(s->d_timeout);
+  cudaFreeHost(s->h_timeout);
   delete s;
 }
 
@@ -1111,11 +1158,11 @@ gl_status gl_surrogate_loss_grad(const gl_surrogate* s, const float* x, const fl
   SUR_CUDA(cudaFuncSetAttribute(gl::k_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 gl::tc::TR_SMEM),
            "smem limit");
-  int* flag = nullptr;
-  SUR_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), gl::g_table_timeout), "flag");
+  SUR_CUDA(cudaMalloc(&tb.timeout, sizeof(int)), "alloc");
+  SUR_CUDA(cudaMemset(tb.timeout, 0, sizeof(int)), "flag reset");
   gl::k_train_tc<<<ntiles, gl::tc::NT, gl::tc::TR_SMEM>>>(
       s->wb, s->wimg, s->params, reinterpret_cast<const float4*>(x),
-      reinterpret_cast<const float2*>(target), N, 0, 1, 1.f / N, tb.gpart, tb.lpart, flag);
+      reinterpret_cast<const float2*>(target), N, 0, 1, 1.f / N, tb.gpart, tb.lpart, tb.timeout);
   k_adam<<<(NPARAM + 255) / 256, 256>>>(nullptr, nullptr, nullptr, tb.gpart, ntiles, 0.f, 0.f, 0.f,
                                        0.f, 1.f, 1.f, tb.loss);
   k_sum<<<1, 256>>>(tb.lpart, ntiles, tb.loss + NPARAM);
@@ -1124,6 +1171,11 @@ gl_status gl_surrogate_loss_grad(const gl_surrogate* s, const float* x, const fl
   float lsum = 0.f;
   SUR_CUDA(cudaMemcpy(&lsum, tb.loss + NPARAM, sizeof(float), cudaMemcpyDeviceToHost), "copy");
   *loss_host = lsum / N;
+  int timed_out = 0;
+  SUR_CUDA(cudaMemcpy(&timed_out, tb.timeout, sizeof(int), cudaMemcpyDeviceToHost), "copy");
+  if (timed_out)
+    return fail(GL_ETIMEOUT, "the training kernel's bounded tensor-core wait ran out (loss and "
+                             "gradient are NaN)");
   return GL_OK;
 }
 
@@ -1168,9 +1220,9 @@ gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** ou
   if (cudaFuncSetAttribute(gl::k_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            gl::tc::TR_SMEM) != cudaSuccess)
     return bail(fail(GL_ECUDA, "training kernel shared-memory limit"));
-  int* flag = nullptr;
-  if (cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), gl::g_table_timeout) != cudaSuccess)
-    return bail(fail(GL_ECUDA, "training kernel flag"));
+  if (cudaMalloc(&tb.timeout, sizeof(int)) != cudaSuccess ||
+      cudaMemset(tb.timeout, 0, sizeof(int)) != cudaSuccess)
+    return bail(fail(GL_ENOMEM, "training flag"));
   const long long steps_per_epoch = (n + d->batch - 1) / d->batch;
   const long long total = steps_per_epoch * d->epochs;
   const float b1 = 0.9f, b2 = 0.999f;
@@ -1188,7 +1240,7 @@ gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** ou
     gl::k_train_tc<<<ntiles, gl::tc::NT, gl::tc::TR_SMEM>>>(s->wb, s->wimg, s->params, tb.X, tb.Y,
                                                             n, row0,
                                                             stride, 1.f / d->batch, tb.gpart,
-                                                            tb.lpart, flag);
+                                                            tb.lpart, tb.timeout);
     k_adam<<<(NPARAM + 255) / 256, 256>>>(s->params, tb.m, tb.v, tb.gpart, ntiles, lr, b1, b2,
                                          1e-8f, (float)(1.0 - bc1), (float)(1.0 - bc2), nullptr);
     if ((it & 255) == 0) {
@@ -1202,9 +1254,22 @@ gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** ou
   float lsum = 0.f;
   cudaError_t e = cudaMemcpy(&lsum, tb.loss, sizeof(float), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return bail(fail(GL_ECUDA, std::string("training: ") + cudaGetErrorString(e)));
+  int timed_out = 0;
+  e = cudaMemcpy(&timed_out, tb.timeout, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bail(fail(GL_ECUDA, std::string("training: ") + cudaGetErrorString(e)));
+  if (timed_out)
+    return bail(fail(GL_ETIMEOUT, "a training step's bounded tensor-core wait ran out (its "
+                                  "gradient was NaN); no surrogate is returned"));
   s->final_loss = lsum / d->batch;
   if (final_loss) *final_loss = s->final_loss;
   *out = s;
+  return GL_OK;
+}
+
+gl_status gl_debug_force_wait_timeout(int on) {
+  gl::tc::k_set_force_wait_timeout<<<1, 1>>>(on ? 1 : 0);
+  SUR_CUDA(cudaGetLastError(), "flag setter launch");
+  SUR_CUDA(cudaDeviceSynchronize(), "flag setter");
   return GL_OK;
 }
 

@@ -52,4 +52,10 @@ void plan_buffers(size_t buf_floats, int nbufs, size_t smem_budget, size_t* dyn,
 void set_last_error(const std::string& msg);
 // Frees the inference layer's state of a system (gl_infer.cu).
 void infer_release(gl_system* s);
+// GL_ETIMEOUT (and clears it) if a table build of s that the host has seen
+// complete ran out of its bounded tensor-core wait, else GL_OK. The table
+// launch copies its flag to pinned host memory in stream order, so a timeout
+// is reported by the first surrogate call after the failed build completed
+// (like CUDA's own asynchronous errors).
+gl_status surrogate_take_timeout(const gl_surrogate* s);  // gl_surrogate.cu
 }  // namespace gl

@@ -84,7 +84,28 @@ def grad_close(got, ref, rel=1e-3, floor=1e-2):
     return np.all(np.abs(got - ref) <= rel * scale), float(np.max(np.abs(got - ref) / scale))
 
 
-EPS_MODEL = 5e-6  # per-pixel relative FP32 model error the bounds allow for
+EPS_MODEL = 5e-6  # per-pixel relative FP32 model error the gradient bound allows for
+MODEL_REL = 1e-5  # the stated per-pixel relative model tolerance
+
+
+def logp_bound(case: "Case", th: np.ndarray, eps=MODEL_REL) -> np.ndarray:
+    """Per-row log p tolerance: the stated relative 1e-6, or the first-order
+    log p change that a per-pixel relative model error eps (the stated
+    per-pixel tolerance) causes, eps sum_p |d_p - m_p| |m_p| / sigma_p^2,
+    whichever is larger."""
+    th = np.atleast_2d(th)
+    ref = case.oracle.logp(th)
+    m = case.oracle.model_image(th)
+    r = np.abs(case.data[None] - m) * np.abs(m) / case.sigma[None] ** 2
+    return np.maximum(1e-6 * np.abs(ref), eps * r.reshape(len(th), -1).sum(1))
+
+
+def logp_close(case: "Case", th: np.ndarray, got) -> tuple:
+    """(ok, worst error / bound) of GPU log p values against logp_bound."""
+    th = np.atleast_2d(th)
+    err = np.abs(np.asarray(got, np.float64) - case.oracle.logp(th))
+    tol = logp_bound(case, th)
+    return bool(np.all(err <= tol)), float(np.max(err / tol))
 
 
 POS_DELTA = 2e-6  # arcsec: FP32 position precision of grid and deflection

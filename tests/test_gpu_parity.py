@@ -2,23 +2,20 @@
 same seeded, float32-rounded inputs.
 
 Tolerances (FP32 path vs FP64 oracle):
-  model image  a pixel fails only if |dm| > 1e-5 |m| and |dm| > 1e-4 max|m|;
-  log p        near the posterior mode (the truth and vectors a small step
-               from it, where samplers spend their time): relative 1e-6, or
-               the first-order error of a per-pixel relative model error of
-               EPS_MODEL = 5e-6, EPS_MODEL sum_p |d_p - m_p| m_p / sigma_p^2,
-               whichever is larger (bright pixels have m/sigma ~ 600, so a few
-               1e-6 of model error moves log p by ~1e-3 on small images);
-               at prior draws far from the mode: relative 1e-5. There chi^2 is
-               dominated by bright, mis-placed Sersic cores whose FP32 exponent
-               b_n p (5-25) turns the ~2e-7 relative error of p = (R/R_e)^(1/n)
-               into a relative model error of ~1e-6 (measured up to 5.2e-6 in
-               log p);
+  model image  a pixel fails only if |dm| > 1e-5 |m| and |dm| > 1e-4 max|m|
+               (the stated per-pixel bound);
+  log p        relative 1e-6, or the first-order log p change of the stated
+               per-pixel model tolerance, 1e-5 sum_p |d_p - m_p| |m_p| /
+               sigma_p^2, whichever is larger (lenscase.logp_bound). On these
+               small, bright images (m/sigma up to ~600) with compact sources
+               an FP32 lens equation misses the plain 1e-6 (the stated bounds
+               are asserted as they stand on the ground-based workloads near
+               the mode in test_gpu_tolerances.py);
   gradient     |g_k - g_ref,k| <= 1e-3 |g_ref,k| + EPS_MODEL sum_p (|m_p| +
                |d_p - m_p|) |dm_p/dtheta_k| / sigma_p^2 (the gradient change
-               that the same per-pixel model error causes, from the oracle's
-               FP64 Jacobian), plus the oracle gradient's change under a
-               2e-6 arcsec shift of every component centre (FP32 position
+               that a per-pixel model error EPS_MODEL = 5e-6 causes, from the
+               oracle's FP64 Jacobian), plus the oracle gradient's change under
+               a 2e-6 arcsec shift of every component centre (FP32 position
                precision; far from the mode the gradient can move by ~5e-3 per
                1e-6 arcsec); against central differences the same bound.
 """
@@ -28,8 +25,8 @@ import numpy as np
 import pytest
 
 import synth
-from lenscase import (grad_bound, grad_close, grad_close_bound, image_close, make_case,
-                      small_workload)
+from lenscase import (grad_bound, grad_close, grad_close_bound, image_close, logp_close,
+                      make_case, small_workload)
 
 pytestmark = pytest.mark.gpu
 
@@ -42,29 +39,14 @@ def torch():
     return torch
 
 
-REL_MODE, REL_PRIOR, EPS_MODEL = 1e-6, 1e-5, 5e-6
-
-
 def _mode_close(c, th, got):
-    """Near-mode log p check (see the module docstring)."""
-    ref = c.oracle.logp(th)
-    m = c.oracle.model_image(th)
-    r = np.abs(c.data[None] - m) * m / c.sigma[None] ** 2
-    tol = np.maximum(REL_MODE * np.abs(ref), EPS_MODEL * r.reshape(len(th), -1).sum(1))
-    err = np.abs(np.asarray(got, np.float64) - ref)
-    return bool(np.all(err <= tol)), float(np.max(err / tol))
+    return logp_close(c, th, got)
 
 
 def _near_mode(c, n, seed=1):
     th = synth.jitter(c.truth, c.W.prior(), n, seed, rel=0.01)
     th[0] = c.truth
     return np.asarray(np.asarray(th, np.float32), np.float64)
-
-
-def _lp_close(got, ref, rel=REL_PRIOR, absol=1e-3):
-    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
-    err = np.abs(got - ref)
-    return np.all(err <= np.maximum(rel * np.abs(ref), absol)), float(np.max(err / np.abs(ref)))
 
 
 CASES = [
@@ -103,7 +85,7 @@ def test_logp_matches_oracle(torch, case):
     ref = case.oracle.logp(th)
     ok, worst = _mode_close(case, th[:8], lp[:8])
     assert ok, (worst, lp[:4], ref[:4])
-    ok, worst = _lp_close(lp[8:], ref[8:], rel=REL_PRIOR)
+    ok, worst = logp_close(case, th[8:], lp[8:])
     assert ok, (worst, lp[8:12], ref[8:12])
     # gl_logp_grad returns the same log p (same kernel arithmetic for the forward)
     lp2, _ = sysg.logp_grad(t)
@@ -117,7 +99,7 @@ def test_gradient_matches_oracle(torch, case):
     lref, gref = case.oracle.logp_grad(th)
     lp = lp.cpu().numpy()
     assert _mode_close(case, th[:4], lp[:4])[0]
-    ok, worst = _lp_close(lp, lref)
+    ok, worst = logp_close(case, th, lp)
     assert ok, worst
     ok, worst = grad_close_bound(g.cpu().numpy(), gref, grad_bound(case, th))
     assert ok, worst
@@ -193,7 +175,7 @@ def test_degenerate_lenses(torch):
     lp, g = s.logp_grad(t)
     lp, g = lp.cpu().numpy(), g.cpu().numpy().astype(np.float64)
     assert np.isfinite(lp).all() and np.isfinite(g).all()
-    ok, worst = _lp_close(lp, c.oracle.logp(th))
+    ok, worst = logp_close(c, th, lp)
     assert ok, worst
     lref, gref = c.oracle.logp_grad(th[1:3])
     ok, worst = grad_close_bound(g[1:3], gref, grad_bound(c, th[1:3]))
@@ -242,7 +224,7 @@ def test_zero_intensity_components(torch):
     lp, g = lp.cpu().numpy(), g.cpu().numpy().astype(np.float64)
     assert np.isfinite(lp).all() and np.isfinite(g).all()
     lref, gref = orc.logp_grad(th)
-    ok, worst = _lp_close(lp, lref)
+    ok, worst = logp_close(cf, th, lp)
     assert ok, worst
     ok, worst = grad_close_bound(g, gref, grad_bound(cf, th))
     assert ok, worst
@@ -254,7 +236,7 @@ def test_tiny_image_single_pixel(torch):
     th = c.theta(4)
     lp, g = c.gpu_system().logp_grad(torch.tensor(th, dtype=torch.float32, device="cuda"))
     lref, gref = c.oracle.logp_grad(th)
-    assert _lp_close(lp.cpu().numpy(), lref)[0]
+    assert logp_close(c, th, lp.cpu().numpy())[0]
     assert grad_close_bound(g.cpu().numpy(), gref, grad_bound(c, th))[0]
 
 
@@ -277,7 +259,7 @@ def test_maximum_image_size(torch):
     lp = lp.cpu().numpy()
     ok, worst = _mode_close(c, th[:2], lp[:2])
     assert ok, worst
-    ok, worst = _lp_close(lp[2:], c.oracle.logp(th[2:]))
+    ok, worst = logp_close(c, th[2:], lp[2:])
     assert ok, worst
     np.testing.assert_array_equal(sysg.logp(t).cpu().numpy(), lp)
     sysg.close()
@@ -330,7 +312,7 @@ def test_full_size_sampled_rows(torch, which):
     lp, g = lp.cpu().numpy(), g.cpu().numpy().astype(np.float64)
     assert np.isfinite(lp).all()
     ref = c.oracle.logp(th_all[rows_lp])
-    ok, worst = _lp_close(lp[rows_lp], ref)
+    ok, worst = logp_close(c, th_all[rows_lp], lp[rows_lp])
     assert ok, worst
     assert _mode_close(c, th_all[1:2], lp[1:2])[0]
     lref, gref = c.oracle.logp_grad(th_all[rows_g])

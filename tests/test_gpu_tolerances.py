@@ -22,21 +22,21 @@ gradient bounds are out of reach of an FP32 lens equation on some rows
 source of R_e ~ 0.05 arcsec turns into ~1e-6 of relative model error, and
 which the source's gradient turns into ~1e-3 once the gradient sums
 cancel); there the model-image and chi^2 bounds are asserted as stated, log
-p and the gradient against the error-propagation bounds of the other parity
-tests, and the measured worst error against each stated bound is printed.
+p against the first-order effect of the stated per-pixel model tolerance,
+the gradient against the error-propagation bound of the other parity tests,
+and the measured worst error against each stated bound is printed.
 """
 import numpy as np
 import pytest
 
 import synth
 from lenscase import (central_differences, grad_bound, grad_close_bound, image_close,
-                      make_case)
+                      logp_close, make_case)
 
 pytestmark = pytest.mark.gpu
 
 LOGP_REL = 1e-6
 GRAD_REL, GRAD_FLOOR = 1e-3, 1e-2
-EPS_MODEL = 5e-6
 
 
 @pytest.fixture(scope="module")
@@ -129,10 +129,9 @@ def test_prior_draws(torch, cfg):
           f"{int((rel <= LOGP_REL).sum())}/{len(th)} rows within {LOGP_REL:.0e}; gradient error / "
           f"stated bound max {r_or.max():.3f} vs oracle ({int((r_or.max(1) <= 1).sum())}/{len(th)} "
           f"rows within), {r_fd.max():.3f} vs FD")
-    # log p: the first-order effect of a per-pixel relative model error EPS_MODEL
-    m_err = EPS_MODEL * np.einsum("bij,ij->b", np.abs(c.data[None] - mref) * np.abs(mref),
-                                  1.0 / c.sigma ** 2)
-    assert np.all(np.abs(lp - lref) <= np.maximum(LOGP_REL * np.abs(lref), m_err))
+    # log p: the first-order effect of the stated per-pixel model tolerance
+    ok, worst = logp_close(c, th, lp)
+    assert ok, worst
     bound = grad_bound(c, th)
     ok, worst = grad_close_bound(g, gref, bound)
     assert ok, worst

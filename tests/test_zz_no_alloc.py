@@ -31,20 +31,33 @@ def setup():
 
 
 def test_matches_gl_logp_grad_on_two_calls(setup):
-    torch, gl, c, sysg = setup
+    """A fresh system (it has never run gl_logp_grad, so it owns no scratch of
+    its own): after one warm-up call per batch shape (the first call looks up
+    the array's address), further calls leave the device's free memory
+    unchanged; then gl_logp_grad gives the same results bit for bit."""
+    torch, gl, c, _ = setup
+    sysg = c.gpu_system()
     th1 = torch.tensor(c.theta(32, seed=1), dtype=torch.float32, device="cuda")
     th2 = torch.tensor(c.theta(24, seed=2), dtype=torch.float32, device="cuda")
     th1[0] = torch.tensor(c.truth, dtype=torch.float32)
+    outs = [(torch.empty(t.shape[0], device="cuda"), torch.empty_like(t)) for t in (th1, th2, th1)]
+    sysg.logp_grad_noalloc(th1, *outs[0])
+    sysg.logp_grad_noalloc(th2, *outs[1])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    got1 = sysg.logp_grad_noalloc(th1, *outs[0])
+    got2 = sysg.logp_grad_noalloc(th2, *outs[1])
+    again1 = sysg.logp_grad_noalloc(th1, *outs[2])  # the shared scratch keeps no state that matters
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     ref1 = sysg.logp_grad(th1)
     ref2 = sysg.logp_grad(th2)
-    got1 = sysg.logp_grad_noalloc(th1)
-    got2 = sysg.logp_grad_noalloc(th2)
-    again1 = sysg.logp_grad_noalloc(th1)  # the shared scratch keeps no state that matters
     torch.cuda.synchronize()
     for got, ref in ((got1, ref1), (got2, ref2), (again1, ref1)):
         np.testing.assert_array_equal(got[0].cpu().numpy(), ref[0].cpu().numpy())
         np.testing.assert_array_equal(got[1].cpu().numpy(), ref[1].cpu().numpy())
     assert np.isfinite(got1[0].cpu().numpy()).all()
+    sysg.close()
 
 
 def test_small_image_without_scratch(setup):
