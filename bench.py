@@ -8,6 +8,13 @@ the library itself with seeded noise. A step is one fused forward + adjoint
 launch over the whole batch. L2 is flushed (a 256 MB write) before every timed
 step; each step is timed with CUDA events on its stream.
 
+The same line also carries, as the sub-objects "space" and "uneven", a few
+timed steps of the space-telescope workload (200x200 px at 0.05"/px, s = 5,
+21x21 PSF, two sources, 16384 HMC chains; a step is one CUDA graph of 10
+leapfrogs plus a Metropolis-Hastings test) and of the uneven multi-system
+batch (100 systems of 40-200 px, s = 2-5, 256 rows each), each with its own
+clocks and roofline (--no-extra-workloads leaves them out).
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (the only reference this method
@@ -325,7 +332,7 @@ def learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world) -
     q, t, thE = X[:, 0].astype(np.float64), X[:, 1] - 1.0, 1.25
     b = thE * np.sqrt(q)
     dal = 2 * b / (1 + q) * (b / (np.exp(X[:, 2]) * thE)) ** (t - 1) * np.hypot(dF[:, 0], dF[:, 1])
-    return {"value": out["surrogate"], "unit": "evals/s",
+    return sur, {"value": out["surrogate"], "unit": "evals/s",
             "deflection": "learned surrogate (4-64x4-2 SiLU MLP, BF16 tensor cores), tables per row",
             "dlogp_abs_max_near_mode": float(d_near.max()),
             "dlogp_abs_prior_draws": {"p50": float(np.median(d_prior)),
@@ -436,7 +443,7 @@ def run_ours(args) -> dict | None:
             e2e_ms.append(dt * 1e3)
     e2e_value = world * B / (statistics.mean(e2e_ms) / 1e3)
 
-    learned = learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world)
+    sur, learned = learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world)
 
     ops, mufu = algorithmic_ops(theta_np.astype(np.float64), W.ny, W.nx, W.supersample,
                                 W.psf.shape[0], 1, 1)
@@ -475,34 +482,36 @@ def run_ours(args) -> dict | None:
             "gpu_launches": args.steps,
             "clocks": clocks,
         }
-        if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline_leg()
+    if not args.no_extra_workloads:
+        # the space-telescope HMC graph and the uneven multi-system batch, each
+        # timed on its own (a few steps; their own clocks and rooflines)
+        space = space_leg(args.extra_steps, 3, world, local, e2e_reps=1)
+        uneven = uneven_leg(max(args.extra_steps, 5), 3, world, local, sur=sur)
+        if out is not None:
+            out["space"] = space
+            out["uneven"] = uneven
+    if out is not None and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_leg()
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
 
 
-def run_leapfrog(args) -> dict | None:
+def space_leg(steps: int, warmup: int, world: int, local: int, e2e_reps: int = 2,
+              batch: int | None = None) -> dict:
     """Space-telescope-like system under the batched gradient loop: 200x200 px
     at 0.05"/px, s = 5, 21x21 Gaussian-core PSF, two source components, 16384
     chains started near the truth; a step is one HMC transition: a CUDA graph of
     10 leapfrogs (each a fused forward + adjoint over all chains) in the
     unconstrained space of the prior's bijection, then a Metropolis-Hastings
-    test, with the step size from dual averaging on 512 of the chains."""
+    test, with the step size from dual averaging on 512 of the chains.
+    Returns the leg's figures (rank 0's copy is the one reported)."""
     import torch
     import paper_2606_30633_b300 as gl
-    from paper_2606_30633_b300 import build as glbuild
-
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    glbuild.build()
     dev = torch.device("cuda", local)
     W = synth.space_200()
-    if args.batch:
-        W.batch = args.batch
+    if batch:
+        W.batch = batch
     spec = W.prior()
     B, L = W.batch, 10
     blank = gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
@@ -528,26 +537,26 @@ def run_leapfrog(args) -> dict | None:
     eps = ha.state()[3]
     ha.close()
     h = gl.Hmc(S, u0, L, eps, 0.8, seed=W.seed_samples + 3)
-    acc = torch.empty(args.warmup + args.steps, device=dev)
-    for k in range(args.warmup):
+    acc = torch.empty(warmup + steps, device=dev)
+    for k in range(warmup):
         flush.zero_()
         h.run(1, 0, None, acc[k:k + 1], stream=stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+          for _ in range(steps)]
     with ClockSampler(local) as clk:
         for k, (a, b) in enumerate(ev):
             flush.zero_()
             a.record(stream)
-            h.run(1, 0, None, acc[args.warmup + k:args.warmup + k + 1], stream=stream)
+            h.run(1, 0, None, acc[warmup + k:warmup + k + 1], stream=stream)
             b.record(stream)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = sum(step_ms)
     t_ms = max_over_ranks(t_ms, world, dev)
-    value = job_rate(B * L * args.steps, world, t_ms)
+    value = job_rate(B * L * steps, world, t_ms)
     u_end, lp_end, _, _ = h.state()
     h.close()
     finite = float(torch.isfinite(lp_end).float().mean())
@@ -557,7 +566,7 @@ def run_leapfrog(args) -> dict | None:
     h_u = u0.cpu().pin_memory()
     h_lp = torch.empty(B).pin_memory()
     e2e_ms = []
-    for _ in range(2):
+    for _ in range(e2e_reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ud = h_u.to(dev, non_blocking=True)
@@ -568,52 +577,40 @@ def run_leapfrog(args) -> dict | None:
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         h2.close()
+    S.close()
     e2e_value = world * B * (L + 1) / (min(e2e_ms) / 1e3)
-    ops, mufu = algorithmic_ops(th_end, W.ny, W.nx, W.supersample,
-                                W.psf.shape[0], W.n_lens_light, W.n_source)
+    ops, _ = algorithmic_ops(th_end, W.ny, W.nx, W.supersample,
+                             W.psf.shape[0], W.n_lens_light, W.n_source)
     mean_s = statistics.mean(step_ms) / 1e3
     peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2.032e9 / 1e12
     achieved = ops * L / mean_s / 1e12
-    out = None
-    if rank == 0:
-        out = {
-            "metric": "logp+grad evals/s (200x200 px, 5x SS, 16384 chains, 10-leapfrog graph "
-                      "blocks, one Metropolis-Hastings test per block) on 1 B300",
-            "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded priors, library-rendered truth, seeded noise)",
-            "config": {"workload": W.name, "chains": B, "leapfrogs_per_step": L,
-                       "step_size_unconstrained": eps,
-                       "mean_accept": float(acc[args.warmup:].mean()),
-                       "ny": W.ny, "nx": W.nx, "supersample": W.supersample,
-                       "psf": int(W.psf.shape[0]), "params": W.P,
-                       "l2": "flushed (256 MB write) before every timed step",
-                       "finite_chains_at_end": finite},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak,
-                         "traffic": captured_traffic(TRAFFIC_SPACE_PER_ROW * B),
-                         "traffic_note": "ncu DRAM bytes of a 512-row launch scaled to the "
-                                         "launch's rows (per-row scratch images)"},
-            "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": B * W.P * 4,
-                    "d2h_bytes_per_step": B * 4},
-            "gpu_launches": (2 * L + 4) * args.steps,
-            "clocks": clk.summary(),
-        }
-    if world > 1:
-        torch.distributed.destroy_process_group()
-    return out
+    return {
+        "metric": "logp+grad evals/s (200x200 px, 5x SS, 16384 chains, 10-leapfrog graph "
+                  "blocks, one Metropolis-Hastings test per block) on 1 B300",
+        "value": value, "unit": "evals/s", "steps": steps, "warmup": warmup,
+        "ms_per_step": t_ms / steps,
+        "config": {"workload": W.name, "chains": B, "leapfrogs_per_step": L,
+                   "step_size_unconstrained": eps,
+                   "mean_accept": float(acc[warmup:].mean()),
+                   "ny": W.ny, "nx": W.nx, "supersample": W.supersample,
+                   "psf": int(W.psf.shape[0]), "params": W.P,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "finite_chains_at_end": finite},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak,
+                     "traffic": captured_traffic(TRAFFIC_SPACE_PER_ROW * B),
+                     "traffic_note": "ncu DRAM bytes of a 512-row launch scaled to the "
+                                     "launch's rows (per-row scratch images)"},
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": B * W.P * 4,
+                "d2h_bytes_per_step": B * 4},
+        "gpu_launches": (2 * L + 4) * steps,
+        "clocks": clk.summary(),
+    }
 
 
-def run_uneven(args) -> dict | None:
-    """Uneven-batch persistent run: 100 synthetic systems (sides 40-200 px,
-    s = 2-5, 1-3 source components, 0.262"/px, 11x11 Moffat), 256 rows each,
-    all evaluated per step by gl_multi_logp_grad (one persistent launch per
-    component-count group); the shared-memory policy is picked by the
-    autotuner; the exact series and the learned surrogate side by side."""
+def run_leapfrog(args) -> dict | None:
+    """The space-telescope workload on its own (see space_leg)."""
     import torch
-    import paper_2606_30633_b300 as gl
-    from paper_2606_30633_b300 import autotune
     from paper_2606_30633_b300 import build as glbuild
 
     rank, world, local = dist_env()
@@ -622,12 +619,35 @@ def run_uneven(args) -> dict | None:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     glbuild.build()
+    leg = space_leg(args.steps, args.warmup, world, local, batch=args.batch)
+    out = None
+    if rank == 0:
+        out = {"metric": leg.pop("metric"), "value": leg.pop("value"), "unit": "evals/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": leg.pop("ms_per_step"), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic (seeded priors, library-rendered truth, seeded noise)", **leg}
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def uneven_leg(steps: int, warmup: int, world: int, local: int, sur=None,
+               batch: int | None = None) -> dict:
+    """Uneven-batch persistent run: 100 synthetic systems (sides 40-200 px,
+    s = 2-5, 1-3 source components, 0.262"/px, 11x11 Moffat), 256 rows each,
+    all evaluated per step by gl_multi_logp_grad (persistent launches per
+    group); the launch shapes are picked by the autotuner; the exact series
+    and the learned surrogate (sur, trained here when None) side by side."""
+    import torch
+    import paper_2606_30633_b300 as gl
+    from paper_2606_30633_b300 import autotune
     dev = torch.device("cuda", local)
     Ws = synth.uneven_systems()
     systems, thetas, rows = [], [], []
     for W in Ws:
-        if args.batch:
-            W.batch = args.batch  # rows per system (profiling runs)
+        if batch:
+            W.batch = batch  # rows per system (profiling runs)
         spec = W.prior()
         blank = gl.System(W.ny, W.nx, W.pixel_scale, W.supersample, np.zeros((W.ny, W.nx)),
                           np.ones((W.ny, W.nx)), W.psf, W.n_lens_light, W.n_source, spec)
@@ -644,17 +664,19 @@ def run_uneven(args) -> dict | None:
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     logps, grads = plan.logp_grad(thetas)
+    if world > 1:
+        torch.distributed.barrier()
     with ClockSampler(local) as clk:
-        ms = timed_steps(lambda: plan.logp_grad(thetas, logps, grads, stream=stream), args.steps,
-                         args.warmup, stream, flush)
-    sur = gl.Surrogate.train(n_samples=10_000_000, epochs=120, batch=16384, lr=2e-3, lr_min=1e-5,
-                             seed_data=401, seed_init=402)
+        ms = timed_steps(lambda: plan.logp_grad(thetas, logps, grads, stream=stream), steps,
+                         warmup, stream, flush)
+    if sur is None:
+        sur = gl.Surrogate.train(n_samples=10_000_000, epochs=120, batch=16384, lr=2e-3,
+                                 lr_min=1e-5, seed_data=401, seed_init=402)
     for s_ in systems:
         s_.set_surrogate(sur)
     lps_s = [t.clone() for t in logps]
     ms_sur = timed_steps(lambda: plan.logp_grad(thetas, logps, grads, defl=gl.GL_DEFL_SURROGATE,
-                                                stream=stream), args.steps, args.warmup, stream,
-                         flush)
+                                                stream=stream), steps, warmup, stream, flush)
     dl = torch.cat([(a - b).abs() for a, b in zip(logps, lps_s)]).cpu().numpy()
     # end to end: every system's rows from pinned host memory, one multi-system
     # evaluation (exact series), log p and gradients back to pinned host memory
@@ -677,7 +699,7 @@ def run_uneven(args) -> dict | None:
     d2h = sum(t.numel() * 4 + t.shape[0] * 4 for t in thetas)
     t_ms = sum(ms)
     t_ms = max_over_ranks(t_ms, world, dev)
-    value = job_rate(n_rows * args.steps, world, t_ms)
+    value = job_rate(n_rows * steps, world, t_ms)
     ops = 0.0
     for W, th in zip(Ws, thetas):
         o, _ = algorithmic_ops(th.double().cpu().numpy(), W.ny, W.nx, W.supersample,
@@ -685,29 +707,50 @@ def run_uneven(args) -> dict | None:
         ops += o
     peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2.032e9 / 1e12
     achieved = ops / (statistics.mean(ms) / 1e3) / 1e12
+    launches = len({(W.n_lens_light, W.n_source) for W in Ws})  # one launch per group
+    shapes = {"smem_policy": {v: k for k, v in autotune.POLICIES.items()}[plan.smem_policy]}
+    plan.close()
+    for s_ in systems:
+        s_.close()
+    return {
+        "metric": "logp+grad evals/s (100 uneven systems: 40-200 px, 2-5x SS, 1-3 sources, "
+                  "256 rows each) on 1 B300",
+        "value": value, "unit": "evals/s", "steps": steps, "warmup": warmup,
+        "ms_per_step": t_ms / steps,
+        "config": {"workload": "uneven-100-systems", "systems": len(Ws), "rows": n_rows,
+                   "launch_shapes": shapes, "autotune_ms": tune_ms,
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "learned": {"value": world * n_rows / (statistics.mean(ms_sur) / 1e3), "unit": "evals/s",
+                    "dlogp_abs_median": float(np.median(dl)),
+                    "dlogp_abs_p90": float(np.quantile(dl, 0.9))},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": None},
+        "e2e": {"value": world * n_rows / (min(e2e_ms) / 1e3), "unit": "evals/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * steps,
+        "clocks": clk.summary(),
+    }
+
+
+def run_uneven(args) -> dict | None:
+    """The uneven multi-system workload on its own (see uneven_leg)."""
+    import torch
+    from paper_2606_30633_b300 import build as glbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    glbuild.build()
+    leg = uneven_leg(args.steps, args.warmup, world, local, batch=args.batch)
     out = None
     if rank == 0:
-        out = {
-            "metric": "logp+grad evals/s (100 uneven systems: 40-200 px, 2-5x SS, 1-3 sources, "
-                      "256 rows each) on 1 B300",
-            "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded priors, library-rendered truths, seeded noise)",
-            "config": {"workload": "uneven-100-systems", "systems": len(Ws), "rows": n_rows,
-                       "smem_policy": {v: k for k, v in autotune.POLICIES.items()}[plan.smem_policy],
-                       "autotune_ms": tune_ms,
-                       "l2": "flushed (256 MB write) before every timed step"},
-            "learned": {"value": world * n_rows / (statistics.mean(ms_sur) / 1e3), "unit": "evals/s",
-                        "dlogp_abs_median": float(np.median(dl)),
-                        "dlogp_abs_p90": float(np.quantile(dl, 0.9))},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None},
-            "e2e": {"value": world * n_rows / (min(e2e_ms) / 1e3), "unit": "evals/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 3 * args.steps,
-            "clocks": clk.summary(),
-        }
+        out = {"metric": leg.pop("metric"), "value": leg.pop("value"), "unit": "evals/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": leg.pop("ms_per_step"), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic (seeded priors, library-rendered truths, seeded noise)", **leg}
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
@@ -967,6 +1010,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="ground100 only: skip the space-telescope and uneven-batch legs")
+    ap.add_argument("--extra-steps", type=int, default=3,
+                    help="timed steps of the space-telescope leg (the uneven leg takes at "
+                         "least 5) in the default run")
     ap.add_argument("--batch", type=int, default=None,
                     help="rows per step (rows per system for uneven; default: the "
                          "workload's); for profiling runs")
