@@ -309,7 +309,8 @@ def learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world) -
     train_s = time.perf_counter() - t0
     S.set_surrogate(sur)
     out = {}
-    for name, defl in (("surrogate", gl.GL_DEFL_SURROGATE), ("exact_tables", gl.GL_DEFL_TABLE)):
+    for name, defl in (("surrogate", gl.GL_DEFL_SURROGATE), ("exact_tables", gl.GL_DEFL_TABLE),
+                       ("exact_tables_fp32", gl.GL_DEFL_TABLE32)):
         ms = timed_steps(lambda: S.logp_grad(theta, defl=defl, out=logp, grad=grad, stream=stream),
                          args.steps, args.warmup, stream, flush)
         out[name] = world * W.batch / (statistics.mean(ms) / 1e3)
@@ -318,6 +319,8 @@ def learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world) -
     tn = torch.tensor(near, device=theta.device)
     d_near = (S.logp(tn, defl=gl.GL_DEFL_SURROGATE) - S.logp(tn)).abs().cpu().numpy()
     d_prior = (S.logp(theta, defl=gl.GL_DEFL_SURROGATE) - S.logp(theta)).abs().cpu().numpy()
+    t_near = (S.logp(tn, defl=gl.GL_DEFL_TABLE32) - S.logp(tn)).abs().cpu().numpy()
+    t_prior = (S.logp(theta, defl=gl.GL_DEFL_TABLE32) - S.logp(theta)).abs().cpu().numpy()
     e = np.hypot(theta_np[:, 2], theta_np[:, 3])
     in_dom = float(np.mean(((1 - e) / (1 + e) >= 0.5) & (e >= 0.01)))
     # deflection error against the library's FP64 series on 2e5 held-out tuples
@@ -345,9 +348,17 @@ def learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world) -
             "rows_in_surrogate_domain": in_dom,
             "train_seconds": train_s, "train_final_loss": sur.final_loss,
             "exact_series_tables_evals_per_s": out["exact_tables"],
-            "note": "speed-up comes from tabulating F per row; the exact series tabulated the "
-                    "same way (exact_series_tables) is nearly as fast (its FP64 table build "
-                    "costs more than the network's)"}
+            "exact_series_tables_fp32": {
+                "value": out["exact_tables_fp32"], "unit": "evals/s",
+                "dlogp_abs_max_near_mode": float(t_near.max()),
+                "dlogp_abs_prior_draws": {"p50": float(np.median(t_prior)),
+                                          "p90": float(np.percentile(t_prior, 90)),
+                                          "p99": float(np.percentile(t_prior, 99)),
+                                          "max": float(t_prior.max())}},
+            "note": "the speed-up over the per-sub-pixel series comes from tabulating F per "
+                    "row; exact_series_tables(_fp32) tabulate the exact series the same way "
+                    "(FP64 / FP32 build): what the network adds over tabulation is the "
+                    "difference between those figures and the surrogate's"}
 
 
 def cpu_baseline_leg(budget_s: float = 12.0) -> dict:

@@ -80,10 +80,18 @@ typedef enum {
  *                      network, interpolated (cubic Hermite) at every
  *                      sub-pixel; rows outside its training domain use the
  *                      exact series;
- *   GL_DEFL_TABLE      the same tables filled from the exact series (rows with
- *                      |e| > 0.5 use the series): differs from GL_DEFL_SERIES by
- *                      the interpolation error only. */
-typedef enum { GL_DEFL_SERIES = 0, GL_DEFL_SURROGATE = 1, GL_DEFL_TABLE = 2 } gl_deflection;
+ *   GL_DEFL_TABLE      the same tables filled from the exact series summed in
+ *                      FP64 (rows with |e| > 0.5 use the series): differs from
+ *                      GL_DEFL_SERIES by the interpolation error only;
+ *   GL_DEFL_TABLE32    the same, with the series at the table's nodes summed in
+ *                      FP32 (the build takes a fraction of the FP64 one's time on
+ *                      a GPU whose FP64 rate is 1/64 of its FP32 rate). */
+typedef enum {
+  GL_DEFL_SERIES = 0,
+  GL_DEFL_SURROGATE = 1,
+  GL_DEFL_TABLE = 2,
+  GL_DEFL_TABLE32 = 3
+} gl_deflection;
 
 /* Prior kinds (Eq. sim-dist, Sec. 4.2). */
 typedef enum {

@@ -122,10 +122,9 @@ gl_status prepare_surrogate(gl_system* s, const float* theta, int B, SysParams& 
             "surrogate table allocation");
     s->table_rows = B;
   }
-  const gl_surrogate* src = defl == GL_DEFL_TABLE ? nullptr : s->sur;
-  GL_CUDA(gl::launch_table(src, theta, s->sp.P, B, s->d_table, st), "table launch");
+  GL_CUDA(gl::launch_table(defl, s->sur, theta, s->sp.P, B, s->d_table, st), "table launch");
   sp.table = s->d_table;
-  gl::surrogate_domain(src, &sp.sq_lo, &sp.sq_hi, &sp.sg_lo, &sp.sg_hi);
+  gl::table_domain(defl, s->sur, &sp.sq_lo, &sp.sq_hi, &sp.sg_lo, &sp.sg_hi);
   return GL_OK;
 }
 
@@ -134,8 +133,7 @@ gl_status check_call(gl_system* sys, const void* theta, int B, const void* out,
   if (!sys) return fail(GL_EINVAL, "system is NULL");
   if (B < 0) return fail(GL_EINVAL, "B < 0");
   if (B > 0 && (!theta || !out)) return fail(GL_EINVAL, "NULL theta or output");
-  if (defl != GL_DEFL_SERIES && defl != GL_DEFL_SURROGATE && defl != GL_DEFL_TABLE)
-    return fail(GL_EINVAL, "unknown deflection kind");
+  if (!gl::defl_valid(defl)) return fail(GL_EINVAL, "unknown deflection kind");
   if (defl == GL_DEFL_SURROGATE && !sys->sur)
     return fail(GL_ENOSURROGATE, "no surrogate attached to this system");
   return GL_OK;
@@ -548,8 +546,7 @@ gl_status eval_prepare(gl_system* s, int B, gl_deflection defl, bool with_grad, 
       s->table_rows = B;
     }
     sp->table = s->d_table;
-    gl::surrogate_domain(defl == GL_DEFL_TABLE ? nullptr : s->sur, &sp->sq_lo, &sp->sq_hi,
-                         &sp->sg_lo, &sp->sg_hi);
+    gl::table_domain(defl, s->sur, &sp->sq_lo, &sp->sq_hi, &sp->sg_lo, &sp->sg_hi);
   }
   *dyn = with_grad ? s->grad_smem : s->fwd_smem;
   return GL_OK;
@@ -558,8 +555,8 @@ gl_status eval_prepare(gl_system* s, int B, gl_deflection defl, bool with_grad, 
 cudaError_t eval_launch(const gl_system* s, const SysParams& sp, size_t dyn, const float* theta,
                         int B, float* logp, float* grad, gl_deflection defl, cudaStream_t st) {
   if (sp.table) {
-    cudaError_t e = gl::launch_table(defl == GL_DEFL_TABLE ? nullptr : s->sur, theta, sp.P, B,
-                                     const_cast<float4*>(sp.table), st);
+    cudaError_t e =
+        gl::launch_table(defl, s->sur, theta, sp.P, B, const_cast<float4*>(sp.table), st);
     if (e != cudaSuccess) return e;
   }
   if (grad) return gl::launch_grad(sp, theta, B, logp, grad, dyn, st);

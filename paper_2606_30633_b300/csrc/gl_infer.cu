@@ -1608,8 +1608,7 @@ gl_status gl_logp_grad_backward(gl_system* sys, const float* theta, int B, float
   k_bwd_rows<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(theta, B, P, K, rows);
   GI_CUDA(cudaGetLastError(), "row launch");
   if (sf.table)
-    GI_CUDA(gl::launch_table(defl == GL_DEFL_TABLE ? nullptr : sys->sur, rows, P, B * K,
-                             const_cast<float4*>(sf.table), st),
+    GI_CUDA(gl::launch_table(defl, sys->sur, rows, P, B * K, const_cast<float4*>(sf.table), st),
             "table launch");
   GI_CUDA(gl::launch_component_images(sf, rows, B * K, imgs, df, st), "image launch");
   switch (K) {

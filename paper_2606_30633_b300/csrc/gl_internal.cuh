@@ -91,10 +91,17 @@ cudaError_t launch_leapfrog_block(const SysParams& sp, size_t dyn, float* theta,
 cudaError_t launch_grad_multi(int nL, int nS, bool surr, const SysParams* systems,
                               const void* items, int n_items, int* counter, int grid, size_t dyn,
                               cudaStream_t st);
-// Surrogate tables [B][TABLE_ROW] for the rows of theta (gl_surrogate.cu).
-cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B, float4* table,
-                         cudaStream_t st);
-void surrogate_domain(const gl_surrogate* s, float* q_lo, float* q_hi, float* g_lo, float* g_hi);
+// Per-row tables [B][TABLE_ROW] for the rows of theta (gl_surrogate.cu): from
+// the network s (defl GL_DEFL_SURROGATE) or from the exact series in FP64
+// (GL_DEFL_TABLE) or FP32 (GL_DEFL_TABLE32); s is ignored for the latter two.
+cudaError_t launch_table(int defl, const gl_surrogate* s, const float* theta, int P, int B,
+                         float4* table, cudaStream_t st);
+// The (q, gamma) domain the tables of a deflection kind cover: the network's
+// training domain for GL_DEFL_SURROGATE, |e| <= 0.5 for the exact tables.
+void table_domain(int defl, const gl_surrogate* s, float* q_lo, float* q_hi, float* g_lo,
+                  float* g_hi);
+// A valid deflection kind (gl_deflection).
+inline bool defl_valid(int defl) { return defl >= 0 && defl <= 3; }
 
 // Largest static shared memory of the forward and gradient kernels (bytes,
 // with the surrogate table), or of the multi-system kernel.

@@ -159,8 +159,7 @@ gl_status gl_multi_logp_grad(gl_multi* m, const float* const* theta, float* cons
   gl::Range nvtx_range("gl_multi_logp_grad");
   if (!m) return fail(GL_EINVAL, "multi is NULL");
   if (!theta || !logp || !grad) return fail(GL_EINVAL, "NULL pointer arrays");
-  if (defl != GL_DEFL_SERIES && defl != GL_DEFL_SURROGATE && defl != GL_DEFL_TABLE)
-    return fail(GL_EINVAL, "unknown deflection kind");
+  if (!gl::defl_valid(defl)) return fail(GL_EINVAL, "unknown deflection kind");
   const int n_sys = (int)m->systems.size();
   for (int k = 0; k < n_sys; ++k) {
     if (m->counts[k] > 0 && (!theta[k] || !logp[k] || !grad[k]))
@@ -185,8 +184,7 @@ gl_status gl_multi_logp_grad(gl_multi* m, const float* const* theta, float* cons
               "table allocation");
     for (int k = 0; k < n_sys; ++k) {
       if (!m->counts[k]) continue;
-      const gl_surrogate* src = defl == GL_DEFL_TABLE ? nullptr : m->systems[k]->sur;
-      MU_CUDA(gl::launch_table(src, theta[k], m->h_sys[k].P, m->counts[k],
+      MU_CUDA(gl::launch_table(defl, m->systems[k]->sur, theta[k], m->h_sys[k].P, m->counts[k],
                                m->d_table + m->row_offset[k] * gl::TABLE_ROW, st),
               "table launch");
     }
@@ -196,9 +194,8 @@ gl_status gl_multi_logp_grad(gl_multi* m, const float* const* theta, float* cons
     for (int k = 0; k < n_sys; ++k) {
       gl::SysParams& sp = m->h_sys[k];
       if (surr) {
-        const gl_surrogate* src = defl == GL_DEFL_TABLE ? nullptr : m->systems[k]->sur;
         sp.table = m->d_table;
-        gl::surrogate_domain(src, &sp.sq_lo, &sp.sq_hi, &sp.sg_lo, &sp.sg_hi);
+        gl::table_domain(defl, m->systems[k]->sur, &sp.sq_lo, &sp.sq_hi, &sp.sg_lo, &sp.sg_hi);
       } else {
         sp.table = nullptr;
       }

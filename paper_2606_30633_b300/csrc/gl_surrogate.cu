@@ -311,10 +311,15 @@ __device__ void write_intervals(const float4 (*node)[2], float4* __restrict__ ou
   }
 }
 
-// The same tables from the exact series (FP64 per node): F, dF/dvphi =
-// F'(z) 2iz, dF/dq = -F'(z) e^{2i vphi} df/dq, dF/dt = sum c_n h_n z^n, with
-// F'(z) = [t F - (2-t) E]/(2(1-z)) and F = 1 + zE. Rows with |e| above 0.5
-// (q < 1/3) are skipped: the lens kernels use the series there.
+// The same tables from the exact series: F, dF/dvphi = F'(z) 2iz,
+// dF/dq = -F'(z) e^{2i vphi} df/dq, dF/dt = sum c_n h_n z^n, with
+// F'(z) = [t F - (2-t) E]/(2(1-z)) and F = 1 + zE, summed per node in Real
+// (double, or float for the fast build: the terms fall below the FP32
+// rounding of F after ~30 terms at |z| <= 1/2, and the recurrences for c_n
+// and h_n are products and sums of O(1) factors, so FP32 keeps F to a few
+// ulp). Rows with |e| above 0.5 (q < 1/3) are skipped: the lens kernels use
+// the series there.
+template <class Real>
 __global__ void k_table_exact(const float* __restrict__ theta, int P, int B, float q_lo,
                               float4* __restrict__ table) {
   const int b = blockIdx.x;
@@ -324,35 +329,44 @@ __global__ void k_table_exact(const float* __restrict__ theta, int P, int B, flo
   const float cc = sqrtf(e1 * e1 + e2 * e2);
   const float qf = (1.f - cc) / (1.f + cc);
   if (!(qf >= q_lo) || !(th[1] > 1.f && th[1] < 3.f)) return;
-  const double q = qf, t = (double)th[1] - 1.0, f = (1.0 - q) / (1.0 + q);
+  const Real one = 1, two = 2;
+  const Real q = qf, t = (Real)th[1] - one, f = (one - q) / (one + q);
+  // stop once a term is below this fraction of F (~1): FP64 1e-18, FP32 2^-30
+  const Real stop = sizeof(Real) == 8 ? (Real)1e-18 : (Real)9.3e-10;
   __shared__ float4 node[TABLE_M][2];
   for (int j = threadIdx.x; j < TABLE_M; j += blockDim.x) {
     float vpf, dv;
     table_node(j, vpf, dv);
-    const double vp = vpf;
-    const double wr = cos(2.0 * vp), wi = sin(2.0 * vp);
-    const double zr = -f * wr, zi = -f * wi;
+    Real wr, wi;
+    if constexpr (sizeof(Real) == 8) {
+      wr = cos(2.0 * (double)vpf);
+      wi = sin(2.0 * (double)vpf);
+    } else {
+      sincosf(2.f * vpf, &wi, &wr);
+    }
+    const Real zr = -f * wr, zi = -f * wi;
     // E = sum_{n>=1} c_n z^{n-1}, T = sum_{n>=1} c_n h_n z^n
-    double cn = 1.0, hn = 0.0, pr = 1.0, pi = 0.0, Er = 0.0, Ei = 0.0, Tr = 0.0, Ti = 0.0;
+    Real cn = one, hn = 0, pr = one, pi = 0, Er = 0, Ei = 0, Tr = 0, Ti = 0;
     for (int n = 1; n < 2000; ++n) {
-      cn *= (2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
-      hn += 1.0 / (2.0 * n - 2.0 + t) + 1.0 / (2.0 * n + 2.0 - t);
+      const Real a = two * n - two + t, c = two * n + two - t;
+      cn *= a / c;
+      hn += one / a + one / c;
       Er += cn * pr;  // p = z^{n-1}
       Ei += cn * pi;
-      const double nr = pr * zr - pi * zi, ni = pr * zi + pi * zr;
+      const Real nr = pr * zr - pi * zi, ni = pr * zi + pi * zr;
       pr = nr;
       pi = ni;  // now z^n
       Tr += cn * hn * pr;
       Ti += cn * hn * pi;
-      if (fabs(cn) * (fabs(pr) + fabs(pi)) * (1.0 + hn) < 1e-18) break;
+      if (fabs(cn) * (fabs(pr) + fabs(pi)) * (one + hn) < stop) break;
     }
-    const double Fr = 1.0 + zr * Er - zi * Ei, Fi = zr * Ei + zi * Er;
-    const double nr = t * Fr - (2.0 - t) * Er, ni = t * Fi - (2.0 - t) * Ei;
-    const double or_ = 1.0 - zr, oi = -zi, den = 2.0 * (or_ * or_ + oi * oi);
-    const double Dr = (nr * or_ + ni * oi) / den, Di = (ni * or_ - nr * oi) / den;  // F'(z)
-    const double Pr = -2.0 * (Dr * zi + Di * zr), Pi = 2.0 * (Dr * zr - Di * zi);  // F' 2iz
-    const double dfdq = -2.0 / ((1.0 + q) * (1.0 + q));
-    const double Qr = -(Dr * wr - Di * wi) * dfdq, Qi = -(Dr * wi + Di * wr) * dfdq;
+    const Real Fr = one + zr * Er - zi * Ei, Fi = zr * Ei + zi * Er;
+    const Real nr = t * Fr - (two - t) * Er, ni = t * Fi - (two - t) * Ei;
+    const Real or_ = one - zr, oi = -zi, den = two * (or_ * or_ + oi * oi);
+    const Real Dr = (nr * or_ + ni * oi) / den, Di = (ni * or_ - nr * oi) / den;  // F'(z)
+    const Real Pr = -two * (Dr * zi + Di * zr), Pi = two * (Dr * zr - Di * zi);  // F' 2iz
+    const Real dfdq = -two / ((one + q) * (one + q));
+    const Real Qr = -(Dr * wr - Di * wi) * dfdq, Qi = -(Dr * wi + Di * wr) * dfdq;
     node[j][0] = make_float4((float)Fr, (float)Fi, (float)(dv * Pr), (float)(dv * Pi));
     node[j][1] = make_float4((float)Qr, (float)Qi, (float)Tr, (float)Ti);
   }
@@ -981,9 +995,9 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
                  "r"(TR_TMEM_COLS));
 }
 
-cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B, float4* table,
-                         cudaStream_t st) {
-  if (s) {
+cudaError_t launch_table(int defl, const gl_surrogate* s, const float* theta, int P, int B,
+                         float4* table, cudaStream_t st) {
+  if (defl == GL_DEFL_SURROGATE) {
     static thread_local int configured_dev = -1;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1004,8 +1018,10 @@ cudaError_t launch_table(const gl_surrogate* s, const float* theta, int P, int B
     if (e != cudaSuccess) return e;
     // the flag's stream-ordered copy, read by the next call that uses the surrogate
     return cudaMemcpyAsync(s->h_timeout, s->d_timeout, sizeof(int), cudaMemcpyDeviceToHost, st);
+  } else if (defl == GL_DEFL_TABLE32) {
+    k_table_exact<float><<<B, TABLE_M, 0, st>>>(theta, P, B, 1.f / 3.f, table);
   } else {
-    k_table_exact<<<B, TABLE_M, 0, st>>>(theta, P, B, 1.f / 3.f, table);
+    k_table_exact<double><<<B, TABLE_M, 0, st>>>(theta, P, B, 1.f / 3.f, table);
   }
   return cudaGetLastError();
 }
@@ -1018,8 +1034,9 @@ gl_status surrogate_take_timeout(const gl_surrogate* s) {
   return GL_ETIMEOUT;
 }
 
-void surrogate_domain(const gl_surrogate* s, float* q_lo, float* q_hi, float* g_lo, float* g_hi) {
-  if (!s) {  // tabulated exact series: |e| <= 0.5, the model's gamma range
+void table_domain(int defl, const gl_surrogate* s, float* q_lo, float* q_hi, float* g_lo,
+                  float* g_hi) {
+  if (defl != GL_DEFL_SURROGATE || !s) {  // tabulated exact series: |e| <= 0.5, the model's gamma range
     *q_lo = 1.f / 3.f;
     *q_hi = 1.f;
     *g_lo = 1.f;
