@@ -671,7 +671,7 @@ def uneven_leg(steps: int, warmup: int, world: int, local: int, sur=None,
         thetas.append(torch.tensor(W.samples().astype(np.float32), device=dev))
         rows.append(W.batch)
     n_rows = sum(rows)
-    plan, tune_ms = autotune.tune_multi(systems, rows, thetas, reps=2)
+    plan, tune = autotune.tune_multi(systems, rows, thetas, reps=2)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     logps, grads = plan.logp_grad(thetas)
@@ -718,8 +718,15 @@ def uneven_leg(steps: int, warmup: int, world: int, local: int, sur=None,
         ops += o
     peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2.032e9 / 1e12
     achieved = ops / (statistics.mean(ms) / 1e3) / 1e12
-    launches = len({(W.n_lens_light, W.n_source) for W in Ws})  # one launch per group
-    shapes = {"smem_policy": {v: k for k, v in autotune.POLICIES.items()}[plan.smem_policy]}
+    # one launch per group of (component counts, launch shape)
+    launches = len({(W.n_lens_light, W.n_source, sh) for W, sh in zip(Ws, plan.shapes())})
+    shapes = {"assignment": tune["assignment"], "smem_policy": tune["policy"],
+              "batch_ms": {a: {k: round(v, 3) for k, v in d.items()}
+                           for a, d in tune["batch_ms"].items()},
+              "per_class": {name: {"threads_per_cta": c["shape"][0], "pixel_pairs": c["shape"][1],
+                                   "systems": c["systems"],
+                                   "ms": {f"{t}x{p}": round(v, 4) for (t, p), v in c["ms"].items()}}
+                            for name, c in tune["classes"].items()}}
     plan.close()
     for s_ in systems:
         s_.close()
@@ -729,7 +736,7 @@ def uneven_leg(steps: int, warmup: int, world: int, local: int, sur=None,
         "value": value, "unit": "evals/s", "steps": steps, "warmup": warmup,
         "ms_per_step": t_ms / steps,
         "config": {"workload": "uneven-100-systems", "systems": len(Ws), "rows": n_rows,
-                   "launch_shapes": shapes, "autotune_ms": tune_ms,
+                   "launch_shapes": shapes,
                    "l2": "flushed (256 MB write) before every timed step"},
         "learned": {"value": world * n_rows / (statistics.mean(ms_sur) / 1e3), "unit": "evals/s",
                     "dlogp_abs_median": float(np.median(dl)),

@@ -158,15 +158,22 @@ gl_status gl_logp_grad_host(gl_system* sys, const float* theta_host, int B, floa
 
 /* ---------------------------------------------------------------------------
  * Uneven multi-system batches: many systems (different image sizes,
- * supersampling, component counts), each with its own rows, per call. One
- * persistent launch per (n_lens_light, n_source) group evaluates all rows of
- * the group; rows are taken heaviest system first from a device work queue.
+ * supersampling, component counts), each with its own rows, per call (the
+ * batched structure of Sec. 3.1 over the simulated systems of Sec. 4.2). One
+ * persistent launch per group of systems sharing (n_lens_light, n_source)
+ * and launch shape evaluates all rows of the group; rows are taken heaviest
+ * system first from a device work queue. The groups' launches run
+ * concurrently on streams the plan owns (so one group's tail overlaps the
+ * next group's start), forked from and joined back into the caller's stream:
+ * the call stays stream-ordered for the caller.
  * ------------------------------------------------------------------------- */
 typedef struct gl_multi gl_multi;
 
 /* Shared-memory policies for the image buffers of a multi-system launch:
  *   0  all buffers in global scratch (occupancy set by registers alone);
- *   1  shared memory while two CTAs fit per SM, the rest in global scratch;
+ *   1  shared memory while the launch shape's full occupancy still fits
+ *      (two CTAs of 256 threads or four of 128 per SM), the rest in global
+ *      scratch;
  *   2  shared memory up to one CTA per SM.
  * Which is fastest depends on the size mix; the package's autotuner times them. */
 enum { GL_MULTI_SMEM_GLOBAL = 0, GL_MULTI_SMEM_TWO_CTAS = 1, GL_MULTI_SMEM_ONE_CTA = 2 };
@@ -177,10 +184,24 @@ enum { GL_MULTI_SMEM_GLOBAL = 0, GL_MULTI_SMEM_TWO_CTAS = 1, GL_MULTI_SMEM_ONE_C
 gl_status gl_multi_create(gl_system* const* systems, int n_sys, const int* rows_per_sys,
                           int smem_policy, gl_multi** out);
 
+/* The same with a launch shape per system (the tile shape that the package's
+ * autotuner picks per image class): threads_per_cta[k] in {128, 256} (CTAs
+ * of 128 threads run four per SM, of 256 two, at 128 registers a thread) and
+ * pixel_pairs[k] in {2, 3}, the pixel pairs each thread keeps in flight in
+ * the forward binning (more independent work per thread for the latency of
+ * the MUFU/FP32 chain). Either array may be NULL: 256 threads, 2 pairs (the
+ * shape of gl_logp_grad, whose results the default shape reproduces bit for
+ * bit; other shapes sum the chi^2 and gradient terms in another order, so
+ * they agree to FP32 reassociation). Other values: GL_EINVAL. */
+gl_status gl_multi_create_ex(gl_system* const* systems, int n_sys, const int* rows_per_sys,
+                             int smem_policy, const int* threads_per_cta,
+                             const int* pixel_pairs, gl_multi** out);
+
 /* log p and gradient of every row of every system: theta[k] device
  * [rows_k][P_k], logp[k] device [rows_k], grad[k] device [rows_k][P_k] (host
  * arrays of device pointers). Results equal gl_logp_grad per system with the
- * same deflection. The work lists are re-uploaded when a pointer changes. */
+ * same deflection (bit for bit in the default launch shape). The work lists
+ * are re-uploaded when a pointer changes. */
 gl_status gl_multi_logp_grad(gl_multi* multi, const float* const* theta, float* const* logp,
                              float* const* grad, gl_deflection defl, void* stream);
 

@@ -83,6 +83,8 @@ SIGNATURES = {
     "gl_surrogate_destroy": (None, [_VP]),
     "gl_system_set_surrogate": (ctypes.c_int, [_VP, _VP]),
     "gl_multi_create": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "gl_multi_create_ex": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
+                                          ctypes.POINTER(_VP)]),
     "gl_multi_logp_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     "gl_multi_destroy": (ctypes.c_int, [_VP]),
     "gl_bijector_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
@@ -213,6 +215,7 @@ class System:
         _check(lib.gl_system_create(ctypes.byref(desc), ctypes.byref(h)))
         self._h = h
         self.ny, self.nx, self.P = ny, nx, int(lib.gl_system_num_params(h))
+        self.s, self.psf_size = int(supersample), int(psf.shape[0])
         self.n_lens_light, self.n_source = n_lens_light, n_source
 
     @property
@@ -476,21 +479,34 @@ class Hmc:
 
 
 class Multi:
-    """An uneven multi-system batch plan (gl_multi_create / gl_multi_logp_grad)."""
+    """An uneven multi-system batch plan (gl_multi_create_ex /
+    gl_multi_logp_grad). threads / pairs: per-system launch shapes (threads per
+    CTA in {128, 256}, phase-1 pixel pairs in {2, 3}); None gives 256 / 2."""
 
-    def __init__(self, systems, rows, smem_policy: int = GL_MULTI_SMEM_TWO_CTAS):
+    def __init__(self, systems, rows, smem_policy: int = GL_MULTI_SMEM_TWO_CTAS,
+                 threads: Optional[Sequence[int]] = None, pairs: Optional[Sequence[int]] = None):
         self._lib = load()
         self.systems = list(systems)
         self.rows = [int(r) for r in rows]
-        if len(self.rows) != len(self.systems):
+        n = len(self.systems)
+        if len(self.rows) != n:
             raise ValueError("one row count per system")
-        hs = (_VP * len(self.systems))(*[s.handle for s in self.systems])
-        rs = (ctypes.c_int * len(self.rows))(*self.rows)
+        self.threads = [256] * n if threads is None else [int(t) for t in threads]
+        self.pairs = [2] * n if pairs is None else [int(p) for p in pairs]
+        if len(self.threads) != n or len(self.pairs) != n:
+            raise ValueError("one launch shape per system")
+        hs = (_VP * n)(*[s.handle for s in self.systems])
+        rs = (ctypes.c_int * n)(*self.rows)
+        ts = (ctypes.c_int * n)(*self.threads)
+        ps = (ctypes.c_int * n)(*self.pairs)
         h = _VP()
-        _check(self._lib.gl_multi_create(hs, len(self.systems), rs, int(smem_policy),
-                                         ctypes.byref(h)))
+        _check(self._lib.gl_multi_create_ex(hs, n, rs, int(smem_policy), ts, ps, ctypes.byref(h)))
         self._h = h
         self.smem_policy = smem_policy
+
+    def shapes(self):
+        """(threads per CTA, pixel pairs) of each system."""
+        return list(zip(self.threads, self.pairs))
 
     def logp_grad(self, thetas, logps=None, grads=None, defl: int = GL_DEFL_SERIES, stream=None):
         """thetas: list of CUDA float32 [rows_k, P_k]; returns lists of logp, grad."""

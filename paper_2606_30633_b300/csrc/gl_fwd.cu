@@ -30,11 +30,11 @@ cudaError_t launch_component_images(const SysParams& sp, const float* theta, int
   return cudaGetLastError();
 }
 
-size_t static_smem_bytes(bool multi) {
+size_t static_smem_bytes(bool multi, int threads) {
   // SmemStatic + the table (+ k_grad_multi's work index and parameter
   // block), with alignment slack
-  return sizeof(SmemStatic) + TABLE_ROW * sizeof(float4) + 256 +
-         (multi ? sizeof(SysParams) + 16 : 0);
+  const size_t smem_static = threads == 128 ? sizeof(SmemStatic<4>) : sizeof(SmemStatic<NWARPS>);
+  return smem_static + TABLE_ROW * sizeof(float4) + 256 + (multi ? sizeof(SysParams) + 16 : 0);
 }
 
 cudaError_t set_smem_limits_fwd(size_t block_max) {

@@ -21,13 +21,15 @@ cudaError_t launch_grad(const SysParams& sp, const float* theta, int B, float* l
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_grad_multi(int nL, int nS, bool surr, const SysParams* systems,
-                              const void* items, int n_items, int* counter, int grid, size_t dyn,
-                              cudaStream_t st) {
-#define GL_CASE(a, b)                                                                          \
-  if (nL == a && nS == b)                                                                      \
-    return surr ? grad_multi_launch<a, b, true>(systems, items, n_items, counter, grid, dyn, st) \
-                : grad_multi_launch<a, b, false>(systems, items, n_items, counter, grid, dyn, st);
+cudaError_t launch_grad_multi(int nL, int nS, bool surr, int threads, int pairs,
+                              const SysParams* systems, const void* items, int n_items,
+                              int* counter, int grid, size_t dyn, cudaStream_t st) {
+#define GL_CASE(a, b)                                                                        \
+  if (nL == a && nS == b)                                                                    \
+    return surr ? grad_multi_launch<a, b, true>(threads, pairs, systems, items, n_items,     \
+                                                counter, grid, dyn, st)                      \
+                : grad_multi_launch<a, b, false>(threads, pairs, systems, items, n_items,    \
+                                                 counter, grid, dyn, st);
   GL_CASE(0, 1) GL_CASE(0, 2) GL_CASE(0, 3)
   GL_CASE(1, 1) GL_CASE(1, 2) GL_CASE(1, 3)
   GL_CASE(2, 1) GL_CASE(2, 2) GL_CASE(2, 3)
@@ -37,13 +39,12 @@ cudaError_t launch_grad_multi(int nL, int nS, bool surr, const SysParams* system
 
 cudaError_t set_smem_limits_grad(size_t block_max) {
   // dynamic limit = the per-block maximum less each kernel's static memory
-  const size_t st = static_smem_bytes(false), sm = static_smem_bytes(true);
+  const size_t st = static_smem_bytes(false);
   const size_t bytes = block_max > st ? block_max - st : 0;
-  const size_t bytes_multi = block_max > sm ? block_max - sm : 0;
   cudaError_t e = cudaSuccess;
 #define GL_SET(a, b) \
-  if (e == cudaSuccess) e = grad_smem<a, b, false>(bytes, bytes_multi); \
-  if (e == cudaSuccess) e = grad_smem<a, b, true>(bytes, bytes_multi);
+  if (e == cudaSuccess) e = grad_smem<a, b, false>(bytes, block_max); \
+  if (e == cudaSuccess) e = grad_smem<a, b, true>(bytes, block_max);
   GL_SET(0, 1) GL_SET(0, 2) GL_SET(0, 3)
   GL_SET(1, 1) GL_SET(1, 2) GL_SET(1, 3)
   GL_SET(2, 1) GL_SET(2, 2) GL_SET(2, 3)

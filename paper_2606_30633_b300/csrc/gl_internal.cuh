@@ -87,10 +87,11 @@ cudaError_t launch_grad(const SysParams& sp, const float* theta, int B, float* l
 cudaError_t launch_leapfrog_block(const SysParams& sp, size_t dyn, float* theta, float* p,
                                   float* logp, float* grad, const float* inv_mass, float eps,
                                   int n_steps, int B, cudaStream_t st);
-// Persistent forward + adjoint over multi-system work items (MultiItem array).
-cudaError_t launch_grad_multi(int nL, int nS, bool surr, const SysParams* systems,
-                              const void* items, int n_items, int* counter, int grid, size_t dyn,
-                              cudaStream_t st);
+// Persistent forward + adjoint over multi-system work items (MultiItem array),
+// launch shape (threads per CTA 128 or 256, phase-1 pixel pairs 2 or 3).
+cudaError_t launch_grad_multi(int nL, int nS, bool surr, int threads, int pairs,
+                              const SysParams* systems, const void* items, int n_items,
+                              int* counter, int grid, size_t dyn, cudaStream_t st);
 // Per-row tables [B][TABLE_ROW] for the rows of theta (gl_surrogate.cu): from
 // the network s (defl GL_DEFL_SURROGATE) or from the exact series in FP64
 // (GL_DEFL_TABLE) or FP32 (GL_DEFL_TABLE32); s is ignored for the latter two.
@@ -104,8 +105,9 @@ void table_domain(int defl, const gl_surrogate* s, float* q_lo, float* q_hi, flo
 inline bool defl_valid(int defl) { return defl >= 0 && defl <= 3; }
 
 // Largest static shared memory of the forward and gradient kernels (bytes,
-// with the surrogate table), or of the multi-system kernel.
-size_t static_smem_bytes(bool multi = false);
+// with the surrogate table), or of the multi-system kernel of CTAs of
+// `threads` threads.
+size_t static_smem_bytes(bool multi = false, int threads = THREADS);
 // Sets the kernels' dynamic shared-memory limit from the device's per-block
 // maximum (each kernel's own static memory deducted).
 cudaError_t set_smem_limits_fwd(size_t block_max);

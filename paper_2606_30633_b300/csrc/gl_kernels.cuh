@@ -20,20 +20,21 @@
 namespace gl {
 
 // ---------------------------------------------------------------- conv ----
-// Correlation of a zero-padded buffer: out(i, j) = sum_{u,v} k[u][v] in(i+u, j+v).
+// Correlation of a zero-padded buffer: out(i, j) = sum_{u,v} k[u][v] in(i+u, j+v),
+// by a CTA of T threads.
 // Each thread computes ROWS_STRIP outputs of one column; lanes own adjacent
 // columns (conflict-free loads); taps are compile-time indices into the
 // kernel's parameter block.
 // RELOAD (parameter block in shared memory): the tap columns are a loop
 // unrolled by 3, so a few columns of taps are live (fully unrolled, the
 // compiler hoisted all K^2 shared-memory taps into registers and spilled).
-template <int K, bool CONV, bool RELOAD, class Epi>
+template <int T, int K, bool CONV, bool RELOAD, class Epi>
 __device__ __forceinline__ void correlate_fixed(const SysParams& sp, const float* in, Epi epi) {
   constexpr int RS = ROWS_STRIP;
   const int ny = sp.ny, nx = sp.nx, Wp = sp.Wp;
   const int nrb = (ny + RS - 1) / RS;
   const int total = nrb * nx;
-  for (int s = threadIdx.x; s < total; s += THREADS) {
+  for (int s = threadIdx.x; s < total; s += T) {
     const int rb = s / nx;
     const int j = s - rb * nx;
     const int i0 = rb * RS;
@@ -66,10 +67,10 @@ __device__ __forceinline__ void correlate_fixed(const SysParams& sp, const float
   }
 }
 
-template <bool CONV, class Epi>
+template <int T, bool CONV, class Epi>
 __device__ __forceinline__ void correlate_generic(const SysParams& sp, const float* in, Epi epi) {
   const int ny = sp.ny, nx = sp.nx, Wp = sp.Wp, ky = sp.ky, kx = sp.kx;
-  for (int s = threadIdx.x; s < ny * nx; s += THREADS) {
+  for (int s = threadIdx.x; s < ny * nx; s += T) {
     const int i = s / nx;
     const int j = s - i * nx;
     float acc = 0.f;
@@ -81,21 +82,23 @@ __device__ __forceinline__ void correlate_generic(const SysParams& sp, const flo
   }
 }
 
-template <bool CONV, bool RELOAD = false, class Epi>
+template <int T, bool CONV, bool RELOAD = false, class Epi>
 __device__ __forceinline__ void correlate(const SysParams& sp, const float* in, Epi epi) {
   if (sp.ky == 11 && sp.kx == 11)
-    correlate_fixed<11, CONV, RELOAD>(sp, in, epi);
+    correlate_fixed<T, 11, CONV, RELOAD>(sp, in, epi);
   else if (sp.ky == 21 && sp.kx == 21)
-    correlate_fixed<21, CONV, RELOAD>(sp, in, epi);
+    correlate_fixed<T, 21, CONV, RELOAD>(sp, in, epi);
   else
-    correlate_generic<CONV>(sp, in, epi);
+    correlate_generic<T, CONV>(sp, in, epi);
 }
 
 // Zero the halo of a padded buffer (the interior is written by a phase).
-// first_thread: the threads taking part start at this index (warp 0 may be busy).
+// first_thread: the threads taking part start at this index (warp 0 may be busy);
+// T threads in the CTA.
+template <int T>
 __device__ __forceinline__ void zero_halo(const SysParams& sp, float* buf, int first_thread) {
   const int Hp = sp.Hp, Wp = sp.Wp;
-  const int t0 = (int)threadIdx.x - first_thread, nt = THREADS - first_thread;
+  const int t0 = (int)threadIdx.x - first_thread, nt = T - first_thread;
   if (t0 < 0) return;
   const int top = sp.cy * Wp;                        // rows [0, cy)
   const int bot0 = (sp.cy + sp.ny) * Wp, bot = Hp * Wp - bot0;  // rows [cy+ny, Hp)
@@ -111,14 +114,14 @@ __device__ __forceinline__ void zero_halo(const SysParams& sp, float* buf, int f
   }
 }
 
-// Pixel (i, j) walk for p = threadIdx.x + it * THREADS without a division per step.
+// Pixel (i, j) walk for p = threadIdx.x + it * step without a division per step.
 struct PixelWalk {
   int i, j, di, dj, nx;
-  __device__ __forceinline__ PixelWalk(int nx_) : nx(nx_) {
+  __device__ __forceinline__ PixelWalk(int nx_, int step) : nx(nx_) {
     i = (int)threadIdx.x / nx_;
     j = (int)threadIdx.x - i * nx_;
-    di = THREADS / nx_;
-    dj = THREADS - di * nx_;
+    di = step / nx_;
+    dj = step - di * nx_;
   }
   __device__ __forceinline__ void next() {
     i += di;
@@ -128,6 +131,7 @@ struct PixelWalk {
 };
 
 // ---------------------------------------------------------- reductions ----
+template <int NW>
 __device__ __forceinline__ double block_sum_double(double v, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -136,21 +140,24 @@ __device__ __forceinline__ double block_sum_double(double v, double* red) {
   __syncthreads();
   double s = 0.0;
   if (threadIdx.x == 0)
-    for (int k = 0; k < NWARPS; ++k) s += red[k];
+    for (int k = 0; k < NW; ++k) s += red[k];
   return s;  // valid on thread 0
 }
 
 // ---------------------------------------------------------------- kernels ----
+// Shared memory of a CTA of NW warps.
+template <int NW>
 struct AdjSums {
-  float redP[NWARPS][MAX_P];
+  float redP[NW][MAX_P];
   double gsum[MAX_P];
 };
 // Static shared memory of the kernels (static_smem_bytes() tells the host).
+template <int NW>
 struct SmemStatic {
   SampleC sc;
   FinishC fin[MAX_COMP + 1];
-  double red[NWARPS];
-  AdjSums adj;
+  double red[NW];
+  AdjSums<NW> adj;
 };
 
 __device__ __forceinline__ void buffers(const SysParams& sp, float* dsm, bool two, float*& A,
@@ -170,14 +177,42 @@ __device__ __forceinline__ void buffers(const SysParams& sp, float* dsm, bool tw
 // p + 2T, p + 3T; two interleaved pairs) while all four exist, then pairs,
 // where a missing second pixel repeats the first and is not written.
 // eval4(x0, y0, x1, y1, sb0, sb1) and eval2(x, y) give the brightness at two
-// pairs and at one pair of sub-pixel centres.
-template <class Eval4, class Eval2>
+// pairs and at one pair of sub-pixel centres. T threads in the CTA.
+template <int T, class Eval2>
+__device__ __forceinline__ void bin_tail(const SysParams& sp, float* A, PixelWalk w0, int p,
+                                         Eval2 eval2) {
+  const int s = sp.s, npix = sp.ny * sp.nx, Wp = sp.Wp, cy = sp.cy, cx = sp.cx;
+  const float2 D = f2(sp.D), scale = f2(sp.scale);
+  for (; p < npix; p += 2 * T) {
+    PixelWalk w1 = w0;
+    w1.next();
+    const bool v1 = p + T < npix;
+    const int i1 = v1 ? w1.i : w0.i, j1 = v1 ? w1.j : w0.j;
+    const float2 xj = make_float2((float)w0.j + sp.xg0, (float)j1 + sp.xg0);
+    const float2 yi = make_float2((float)w0.i + sp.yg0, (float)i1 + sp.yg0);
+    float2 acc = f2(0.f);
+    for (int k = 0; k < s; ++k) {
+      const float2 y = mul2(add2(yi, f2(sp.off[k])), D);
+      for (int l = 0; l < s; ++l) {
+        const float2 x = mul2(add2(xj, f2(sp.off[l])), D);
+        acc = add2(acc, eval2(x, y));
+      }
+    }
+    acc = mul2(acc, scale);
+    A[(size_t)(w0.i + cy) * Wp + w0.j + cx] = acc.x;
+    if (v1) A[(size_t)(w1.i + cy) * Wp + w1.j + cx] = acc.y;
+    w0 = w1;
+    w0.next();
+  }
+}
+
+template <int T, class Eval4, class Eval2>
 __device__ __forceinline__ void bin_loop(const SysParams& sp, float* A, Eval4 eval4, Eval2 eval2) {
   const int s = sp.s, npix = sp.ny * sp.nx, Wp = sp.Wp, cy = sp.cy, cx = sp.cx;
   const float2 D = f2(sp.D), scale = f2(sp.scale);
-  PixelWalk w0(sp.nx);
+  PixelWalk w0(sp.nx, T);
   int p = threadIdx.x;
-  for (; p + 3 * THREADS < npix; p += 4 * THREADS) {
+  for (; p + 3 * T < npix; p += 4 * T) {
     PixelWalk w1 = w0;
     w1.next();
     PixelWalk w2 = w1;
@@ -210,33 +245,77 @@ __device__ __forceinline__ void bin_loop(const SysParams& sp, float* A, Eval4 ev
     w0 = w3;
     w0.next();
   }
-  for (; p < npix; p += 2 * THREADS) {
-    PixelWalk w1 = w0;
-    w1.next();
-    const bool v1 = p + THREADS < npix;
-    const int i1 = v1 ? w1.i : w0.i, j1 = v1 ? w1.j : w0.j;
-    const float2 xj = make_float2((float)w0.j + sp.xg0, (float)j1 + sp.xg0);
-    const float2 yi = make_float2((float)w0.i + sp.yg0, (float)i1 + sp.yg0);
-    float2 acc = f2(0.f);
-    for (int k = 0; k < s; ++k) {
-      const float2 y = mul2(add2(yi, f2(sp.off[k])), D);
-      for (int l = 0; l < s; ++l) {
-        const float2 x = mul2(add2(xj, f2(sp.off[l])), D);
-        acc = add2(acc, eval2(x, y));
-      }
-    }
-    acc = mul2(acc, scale);
-    A[(size_t)(w0.i + cy) * Wp + w0.j + cx] = acc.x;
-    if (v1) A[(size_t)(w1.i + cy) * Wp + w1.j + cx] = acc.y;
-    w0 = w1;
-    w0.next();
-  }
+  bin_tail<T>(sp, A, w0, p, eval2);
 }
 
-template <int NL, int NS, bool TAB>
+// The same with six pixels per thread (three interleaved pairs) while all six
+// exist: eval6(x, y, sb) gives the brightness at the three pairs x[k], y[k].
+// More independent work per thread for the forward's MUFU/FP32 latency chain.
+template <int T, class Eval6, class Eval2>
+__device__ __forceinline__ void bin_loop6(const SysParams& sp, float* A, Eval6 eval6, Eval2 eval2) {
+  const int s = sp.s, npix = sp.ny * sp.nx, Wp = sp.Wp, cy = sp.cy, cx = sp.cx;
+  const float2 D = f2(sp.D), scale = f2(sp.scale);
+  PixelWalk w0(sp.nx, T);
+  int p = threadIdx.x;
+  for (; p + 5 * T < npix; p += 6 * T) {
+    int wi[6], wj[6];
+    {
+      PixelWalk t = w0;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        wi[m] = t.i;
+        wj[m] = t.j;
+        if (m < 5) t.next();
+      }
+      w0 = t;
+    }
+    float2 xj[3], yi[3], acc[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      xj[m] = make_float2((float)wj[2 * m] + sp.xg0, (float)wj[2 * m + 1] + sp.xg0);
+      yi[m] = make_float2((float)wi[2 * m] + sp.yg0, (float)wi[2 * m + 1] + sp.yg0);
+      acc[m] = f2(0.f);
+    }
+    for (int k = 0; k < s; ++k) {
+      const float2 ok = f2(sp.off[k]);
+      float2 y[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) y[m] = mul2(add2(yi[m], ok), D);
+      for (int l = 0; l < s; ++l) {
+        const float2 ol = f2(sp.off[l]);
+        float2 x[3], sb[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) x[m] = mul2(add2(xj[m], ol), D);
+        eval6(x, y, sb);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) acc[m] = add2(acc[m], sb[m]);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      acc[m] = mul2(acc[m], scale);
+      A[(size_t)(wi[2 * m] + cy) * Wp + wj[2 * m] + cx] = acc[m].x;
+      A[(size_t)(wi[2 * m + 1] + cy) * Wp + wj[2 * m + 1] + cx] = acc[m].y;
+    }
+    w0.next();
+  }
+  bin_tail<T>(sp, A, w0, p, eval2);
+}
+
+// Phase 1 with NPR pixel pairs per thread in flight (2 or 3).
+template <int T, int NPR, int NL, int NS, bool TAB>
 __device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& sc,
                                            const float4* tab, float* A) {
-  bin_loop(
+  if constexpr (NPR == 3) {
+    bin_loop6<T>(
+        sp, A,
+        [&](const float2* x, const float2* y, float2* sb) {
+          surface_brightness6<NL, NS, TAB>(reload(sc), tab, x, y, sb);
+        },
+        [&](float2 x, float2 y) { return surface_brightness2<NL, NS, TAB>(reload(sc), tab, x, y); });
+    return;
+  }
+  bin_loop<T>(
       sp, A,
       [&](float2 x0, float2 y0, float2 x1, float2 y1, float2& sb0, float2& sb1) {
         surface_brightness4<NL, NS, TAB>(reload(sc), tab, x0, y0, x1, y1, sb0, sb1);
@@ -246,10 +325,10 @@ __device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& s
 
 // Phase 1 for the image of one light component c (a source when source is
 // set): the same walk with only that component evaluated.
-template <bool TAB>
+template <int T, bool TAB>
 __device__ __forceinline__ void bin_component(const SysParams& sp, const SampleC& sc,
                                               const float4* tab, float* A, int c, bool source) {
-  bin_loop(
+  bin_loop<T>(
       sp, A,
       [&](float2 x0, float2 y0, float2 x1, float2 y1, float2& sb0, float2& sb1) {
         component_brightness4<TAB>(reload(sc), tab, c, source, x0, y0, x1, y1, sb0, sb1);
@@ -264,7 +343,7 @@ __device__ __forceinline__ void bin_component(const SysParams& sp, const SampleC
 // flushed into the per-warp sums redP every FLUSH_IT pairs, which bounds the
 // FP32 accumulation length (near the mode the gradient is a small difference
 // of large sums).
-template <int NL, int NS, bool TAB>
+template <int T, int NL, int NS, bool TAB>
 __device__ __forceinline__ void adjoint_pixels(const SysParams& sp, const SampleC& sc,
                                                const float4* tab, const float* A,
                                                float (*redP)[MAX_P]) {
@@ -278,14 +357,14 @@ __device__ __forceinline__ void adjoint_pixels(const SysParams& sp, const Sample
   AccT acc[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) acc[k] = acc_zero<AccT>();
-  const int iters = (npix + 2 * THREADS - 1) / (2 * THREADS);  // the same in every lane
-  PixelWalk w0(sp.nx);
+  const int iters = (npix + 2 * T - 1) / (2 * T);  // the same in every lane
+  PixelWalk w0(sp.nx, T);
   for (int it = 0; it < iters; ++it) {
-    const int p = threadIdx.x + 2 * it * THREADS;
+    const int p = threadIdx.x + 2 * it * T;
     PixelWalk w1 = w0;
     w1.next();
     if (p < npix) {
-      const bool v1 = p + THREADS < npix;
+      const bool v1 = p + T < npix;
       const int i1 = v1 ? w1.i : w0.i, j1 = v1 ? w1.j : w0.j;
       const float u0 = A[(size_t)(w0.i + cy) * Wp + w0.j + cx];
       const float u1 = v1 ? A[(size_t)(i1 + cy) * Wp + j1 + cx] : 0.f;
@@ -339,10 +418,10 @@ __device__ __forceinline__ void adjoint_pixels(const SysParams& sp, const Sample
 }
 
 // The row's surrogate table into shared memory (when the row uses it).
-template <bool SURR>
+template <int T, bool SURR>
 __device__ __forceinline__ void load_table(const float4* src, const SampleC& sc, float4* tab) {
   if (SURR && sc.use_table) {
-    for (int k = threadIdx.x; k < TABLE_ROW; k += THREADS) tab[k] = src[k];
+    for (int k = threadIdx.x; k < TABLE_ROW; k += T) tab[k] = src[k];
   }
   __syncthreads();
 }
@@ -361,7 +440,7 @@ __global__ void __launch_bounds__(THREADS, 2)
 k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta, int B,
           float* __restrict__ logp, float* __restrict__ img) {
   extern __shared__ __align__(16) float dsm[];
-  __shared__ SmemStatic st;
+  __shared__ SmemStatic<NWARPS> st;
   __shared__ float4 tab[SURR ? TABLE_ROW : 1];
   SampleC& sc = st.sc;
   const int b = blockIdx.x;
@@ -372,7 +451,7 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
   if (threadIdx.x < 32)
     stage_warp(sp, theta + (size_t)b * sp.P, sc, st.fin, !want_img);
   else
-    zero_halo(sp, A, 32);
+    zero_halo<THREADS>(sp, A, 32);
   __syncthreads();
   const int npix = sp.ny * sp.nx;
   if (sc.status != 0) {
@@ -383,7 +462,7 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
     }
     return;
   }
-  load_table<SURR>(sp.table + (size_t)blockIdx.x * TABLE_ROW, sc, tab);
+  load_table<THREADS, SURR>(sp.table + (size_t)blockIdx.x * TABLE_ROW, sc, tab);
   if (table_failed<SURR>(sc, tab)) {
     if (want_img) {
       for (int p = threadIdx.x; p < npix; p += THREADS) img[(size_t)b * npix + p] = __int_as_float(0x7fc00000);
@@ -393,13 +472,13 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
     return;
   }
   if (SURR && sc.use_table)
-    bin_pixels<NL, NS, true>(sp, sc, tab, A);
+    bin_pixels<THREADS, 2, NL, NS, true>(sp, sc, tab, A);
   else
-    bin_pixels<NL, NS, false>(sp, sc, tab, A);
+    bin_pixels<THREADS, 2, NL, NS, false>(sp, sc, tab, A);
   __syncthreads();
   float csum = 0.f, ccomp = 0.f;
   float* out = want_img ? img + (size_t)b * npix : nullptr;
-  correlate<true>(sp, A, [&](int i, int j, float m) {
+  correlate<THREADS, true>(sp, A, [&](int i, int j, float m) {
     const int idx = i * sp.nx + j;
     if (want_img) {
       out[idx] = m;
@@ -412,7 +491,7 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
     }
   });
   if (want_img) return;
-  const double chi2 = block_sum_double((double)csum - (double)ccomp, st.red);
+  const double chi2 = block_sum_double<NWARPS>((double)csum - (double)ccomp, st.red);
   if (threadIdx.x == 0) logp[b] = (float)(-0.5 * chi2 + sc.logprior);
 }
 
@@ -425,7 +504,7 @@ __global__ void __launch_bounds__(THREADS, 2)
 k_component_images(const __grid_constant__ SysParams sp, const float* __restrict__ theta, int B,
                    float* __restrict__ img) {
   extern __shared__ __align__(16) float dsm[];
-  __shared__ SmemStatic st;
+  __shared__ SmemStatic<NWARPS> st;
   __shared__ float4 tab[SURR ? TABLE_ROW : 1];
   SampleC& sc = st.sc;
   const int b = blockIdx.x;
@@ -435,7 +514,7 @@ k_component_images(const __grid_constant__ SysParams sp, const float* __restrict
   if (threadIdx.x < 32)
     stage_warp(sp, theta + (size_t)b * sp.P, sc, st.fin, false);
   else
-    zero_halo(sp, A, 32);
+    zero_halo<THREADS>(sp, A, 32);
   __syncthreads();
   const int npix = sp.ny * sp.nx;
   float* out = img + (size_t)b * npix;
@@ -450,40 +529,42 @@ k_component_images(const __grid_constant__ SysParams sp, const float* __restrict
       break;
     }
   const bool source = c >= sp.nL;
-  load_table<SURR>(sp.table + (size_t)blockIdx.x * TABLE_ROW, sc, tab);
+  load_table<THREADS, SURR>(sp.table + (size_t)blockIdx.x * TABLE_ROW, sc, tab);
   if (source && table_failed<SURR>(sc, tab)) {
     for (int p = threadIdx.x; p < npix; p += THREADS) out[p] = __int_as_float(0x7fc00000);
     return;
   }
   if (SURR && sc.use_table && source)
-    bin_component<true>(sp, sc, tab, A, c, source);
+    bin_component<THREADS, true>(sp, sc, tab, A, c, source);
   else
-    bin_component<false>(sp, sc, tab, A, c, source);
+    bin_component<THREADS, false>(sp, sc, tab, A, c, source);
   __syncthreads();
-  correlate<true>(sp, A, [&](int i, int j, float m) { out[i * sp.nx + j] = m; });
+  correlate<THREADS, true>(sp, A, [&](int i, int j, float m) { out[i * sp.nx + j] = m; });
 }
 
-// Forward + adjoint of one row (all threads of the CTA): log p and
+// Forward + adjoint of one row (all T threads of the CTA): log p and
 // d log p / d theta of theta row th into *logp_out and grad_out[0..P).
-// slot_index picks the CTA's global-scratch slot, table_row the row's table.
+// slot_index picks the CTA's global-scratch slot, table_row the row's table;
+// NPR pixel pairs per thread in flight in phase 1 (2 or 3).
 // Ends with a block barrier, so a persistent CTA can start its next row.
-template <int NL, int NS, bool SURR, bool MULTI = false>
+template <int NL, int NS, bool SURR, bool MULTI, int T, int NPR>
 __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __restrict__ th,
                                          float* __restrict__ logp_out,
                                          float* __restrict__ grad_out,
                                          const float4* __restrict__ table_row, int slot_index,
-                                         float* dsm, SmemStatic& st, float4* tab) {
+                                         float* dsm, SmemStatic<T / 32>& st, float4* tab) {
   constexpr int P = 8 + 7 * (NL + NS);
+  constexpr int NW = T / 32;
   SampleC& sc = st.sc;
   float *A, *Bf;
   buffers(sp, dsm, true, A, Bf, slot_index);
   if (threadIdx.x < 32) {
     stage_warp(sp, th, sc, st.fin, true);
   } else {
-    zero_halo(sp, A, 32);
-    zero_halo(sp, Bf, 32);
+    zero_halo<T>(sp, A, 32);
+    zero_halo<T>(sp, Bf, 32);
   }
-  for (int k = threadIdx.x; k < NWARPS * MAX_P; k += THREADS) (&st.adj.redP[0][0])[k] = 0.f;
+  for (int k = threadIdx.x; k < NW * MAX_P; k += T) (&st.adj.redP[0][0])[k] = 0.f;
   __syncthreads();
   if (sc.status != 0) {
     const float lv = sc.status == 2 ? __int_as_float(0x7fc00000) : -__int_as_float(0x7f800000);
@@ -493,7 +574,7 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
     __syncthreads();
     return;
   }
-  load_table<SURR>(table_row, sc, tab);
+  load_table<T, SURR>(table_row, sc, tab);
   if (table_failed<SURR>(sc, tab)) {
     if (threadIdx.x == 0) *logp_out = __int_as_float(0x7fc00000);
     if (threadIdx.x < P) grad_out[threadIdx.x] = __int_as_float(0x7fc00000);
@@ -504,13 +585,13 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
   const int Wp = sp.Wp, cy = sp.cy, cx = sp.cx, nx = sp.nx;
   // phase 1
   if (use_tab)
-    bin_pixels<NL, NS, true>(sp, sc, tab, A);
+    bin_pixels<T, NPR, NL, NS, true>(sp, sc, tab, A);
   else
-    bin_pixels<NL, NS, false>(sp, sc, tab, A);
+    bin_pixels<T, NPR, NL, NS, false>(sp, sc, tab, A);
   __syncthreads();
   // phase 2
   float csum = 0.f, ccomp = 0.f;
-  correlate<true, MULTI>(sp, A, [&](int i, int j, float m) {
+  correlate<T, true, MULTI>(sp, A, [&](int i, int j, float m) {
     const int idx = i * nx + j;
     const float r = sp.data[idx] - m;
     const float wr = sp.w[idx] * r;
@@ -520,23 +601,23 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
     csum = t;
     Bf[(size_t)(i + cy) * Wp + j + cx] = wr;
   });
-  const double chi2 = block_sum_double((double)csum - (double)ccomp, st.red);
+  const double chi2 = block_sum_double<NW>((double)csum - (double)ccomp, st.red);
   // (block_sum_double synchronised the block: phase 2 is complete)
   // phase 3
   const float scale = sp.scale;
-  correlate<false, MULTI>(sp, Bf, [&](int i, int j, float g) {
+  correlate<T, false, MULTI>(sp, Bf, [&](int i, int j, float g) {
     A[(size_t)(i + cy) * Wp + j + cx] = g * scale;
   });
   __syncthreads();
   // phase 4
   if (use_tab)
-    adjoint_pixels<NL, NS, true>(sp, sc, tab, A, st.adj.redP);
+    adjoint_pixels<T, NL, NS, true>(sp, sc, tab, A, st.adj.redP);
   else
-    adjoint_pixels<NL, NS, false>(sp, sc, tab, A, st.adj.redP);
+    adjoint_pixels<T, NL, NS, false>(sp, sc, tab, A, st.adj.redP);
   __syncthreads();
   if (threadIdx.x < P) {
     double v = 0.0;
-    for (int w = 0; w < NWARPS; ++w) v += (double)st.adj.redP[w][threadIdx.x];
+    for (int w = 0; w < NW; ++w) v += (double)st.adj.redP[w][threadIdx.x];
     st.adj.gsum[threadIdx.x] = v;
   }
   __syncthreads();
@@ -566,23 +647,27 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
        float* __restrict__ logp, float* __restrict__ grad) {
   constexpr int P = 8 + 7 * (NL + NS);
   extern __shared__ __align__(16) float dsm[];
-  __shared__ SmemStatic st;
+  __shared__ SmemStatic<NWARPS> st;
   __shared__ float4 tab[SURR ? TABLE_ROW : 1];
   const int b = blockIdx.x;
   if (b >= B) return;
-  grad_row<NL, NS, SURR>(sp, theta + (size_t)b * P, logp + b, grad + (size_t)b * P,
-                         SURR ? sp.table + (size_t)b * TABLE_ROW : nullptr, b, dsm, st, tab);
+  grad_row<NL, NS, SURR, false, THREADS, 2>(sp, theta + (size_t)b * P, logp + b,
+                                            grad + (size_t)b * P,
+                                            SURR ? sp.table + (size_t)b * TABLE_ROW : nullptr, b,
+                                            dsm, st, tab);
 }
 
 // Persistent forward + adjoint over uneven multi-system batches: each CTA
 // takes items from a global counter, heaviest first (the host sorts them by
 // cost), and uses its own global-scratch slot. counter must be 0 at launch.
-template <int NL, int NS, bool SURR>
-__global__ void __launch_bounds__(THREADS, 2)
+// Launch shape: T threads per CTA (128 or 256; 512/T CTAs per SM at 128
+// registers a thread), NPR pixel pairs per thread in phase 1 (2 or 3).
+template <int NL, int NS, bool SURR, int T, int NPR>
+__global__ void __launch_bounds__(T, 512 / T)
 k_grad_multi(const SysParams* __restrict__ systems, const MultiItem* __restrict__ items,
              int n_items, int* __restrict__ counter) {
   extern __shared__ __align__(16) float dsm[];
-  __shared__ SmemStatic st;
+  __shared__ SmemStatic<T / 32> st;
   __shared__ float4 tab[SURR ? TABLE_ROW : 1];
   __shared__ int next;
   __shared__ SysParams sps;  // the item's parameter block
@@ -595,11 +680,12 @@ k_grad_multi(const SysParams* __restrict__ systems, const MultiItem* __restrict_
     {
       const int* src = reinterpret_cast<const int*>(systems + m.sys);
       int* dst = reinterpret_cast<int*>(&sps);
-      for (int k = threadIdx.x; k < (int)(sizeof(SysParams) / sizeof(int)); k += THREADS)
+      for (int k = threadIdx.x; k < (int)(sizeof(SysParams) / sizeof(int)); k += T)
         dst[k] = src[k];
     }
     __syncthreads();
-    grad_row<NL, NS, SURR, true>(sps, m.theta, m.logp, m.grad, m.table, blockIdx.x, dsm, st, tab);
+    grad_row<NL, NS, SURR, true, T, NPR>(sps, m.theta, m.logp, m.grad, m.table, blockIdx.x, dsm,
+                                         st, tab);
   }
 }
 

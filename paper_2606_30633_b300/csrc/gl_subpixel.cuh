@@ -99,6 +99,34 @@ __device__ __forceinline__ void clenshaw2(const float2* __restrict__ c, int n2, 
   s1 = Clen2{q1, q2};
 }
 
+// The same at six points (three pairs interleaved).
+__device__ __forceinline__ void clenshaw3(const float2* __restrict__ c, int n2, const Geo2* g,
+                                          Clen2* out) {
+  const float4* c4 = reinterpret_cast<const float4*>(c);
+  float2 tw[3], b1[3], b2[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    tw[m] = add2(g[m].wr, g[m].wr);
+    b1[m] = f2(0.f);
+    b2[m] = f2(0.f);
+  }
+  for (int k = n2 - 1; k >= 0; --k) {
+    const float4 a = c4[k];
+    const float2 ah = make_float2(a.z, a.w), al = make_float2(a.x, a.y);
+    float2 bh[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) bh[m] = clen_step(tw[m], b1[m], b2[m], ah);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const float2 bl = clen_step(tw[m], bh[m], b1[m], al);
+      b2[m] = bh[m];
+      b1[m] = bl;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m) out[m] = Clen2{b1[m], b2[m]};
+}
+
 // E and the t-derivative sum T together.
 __device__ __forceinline__ void clenshaw_ET(const float2* __restrict__ cE,
                                             const float2* __restrict__ cT, int n2, const Geo2& g,
@@ -290,6 +318,31 @@ __device__ __forceinline__ void surface_brightness4(const SampleC& sc, const flo
                           [&](float2 px, float2 py, float2 bx, float2 by) {
                             return light_sum2<NL, NS>(sc, px, py, bx, by);
                           });
+}
+
+// The same at six points (three pairs x[m], y[m]; the series sums interleaved).
+template <int NL, int NS, bool TAB>
+__device__ __forceinline__ void surface_brightness6(const SampleC& sc, const float4* tab,
+                                                    const float2* x, const float2* y, float2* sb) {
+  Geo2 g[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) g[m] = epl_geometry2(sc.epl, x[m], y[m]);
+  float2 Fr[3], Fi[3];
+  if (TAB) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) deflection_F<true>(sc, tab, g[m], Fr[m], Fi[m]);
+  } else {
+    Clen2 cs[3];
+    clenshaw3(sc.cE, sc.n2, g, cs);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) series_F(sc.epl, g[m], cs[m], Fr[m], Fi[m]);
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    float2 bx, by;
+    lens_equation2(sc, g[m], x[m], y[m], Fr[m], Fi[m], bx, by);
+    sb[m] = light_sum2<NL, NS>(sc, x[m], y[m], bx, by);
+  }
 }
 
 // One light component at four points (two pairs): a lens-light component on

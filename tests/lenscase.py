@@ -177,3 +177,25 @@ def grad_close_bound(got, ref, bound):
     g2, r2 = np.atleast_2d(got), np.atleast_2d(ref)
     return bool(np.all(err <= bound)), (float(r[b, k]), int(b), int(k), float(g2[b, k]),
                                        float(r2[b, k]))
+
+
+FP32_POS = 1.2e-7  # arcsec: half an FP32 ulp of a 2" coordinate (the Einstein radius)
+
+
+def position_floor(case: "Case", th: np.ndarray, delta=FP32_POS) -> np.ndarray:
+    """Per-row, per-parameter conditioning floor of the gradient at the FP32
+    precision of positions: the largest change of the oracle's FP64 gradient
+    when a single component centre (lens, lens light or source) moves by
+    delta in x or in y. An FP32 evaluation's lens-frame and source-plane
+    positions carry rounding of that size, so no FP32 evaluation can be held
+    below this floor on an entry whose floor exceeds the stated bound."""
+    th = np.atleast_2d(np.asarray(th, np.float64))
+    B, P = th.shape
+    xs, ys = centre_indices(case.W.n_lens_light + case.W.n_source)
+    idx = list(xs) + list(ys)
+    shifted = np.repeat(th, len(idx), axis=0).reshape(B, len(idx), P)
+    for m, k in enumerate(idx):
+        shifted[:, m, k] += delta
+    _, g0 = case.oracle.logp_grad(th)
+    _, g = case.oracle.logp_grad(shifted.reshape(-1, P))
+    return np.abs(g.reshape(B, len(idx), P) - g0[:, None, :]).max(1)

@@ -111,3 +111,41 @@ def test_divergent_chains_are_frozen_and_graph_recaptures(env):
     lp_chk, g_chk = s.logp_grad(th)
     torch.testing.assert_close(lp[[0, 1, 3, 4, 5]], lp_chk[[0, 1, 3, 4, 5]])
     torch.testing.assert_close(g[[0, 1, 3, 4, 5]], g_chk[[0, 1, 3, 4, 5]])
+
+
+def test_space_block_matches_fp64_integrator():
+    """One graph block of the space-telescope workload (200 x 200 px at
+    0.05"/px, s = 5, 21 x 21 Gaussian-core PSF, two source components: the
+    image buffers live in global scratch) against the FP64 integrator on the
+    oracle, for 4 chains started near the truth: 10 leapfrogs with the
+    benchmark's step scale. Positions agree to the same bound as the small
+    case's."""
+    import torch
+    c = make_case(synth.space_200())
+    s = c.gpu_system()
+    th, p, im = _start(torch, c, 4, seed=5, rel=0.002)
+    eps, L = 1e-4, 10
+    lp, g = s.logp_grad(th)
+    th64, p64, im64 = th.double().cpu().numpy(), p.double().cpu().numpy(), im.double().cpu().numpy()
+    h0 = lp.double().cpu().numpy() - 0.5 * np.sum(im64 * p64 ** 2, 1)
+    s.leapfrog(th, p, lp, g, im, eps, L)
+    torch.cuda.synchronize()
+    _, gr = c.oracle.logp_grad(th64)
+    t0 = th64.copy()
+    for _ in range(L):
+        p64 = p64 + 0.5 * eps * gr
+        th64 = th64 + eps * im64 * p64
+        lr, gr = c.oracle.logp_grad(th64)
+        p64 = p64 + 0.5 * eps * gr
+    h1 = lr - 0.5 * np.sum(im64 * p64 ** 2, 1)
+    moved = th64 - t0
+    got = th.double().cpu().numpy() - t0
+    err = np.abs(got - moved)
+    lpg = lp.double().cpu().numpy()
+    print(f"\nspace block: |dH| (FP64) {np.array2string(np.abs(h1 - h0), precision=3)}; position err / "
+          f"bound max {(err / (2e-3 * np.abs(moved) + 2e-6 * np.abs(t0) + 1e-7)).max():.3f}; "
+          f"log p rel err {np.abs(lpg - lr).max() / np.abs(lr).max():.2e}")
+    assert np.all(np.isfinite(lpg))
+    assert np.all(err <= 2e-3 * np.abs(moved) + 2e-6 * np.abs(t0) + 1e-7), float(err.max())
+    assert np.all(np.abs(lpg - lr) <= 1e-5 * np.abs(lr))
+    s.close()
