@@ -49,18 +49,22 @@ MUFU_PER_SM_CLK = 16
 # (4096 rows), from one ncu capture of this bench's own launch:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
 #       -k regex:k_grad -s 3 -c 1 python bench.py --steps 5 --warmup 3 --no-cpu-baseline
-# (700,160 read + 0 written; the outputs are still in L2 when the launch ends).
+#       --no-extra-workloads
+# (560,896 read + 0 written; the outputs are still in L2 when the launch ends).
 # Reported only while KGRAD_SOURCES still hash to the value recorded with the
 # capture (kgrad_source_hash()); a changed kernel reports traffic null.
-TRAFFIC_GROUND_4096 = 700160
+TRAFFIC_GROUND_4096 = 560896
 # DRAM bytes of one k_grad launch of the space-telescope workload per row,
 # from one capture of a 512-row launch inside the HMC leg
-# (24,968,704 read + 181,744,384 written); the traffic is the per-row scratch
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+#       -k regex:k_grad -s 5 -c 1 python bench.py --workload space200-leapfrog
+#       --batch 512 --steps 2 --warmup 3
+# (26,635,520 read + 179,077,632 written); the traffic is the per-row scratch
 # images, so it grows in proportion to the rows.
-TRAFFIC_SPACE_PER_ROW = (24968704 + 181744384) / 512
+TRAFFIC_SPACE_PER_ROW = (26635520 + 179077632) / 512
 # kgrad_source_hash() of the sources the two captures above were taken with
 # (None: no capture of the current kernel yet)
-TRAFFIC_SOURCE_HASH = None
+TRAFFIC_SOURCE_HASH = "aa14b46d1cb801a0"
 KGRAD_SOURCES = ["gl_internal.cuh", "gl_model.cuh", "gl_subpixel.cuh", "gl_kernels.cuh",
                  "gl_grad.cu", "gl_grad_impl.cuh", "gl_grad_l0_series.cu", "gl_grad_l1_series.cu",
                  "gl_grad_l2_series.cu"]
@@ -644,7 +648,8 @@ def run_leapfrog(args) -> dict | None:
 
 
 def uneven_leg(steps: int, warmup: int, world: int, local: int, sur=None,
-               batch: int | None = None) -> dict:
+               batch: int | None = None, shape: str | None = None,
+               policy: str | None = None) -> dict:
     """Uneven-batch persistent run: 100 synthetic systems (sides 40-200 px,
     s = 2-5, 1-3 source components, 0.262"/px, 11x11 Moffat), 256 rows each,
     all evaluated per step by gl_multi_logp_grad (persistent launches per
@@ -671,7 +676,15 @@ def uneven_leg(steps: int, warmup: int, world: int, local: int, sur=None,
         thetas.append(torch.tensor(W.samples().astype(np.float32), device=dev))
         rows.append(W.batch)
     n_rows = sum(rows)
-    plan, tune = autotune.tune_multi(systems, rows, thetas, reps=2)
+    if shape:
+        # a fixed launch shape for every system, no tuning (profiling runs)
+        t, p = (int(v) for v in shape.split("x"))
+        pol = policy or "two_ctas"
+        plan = gl.Multi(systems, rows, autotune.POLICIES[pol], threads=[t] * len(systems),
+                        pairs=[p] * len(systems))
+        tune = {"assignment": f"fixed {t}x{p}", "policy": pol, "batch_ms": {}, "classes": {}}
+    else:
+        plan, tune = autotune.tune_multi(systems, rows, thetas, reps=2)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     logps, grads = plan.logp_grad(thetas)
@@ -761,7 +774,8 @@ def run_uneven(args) -> dict | None:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     glbuild.build()
-    leg = uneven_leg(args.steps, args.warmup, world, local, batch=args.batch)
+    leg = uneven_leg(args.steps, args.warmup, world, local, batch=args.batch,
+                     shape=args.uneven_shape, policy=args.uneven_policy)
     out = None
     if rank == 0:
         out = {"metric": leg.pop("metric"), "value": leg.pop("value"), "unit": "evals/s",
@@ -1030,6 +1044,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-workloads", action="store_true",
                     help="ground100 only: skip the space-telescope and uneven-batch legs")
+    ap.add_argument("--uneven-shape", default=None,
+                    help="uneven workload: one launch shape THREADSxPAIRS for every system "
+                         "instead of the autotuner's (profiling runs)")
+    ap.add_argument("--uneven-policy", default=None, choices=["global", "two_ctas", "one_cta"],
+                    help="shared-memory policy with --uneven-shape (default two_ctas)")
     ap.add_argument("--extra-steps", type=int, default=3,
                     help="timed steps of the space-telescope leg (the uneven leg takes at "
                          "least 5) in the default run")
