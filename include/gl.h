@@ -189,10 +189,11 @@ gl_status gl_multi_create(gl_system* const* systems, int n_sys, const int* rows_
  * of 128 threads run four per SM, of 256 two, at 128 registers a thread) and
  * pixel_pairs[k] in {2, 3}, the pixel pairs each thread keeps in flight in
  * the forward binning (more independent work per thread for the latency of
- * the MUFU/FP32 chain). Either array may be NULL: 256 threads, 2 pairs (the
- * shape of gl_logp_grad, whose results the default shape reproduces bit for
- * bit; other shapes sum the chi^2 and gradient terms in another order, so
- * they agree to FP32 reassociation). Other values: GL_EINVAL. */
+ * the MUFU/FP32 chain). Either array may be NULL: 256 threads, 2 pairs. The
+ * pixel pairs do not change results (each pixel sums its sub-pixels in the
+ * same order); with 256 threads the results equal gl_logp_grad's bit for bit,
+ * with 128 the chi^2 and gradient terms are summed in another order and agree
+ * to FP32 reassociation. Other values: GL_EINVAL. */
 gl_status gl_multi_create_ex(gl_system* const* systems, int n_sys, const int* rows_per_sys,
                              int smem_policy, const int* threads_per_cta,
                              const int* pixel_pairs, gl_multi** out);

@@ -302,7 +302,9 @@ __device__ __forceinline__ void bin_loop6(const SysParams& sp, float* A, Eval6 e
   bin_tail<T>(sp, A, w0, p, eval2);
 }
 
-// Phase 1 with NPR pixel pairs per thread in flight (2 or 3).
+// Phase 1 with NPR pixel pairs per thread in flight (2 or 3). Every pixel sums
+// its sub-pixels in the same order whatever NPR is, so the binned image (and
+// everything after it) does not depend on NPR.
 template <int T, int NPR, int NL, int NS, bool TAB>
 __device__ __forceinline__ void bin_pixels(const SysParams& sp, const SampleC& sc,
                                            const float4* tab, float* A) {
@@ -472,9 +474,9 @@ k_forward(const __grid_constant__ SysParams sp, const float* __restrict__ theta,
     return;
   }
   if (SURR && sc.use_table)
-    bin_pixels<THREADS, 2, NL, NS, true>(sp, sc, tab, A);
+    bin_pixels<THREADS, 3, NL, NS, true>(sp, sc, tab, A);
   else
-    bin_pixels<THREADS, 2, NL, NS, false>(sp, sc, tab, A);
+    bin_pixels<THREADS, 3, NL, NS, false>(sp, sc, tab, A);
   __syncthreads();
   float csum = 0.f, ccomp = 0.f;
   float* out = want_img ? img + (size_t)b * npix : nullptr;
@@ -651,7 +653,7 @@ k_grad(const __grid_constant__ SysParams sp, const float* __restrict__ theta, in
   __shared__ float4 tab[SURR ? TABLE_ROW : 1];
   const int b = blockIdx.x;
   if (b >= B) return;
-  grad_row<NL, NS, SURR, false, THREADS, 2>(sp, theta + (size_t)b * P, logp + b,
+  grad_row<NL, NS, SURR, false, THREADS, 3>(sp, theta + (size_t)b * P, logp + b,
                                             grad + (size_t)b * P,
                                             SURR ? sp.table + (size_t)b * TABLE_ROW : nullptr, b,
                                             dsm, st, tab);

@@ -92,6 +92,23 @@ def test_autotuner_picks_the_fastest_it_timed(env):
         np.testing.assert_allclose(lp.cpu().numpy(), rl.cpu().numpy(), rtol=1e-6)
 
 
+@pytest.mark.parametrize("defl", ["series", "table"])
+def test_pixel_pairs_do_not_change_results(env, defl):
+    """Three pixel pairs per thread with 256 threads reproduce gl_logp_grad
+    bit for bit (each pixel sums its sub-pixels in the same order)."""
+    torch, gl, cases, systems, thetas = env
+    d = gl.GL_DEFL_SERIES if defl == "series" else gl.GL_DEFL_TABLE
+    n = len(systems)
+    plan = gl.Multi(systems, [t.shape[0] for t in thetas], gl.GL_MULTI_SMEM_TWO_CTAS,
+                    threads=[256] * n, pairs=[3] * n)
+    lps, gs = plan.logp_grad(thetas, defl=d)
+    torch.cuda.synchronize()
+    for s, t, lp, g in zip(systems, thetas, lps, gs):
+        rl, rg = s.logp_grad(t, defl=d)
+        np.testing.assert_array_equal(lp.cpu().numpy(), rl.cpu().numpy())
+        np.testing.assert_array_equal(g.cpu().numpy(), rg.cpu().numpy())
+
+
 @pytest.mark.parametrize("shape", [(256, 3), (128, 2), (128, 3)])
 @pytest.mark.parametrize("defl", ["series", "table"])
 def test_launch_shapes_agree(env, shape, defl):
