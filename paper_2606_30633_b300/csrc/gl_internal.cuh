@@ -30,7 +30,7 @@ constexpr int N_MAX = 128;     // EPL series terms for |e| < 0.8 at FP32 toleran
 constexpr float TABLE_MIN_E = 1e-2f;  // rows with a smaller |e| use the series, not tables
 constexpr int THREADS = 256;   // threads per CTA of the fused kernels
 constexpr int NWARPS = THREADS / 32;
-constexpr int ROWS_STRIP = 8;  // output rows per thread in the unrolled convolution
+constexpr int ROWS_STRIP = 10;  // output rows per thread in the unrolled convolution
 constexpr int TABLE_M = 128;   // surrogate angular table intervals over [0, pi)
 constexpr int TABLE_ROW = 4 * TABLE_M;  // float4 per row's table (4 per interval)
 
