@@ -79,7 +79,12 @@ typedef enum {
  *                      row, F and its derivatives on 128 angles from the
  *                      network, interpolated (cubic Hermite) at every
  *                      sub-pixel; rows outside its training domain use the
- *                      exact series;
+ *                      exact series. gl_logp_grad evaluates the network
+ *                      inside each row's CTA of the gradient kernel (tensor
+ *                      cores, the table in shared memory) where two such CTAs
+ *                      fit per SM, else, like the other entry points, in a
+ *                      table launch of its own; the results are the same bit
+ *                      for bit;
  *   GL_DEFL_TABLE      the same tables filled from the exact series summed in
  *                      FP64 (rows with |e| > 0.5 use the series): differs from
  *                      GL_DEFL_SERIES by the interpolation error only;

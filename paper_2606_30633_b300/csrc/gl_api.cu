@@ -3,6 +3,7 @@
 // arguments, copies inputs and normalises the PSF once at creation.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -388,11 +389,8 @@ gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, f
   if (B > 0 && !grad) return fail(GL_EINVAL, "grad is NULL");
   if (B == 0) return GL_OK;
   if ((r = set_device(sys)) != GL_OK) return r;
+  const cudaStream_t st = (cudaStream_t)stream;
   SysParams sp = sys->sp;
-  if (defl != GL_DEFL_SERIES) {
-    r = prepare_surrogate(sys, theta, B, sp, defl, (cudaStream_t)stream);
-    if (r != GL_OK) return r;
-  }
   sp.bufA_smem = sys->grad_A;
   sp.bufB_smem = sys->grad_B;
   sp.slot_floats = sys->grad_slot;
@@ -401,8 +399,29 @@ gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, f
     if (r != GL_OK) return r;
     sp.scratch = sys->scratch;
   }
-  GL_CUDA(gl::launch_grad(sp, theta, B, logp, grad, sys->grad_smem, (cudaStream_t)stream),
-          "gradient launch");
+  if (defl == GL_DEFL_SURROGATE && !sys->no_fused) {
+    // the surrogate evaluated inside each row's CTA (no table launch, no
+    // tables in global memory), where two CTAs of it still fit per SM
+    if ((r = gl::surrogate_take_timeout(sys->sur)) != GL_OK) return r;
+    SysParams spf = sp;
+    gl::surrogate_net(sys->sur, &spf);
+    spf.table = nullptr;
+    gl::table_domain(defl, sys->sur, &spf.sq_lo, &spf.sq_hi, &spf.sg_lo, &spf.sg_hi);
+    const size_t dyn = std::max(sys->grad_smem, gl::net_smem_bytes());
+    GL_CUDA(gl::surrogate_flag_begin(sys->sur, st), "timeout flag reset");
+    bool fits = false;
+    GL_CUDA(gl::launch_grad_fused(spf, theta, B, logp, grad, dyn, &fits, st), "fused launch");
+    if (fits) {
+      GL_CUDA(gl::surrogate_flag_end(sys->sur, st), "timeout flag copy");
+      return GL_OK;
+    }
+    sys->no_fused = true;
+  }
+  if (defl != GL_DEFL_SERIES) {
+    r = prepare_surrogate(sys, theta, B, sp, defl, st);
+    if (r != GL_OK) return r;
+  }
+  GL_CUDA(gl::launch_grad(sp, theta, B, logp, grad, sys->grad_smem, st), "gradient launch");
   return GL_OK;
 }
 

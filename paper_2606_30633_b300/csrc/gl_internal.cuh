@@ -61,6 +61,13 @@ struct SysParams {
   float* scratch;          // global scratch base (CTA b uses slot b)
   const float4* table;     // surrogate tables [B][TABLE_ROW] (null: exact series)
   float sq_lo, sq_hi, sg_lo, sg_hi;  // surrogate domain in q and gamma
+  // the network, for the fused kernel that builds each row's table itself
+  // (null: tables come from `table` or the row uses the series)
+  const unsigned char* net_wimg;  // packed weight operands of layers 1-4
+  const void* net_wb;             // BF16 operands (__nv_bfloat16)
+  const float* net_params;        // FP32 parameters (biases)
+  int* net_timeout;               // set when a bounded tensor-core wait ran out
+  int net_forced;                 // test hook: act as if the first wait ran out
   float kconv[MAX_K * MAX_K];  // flipped PSF: m = correlate(b_pad, kconv)
   float kcorr[MAX_K * MAX_K];  // PSF: adjoint = correlate(g_pad, kcorr)
 };
@@ -87,6 +94,11 @@ cudaError_t launch_grad(const SysParams& sp, const float* theta, int B, float* l
 cudaError_t launch_leapfrog_block(const SysParams& sp, size_t dyn, float* theta, float* p,
                                   float* logp, float* grad, const float* inv_mass, float eps,
                                   int n_steps, int B, cudaStream_t st);
+// Forward + adjoint with the surrogate's tables built by the network inside
+// each row's CTA (sp.net_* set); false in *fits when two CTAs of it do not fit
+// per SM with dyn_smem bytes, in which case nothing is launched.
+cudaError_t launch_grad_fused(const SysParams& sp, const float* theta, int B, float* logp,
+                              float* grad, size_t dyn_smem, bool* fits, cudaStream_t st);
 // Persistent forward + adjoint over multi-system work items (MultiItem array),
 // launch shape (threads per CTA 128 or 256, phase-1 pixel pairs 2 or 3).
 cudaError_t launch_grad_multi(int nL, int nS, bool surr, int threads, int pairs,
@@ -101,6 +113,14 @@ cudaError_t launch_table(int defl, const gl_surrogate* s, const float* theta, in
 // training domain for GL_DEFL_SURROGATE, |e| <= 0.5 for the exact tables.
 void table_domain(int defl, const gl_surrogate* s, float* q_lo, float* q_hi, float* g_lo,
                   float* g_hi);
+// The surrogate's device operands for the fused kernel (sp->net_*), the
+// dynamic shared memory its network needs, and its timeout flag's reset
+// before and stream-ordered copy to the host after a launch that may set it
+// (gl_surrogate.cu).
+void surrogate_net(const gl_surrogate* s, SysParams* sp);
+size_t net_smem_bytes();
+cudaError_t surrogate_flag_begin(const gl_surrogate* s, cudaStream_t st);
+cudaError_t surrogate_flag_end(const gl_surrogate* s, cudaStream_t st);
 // A valid deflection kind (gl_deflection).
 inline bool defl_valid(int defl) { return defl >= 0 && defl <= 3; }
 

@@ -547,9 +547,12 @@ k_component_images(const __grid_constant__ SysParams sp, const float* __restrict
 // Forward + adjoint of one row (all T threads of the CTA): log p and
 // d log p / d theta of theta row th into *logp_out and grad_out[0..P).
 // slot_index picks the CTA's global-scratch slot, table_row the row's table;
-// NPR pixel pairs per thread in flight in phase 1 (2 or 3).
+// NPR pixel pairs per thread in flight in phase 1 (2 or 3). STAGED: the
+// caller has staged the row into st, zeroed the adjoint sums and, for a row
+// that uses a table, written it into tab (the fused kernel); the image
+// buffers' halos are then zeroed here.
 // Ends with a block barrier, so a persistent CTA can start its next row.
-template <int NL, int NS, bool SURR, bool MULTI, int T, int NPR>
+template <int NL, int NS, bool SURR, bool MULTI, int T, int NPR, bool STAGED = false>
 __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __restrict__ th,
                                          float* __restrict__ logp_out,
                                          float* __restrict__ grad_out,
@@ -560,13 +563,18 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
   SampleC& sc = st.sc;
   float *A, *Bf;
   buffers(sp, dsm, true, A, Bf, slot_index);
-  if (threadIdx.x < 32) {
-    stage_warp(sp, th, sc, st.fin, true);
+  if constexpr (STAGED) {
+    zero_halo<T>(sp, A, 0);
+    zero_halo<T>(sp, Bf, 0);
   } else {
-    zero_halo<T>(sp, A, 32);
-    zero_halo<T>(sp, Bf, 32);
+    if (threadIdx.x < 32) {
+      stage_warp(sp, th, sc, st.fin, true);
+    } else {
+      zero_halo<T>(sp, A, 32);
+      zero_halo<T>(sp, Bf, 32);
+    }
+    for (int k = threadIdx.x; k < NW * MAX_P; k += T) (&st.adj.redP[0][0])[k] = 0.f;
   }
-  for (int k = threadIdx.x; k < NW * MAX_P; k += T) (&st.adj.redP[0][0])[k] = 0.f;
   __syncthreads();
   if (sc.status != 0) {
     const float lv = sc.status == 2 ? __int_as_float(0x7fc00000) : -__int_as_float(0x7f800000);
@@ -576,7 +584,7 @@ __device__ __forceinline__ void grad_row(const SysParams& sp, const float* __res
     __syncthreads();
     return;
   }
-  load_table<T, SURR>(table_row, sc, tab);
+  if constexpr (!STAGED) load_table<T, SURR>(table_row, sc, tab);
   if (table_failed<SURR>(sc, tab)) {
     if (threadIdx.x == 0) *logp_out = __int_as_float(0x7fc00000);
     if (threadIdx.x < P) grad_out[threadIdx.x] = __int_as_float(0x7fc00000);

@@ -249,7 +249,8 @@ __device__ inline void stage_warp(const SysParams& sp, const float* __restrict__
       sc.ng2 = f2(-th[7]);
       // the table path's rotation term divides d log p / d phi by 2 |e|^2, so
       // nearly round lenses (|e| < TABLE_MIN_E) take the series
-      sc.use_table = sp.table != nullptr && q >= sp.sq_lo && q <= sp.sq_hi &&
+      sc.use_table = (sp.table != nullptr || sp.net_wimg != nullptr) && q >= sp.sq_lo &&
+                     q <= sp.sq_hi &&
                      th[1] >= sp.sg_lo && th[1] <= sp.sg_hi && c >= TABLE_MIN_E;
     } else {
       LightP& L = sc.light[lane - 1];

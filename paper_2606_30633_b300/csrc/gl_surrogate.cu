@@ -14,6 +14,7 @@
 #include "../../include/gl.h"
 #include "gl_internal.cuh"
 #include "gl_mlp.cuh"
+#include "gl_tc.cuh"
 
 namespace gl {
 void set_last_error(const std::string& msg);
@@ -274,43 +275,6 @@ __global__ void k_infer(const __nv_bfloat16* __restrict__ wb, const float* __res
 
 namespace gl {
 
-// Node j of a table: pseudo-angle pa_j = 2j/TABLE_M and its angle vphi_j in
-// [0, pi) (inverse of pa = 1 - cos/(|cos| + sin)), with d vphi/d pa = (|cos| + sin)^2.
-__device__ __forceinline__ void table_node(int j, float& vphi, float& dvdpa) {
-  const float pa = 2.f * j / TABLE_M;
-  vphi = pa <= 1.f ? atan2f(pa, 1.f - pa) : PI_F - atan2f(2.f - pa, pa - 1.f);
-  float s, c;
-  sincosf(vphi, &s, &c);
-  const float d = fabsf(c) + s;
-  dvdpa = d * d;
-}
-
-// Writes a row's interval table from its node values (node j: (F, dF/dpa)
-// and (dF/dq, dF/dt), complex, in shared memory). Interval j covers pa in
-// [pa_j, pa_j + h), h = 2/TABLE_M, with local t = (pa - pa_j)/h, and holds
-//   (a, b), (c, d):  F(t) = a + b t + c t^2 + d t^3, the cubic Hermite
-//                    through nodes j and j+1 (the nodes are periodic);
-//   G0, G1 - G0:     (dF/dq, dF/dt) at node j and its change to node j+1,
-// stored as four arrays of TABLE_M float4 (lanes reading different intervals
-// then hit different shared-memory banks).
-__device__ void write_intervals(const float4 (*node)[2], float4* __restrict__ out) {
-  const float h = 2.f / TABLE_M;
-  for (int j = threadIdx.x; j < TABLE_M; j += blockDim.x) {
-    const int k = (j + 1) & (TABLE_M - 1);
-    const float4 n0 = node[j][0], n1 = node[k][0];
-    const float ar = n0.x, ai = n0.y, br = h * n0.z, bi = h * n0.w;
-    const float er = h * n1.z, ei = h * n1.w;  // h dF/dpa at node j+1
-    const float dr = n1.x - n0.x, di = n1.y - n0.y;
-    const float cr = 3.f * dr - 2.f * br - er, ci = 3.f * di - 2.f * bi - ei;
-    const float d3r = br + er - 2.f * dr, d3i = bi + ei - 2.f * di;
-    const float4 m0 = node[j][1], m1 = node[k][1];
-    out[j] = make_float4(ar, ai, br, bi);
-    out[TABLE_M + j] = make_float4(cr, ci, d3r, d3i);
-    out[2 * TABLE_M + j] = m0;
-    out[3 * TABLE_M + j] = make_float4(m1.x - m0.x, m1.y - m0.y, m1.z - m0.z, m1.w - m0.w);
-  }
-}
-
 // The same tables from the exact series: F, dF/dvphi = F'(z) 2iz,
 // dF/dq = -F'(z) e^{2i vphi} df/dq, dF/dt = sum c_n h_n z^n, with
 // F'(z) = [t F - (2-t) E]/(2(1-z)) and F = 1 + zE, summed per node in Real
@@ -378,77 +342,18 @@ __global__ void k_table_exact(const float* __restrict__ theta, int P, int B, flo
 // Per-sample tables for the lens kernels from the network: for row b with EPL
 // axis ratio q and slope gamma, node j takes (F, dF/dpa, dF/dq, dF/dt) as 4
 // complex numbers, from the network at R = theta_E with forward-mode
-// derivatives, and the row's intervals follow from the nodes; rows outside
-// the training domain are skipped (the lens kernels use the exact series
-// there). The network runs on the 5th-generation tensor
-// cores: per row, the 128 nodes are the M = 128 rows of every layer's MMA
-// (tcgen05.mma kind::f16, BF16 operands in shared memory, FP32 accumulators
-// in tensor memory), for the primal pass and the three forward-mode tangents
-// (d/dvphi, d/dq, d/dgamma) as four accumulators of 64 columns. One thread
-// per node reads its accumulator row back (tcgen05.ld), applies bias and SiLU
-// (and SiLU' to the tangents) and writes the next layer's BF16 operand.
-// Persistent CTAs of 4 warps keep the weights in shared memory across rows.
-//
-// Operands use the canonical K-major layout without swizzle: 8 x 16-byte core
-// matrices, K-adjacent ones 128 B apart (LBO), row-group-adjacent ones
-// K/8 x 128 B apart (SBO).
+// derivatives (net_row, gl_tc.cuh), and the row's intervals follow from the
+// nodes; rows outside the training domain are skipped (the lens kernels use
+// the exact series there). Persistent CTAs of 4 warps keep the weights in
+// shared memory across rows.
 namespace tc {
-
-constexpr int NT = 128;                 // threads = nodes = MMA rows
-constexpr uint32_t TMEM_COLS = 256;     // 4 streams x 64 columns
-constexpr int A0_BYTES = 128 * 16 * 2;  // layer-1 operand [128][16]
-constexpr int A_BYTES = 128 * 64 * 2;   // hidden operands [128][64]
-constexpr int W1_BYTES = 64 * 16 * 2;
-constexpr int WH_BYTES = 64 * 64 * 2;
-constexpr int W5_BYTES = 16 * 64 * 2;   // output layer padded to N = 16
-constexpr int TB_W1 = 0;  // shared-memory byte offsets of the table kernel
-constexpr int TB_WH = TB_W1 + W1_BYTES;
-constexpr int TB_W5 = TB_WH + 3 * WH_BYTES;
-constexpr int TB_A0 = TB_W5 + W5_BYTES;
-constexpr int TB_A = TB_A0 + A0_BYTES;
-constexpr int TB_NODE = TB_A + 4 * A_BYTES;
-constexpr int SMEM_BYTES = TB_NODE + TABLE_M * 2 * 16;
-constexpr long long WAIT_LIMIT = 1ll << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Byte offset of element (r, k) of an [R][K] BF16 operand.
-__device__ __forceinline__ uint32_t core_off(int r, int k, int K) {
-  return (uint32_t)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-// Shared-memory matrix descriptor (no swizzle, base offset 0, version 1).
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-
-// Instruction descriptor, kind::f16: FP32 D, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id,
-                                    uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-      "l"(a), "l"(b), "r"(id), "r"(acc));
-}
-
-__device__ __forceinline__ void commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-      smem_u32(bar)));
-}
 
 // Set through gl_debug_force_wait_timeout: the tensor-core kernels then treat
 // their first completion wait as run out (without waiting), so that the
 // timeout path (drain, flag, NaN outputs, TMEM release) runs with no real wait
 // running out.
 __device__ int g_force_wait_timeout = 0;
+bool g_force_wait_timeout_host = false;  // the same setting for launches that take it as an argument
 
 __global__ void k_set_force_wait_timeout(int v) { g_force_wait_timeout = v; }
 
@@ -456,72 +361,7 @@ __device__ __forceinline__ bool forced_timeout() {
   return *reinterpret_cast<volatile int*>(&g_force_wait_timeout) != 0;
 }
 
-// Bounded wait for the barrier's phase; false on timeout.
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t phase) {
-  uint32_t done = 0;
-  for (long long it = 0; it < WAIT_LIMIT && !done; ++it) {
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(phase));
-  }
-  return done != 0;
-}
-
-__device__ __forceinline__ void ld16(uint32_t addr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(addr));
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ void ld2(uint32_t addr, float (&v)[2]) {
-  uint32_t r0, r1;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
-               : "=r"(r0), "=r"(r1)
-               : "r"(addr));
-  v[0] = __uint_as_float(r0);
-  v[1] = __uint_as_float(r1);
-}
-
-__device__ __forceinline__ void wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// Operand writes by the threads are made visible to the tensor cores, and the
-// accumulator reads finished, before thread 0 issues the next MMAs.
-__device__ __forceinline__ void to_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Copies an [N][K] BF16 row-major matrix (rows >= n_src zero) into the operand layout.
-__device__ void load_operand(unsigned char* dst, const __nv_bfloat16* __restrict__ src, int N,
-                             int K, int n_src) {
-  for (int i = threadIdx.x; i < N * K; i += NT) {
-    const int n = i / K, k = i - n * K;
-    *reinterpret_cast<__nv_bfloat16*>(dst + core_off(n, k, K)) =
-        n < n_src ? src[n * K + k] : __float2bfloat16(0.f);
-  }
-}
-
-// 8 consecutive BF16 values of row r at column k0 (a multiple of 8), one store.
-__device__ __forceinline__ void put8(unsigned char* base, int r, int k0, int K, const float* v) {
-  uint4 u;
-  u.x = pack_bf16(v[0], v[1]);
-  u.y = pack_bf16(v[2], v[3]);
-  u.z = pack_bf16(v[4], v[5]);
-  u.w = pack_bf16(v[6], v[7]);
-  *reinterpret_cast<uint4*>(base + core_off(r, k0, K)) = u;
-}
+constexpr int NT = 128;  // threads = nodes = MMA rows
 
 }  // namespace tc
 
@@ -538,13 +378,7 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
   // P1..P4 are the first bytes of the packed training image (same layout)
   static_assert(TB_W1 == 0 && TB_WH == 64 * 16 * 2 && TB_W5 == 64 * 16 * 2 + 3 * 64 * 64 * 2,
                 "the table kernel's P1..P4 must match the packed image");
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(wimg);
-    uint4* dst = reinterpret_cast<uint4*>(sm + TB_W1);
-#pragma unroll 4
-    for (int k = t; k < TB_W5 / 16; k += NT) dst[k] = src[k];
-  }
-  load_operand(sm + TB_W5, wb + BOFF_P5, 16, 64, 8);
+  load_weights<NT>(sm, wimg, wb);
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -557,115 +391,18 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
   }
   to_async();
   const uint32_t tb = tmem_base;
-  const uint32_t lane_addr = tb + ((uint32_t)(32 * w) << 16);
-  unsigned char* A0 = sm + TB_A0;
-  unsigned char* A = sm + TB_A;
   float4(*node)[2] = reinterpret_cast<float4(*)[2]>(sm + TB_NODE);
-  const uint32_t a0 = smem_u32(A0), aa = smem_u32(A), w1 = smem_u32(sm + TB_W1);
-  const uint32_t wh = smem_u32(sm + TB_WH), w5 = smem_u32(sm + TB_W5);
   uint32_t phase = 0;
   bool ok = true;
   const bool forced = forced_timeout();
-  // tangent seeds of the normalised inputs, rounded to BF16 like every operand
-  const float seed[3] = {__bfloat162float(__float2bfloat16(1.f / PI_F)), 4.f,
-                         __bfloat162float(__float2bfloat16(1.f / 0.3f))};
-  const int seed_in[3] = {3, 0, 1};
   for (int b = blockIdx.x; b < B && ok; b += gridDim.x) {
     const float* th = theta + (size_t)b * P;
     const float e1 = th[2], e2 = th[3];
     const float cc = sqrtf(e1 * e1 + e2 * e2);
     const float q = (1.f - cc) / (1.f + cc), gamma = th[1];
     if (!(q >= q_lo && q <= q_hi && gamma >= g_lo && gamma <= g_hi)) continue;
-    float vp, dv, x[4];
-    table_node(t, vp, dv);
-    features(q, gamma, 0.f, vp, x);
-    {
-      const float v[8] = {x[0], x[1], x[2], x[3], 0.f, 0.f, 0.f, 0.f};
-      const float zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      put8(A0, t, 0, 16, v);
-      put8(A0, t, 8, 16, zero);
-    }
-    to_async();
-    // layer 1 (primal only: the tangents' first pre-activations are W1 seed)
-    if (t == 0) {
-      mma(tb, sdesc(a0, 256), sdesc(w1, 256), idesc(128, 64), 0u);
-      commit(&bar);
-    }
-    for (int layer = 1; layer <= 5 && ok; ++layer) {
-      // the decision is the block's (a thread leaving alone would desert a barrier)
-      if (!__syncthreads_and(!forced && wait_phase(&bar, phase))) {
-        ok = false;  // the commit of phase `phase` is still outstanding
-        break;
-      }
-      phase ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (layer == 5) break;
-      // epilogue of layer `layer`: bias, SiLU, SiLU' on the tangents, BF16 operands
-      const float* bias = params + (layer == 1 ? OFF_B1 : layer == 2 ? OFF_B2
-                                                        : layer == 3 ? OFF_B3 : OFF_B4);
-#pragma unroll 1
-      for (int c0 = 0; c0 < 64; c0 += 16) {
-        float z[16], d1[16], d2[16], d3[16];
-        ld16(lane_addr + c0, z);
-        if (layer > 1) {
-          ld16(lane_addr + 64 + c0, d1);
-          ld16(lane_addr + 128 + c0, d2);
-          ld16(lane_addr + 192 + c0, d3);
-        }
-        wait_ld();
-        if (layer == 1) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const __nv_bfloat16* wrow = wb + BOFF_P1 + (c0 + j) * 16;
-            d1[j] = __bfloat162float(wrow[seed_in[0]]) * seed[0];
-            d2[j] = __bfloat162float(wrow[seed_in[1]]) * seed[1];
-            d3[j] = __bfloat162float(wrow[seed_in[2]]) * seed[2];
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float zz = z[j] + bias[c0 + j];
-          const float sg = sigm(zz);
-          const float dsl = sg * (1.f + zz * (1.f - sg));
-          z[j] = zz * sg;
-          d1[j] *= dsl;
-          d2[j] *= dsl;
-          d3[j] *= dsl;
-        }
-        put8(A, t, c0, 64, z);
-        put8(A, t, c0 + 8, 64, z + 8);
-        put8(A + A_BYTES, t, c0, 64, d1);
-        put8(A + A_BYTES, t, c0 + 8, 64, d1 + 8);
-        put8(A + 2 * A_BYTES, t, c0, 64, d2);
-        put8(A + 2 * A_BYTES, t, c0 + 8, 64, d2 + 8);
-        put8(A + 3 * A_BYTES, t, c0, 64, d3);
-        put8(A + 3 * A_BYTES, t, c0 + 8, 64, d3 + 8);
-      }
-      to_async();
-      if (t == 0) {
-        const bool out = layer == 4;
-        const uint32_t wl = out ? w5 : wh + (uint32_t)(layer - 1) * WH_BYTES;
-        const uint32_t id = out ? idesc(128, 16) : idesc(128, 64);
-        for (int s = 0; s < 4; ++s)
-          for (int kk = 0; kk < 4; ++kk)
-            mma(tb + 64u * s, sdesc(aa + s * A_BYTES + kk * 256, 1024), sdesc(wl + kk * 256, 1024),
-                id, kk > 0 ? 1u : 0u);
-        commit(&bar);
-      }
-    }
+    ok = net_row<NT>(wb, params, q, gamma, sm, node, tb, &bar, phase, forced);
     if (!ok) break;
-    // output layer: y (primal) and the three tangents' dy, two columns each
-    float y[2], dy[3][2];
-    ld2(lane_addr, y);
-    ld2(lane_addr + 64, dy[0]);
-    ld2(lane_addr + 128, dy[1]);
-    ld2(lane_addr + 192, dy[2]);
-    wait_ld();
-    y[0] += params[OFF_B5];
-    y[1] += params[OFF_B5 + 1];
-    const Base bt = compose(base_terms(q, gamma - 1.f, vp), q, vp, y, dy);
-    node[t][0] = make_float4(bt.Fr, bt.Fi, dv * bt.Pr, dv * bt.Pi);
-    node[t][1] = make_float4(bt.Qr, bt.Qi, bt.Tr, bt.Ti);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     write_intervals(node, table + (size_t)b * TABLE_ROW);
@@ -1026,6 +763,24 @@ cudaError_t launch_table(int defl, const gl_surrogate* s, const float* theta, in
   return cudaGetLastError();
 }
 
+void surrogate_net(const gl_surrogate* s, SysParams* sp) {
+  sp->net_wimg = s->wimg;
+  sp->net_wb = s->wb;
+  sp->net_params = s->params;
+  sp->net_timeout = s->d_timeout;
+  sp->net_forced = tc::g_force_wait_timeout_host ? 1 : 0;
+}
+
+size_t net_smem_bytes() { return (size_t)tc::NET_SMEM_BYTES; }
+
+cudaError_t surrogate_flag_begin(const gl_surrogate* s, cudaStream_t st) {
+  return cudaMemsetAsync(s->d_timeout, 0, sizeof(int), st);
+}
+
+cudaError_t surrogate_flag_end(const gl_surrogate* s, cudaStream_t st) {
+  return cudaMemcpyAsync(s->h_timeout, s->d_timeout, sizeof(int), cudaMemcpyDeviceToHost, st);
+}
+
 gl_status surrogate_take_timeout(const gl_surrogate* s) {
   if (!s || *reinterpret_cast<volatile int*>(s->h_timeout) == 0) return GL_OK;
   *reinterpret_cast<volatile int*>(s->h_timeout) = 0;
@@ -1284,6 +1039,7 @@ gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** ou
 }
 
 gl_status gl_debug_force_wait_timeout(int on) {
+  gl::tc::g_force_wait_timeout_host = on != 0;
   gl::tc::k_set_force_wait_timeout<<<1, 1>>>(on ? 1 : 0);
   SUR_CUDA(cudaGetLastError(), "flag setter launch");
   SUR_CUDA(cudaDeviceSynchronize(), "flag setter");

@@ -29,6 +29,7 @@ struct gl_system {
   float *h_stage = nullptr, *d_stage = nullptr;
   size_t stage_floats = 0;
   const gl_surrogate* sur = nullptr;
+  bool no_fused = false;  // the fused surrogate kernel does not fit two CTAs per SM here
   float4* d_table = nullptr;  // surrogate tables, [rows][TABLE_ROW]
   size_t table_rows = 0;
   // leapfrog block: one instantiated CUDA graph, re-captured when its

@@ -274,3 +274,31 @@ def test_what_the_network_gains(gl, trained):
     assert d["surrogate"][0] <= 0.1
     assert r_tab >= 0.97 * r_sur
     assert d["fp32 tables"][0] <= d["surrogate"][0]
+
+
+def test_fused_kernel_matches_the_separate_table_build(gl, trained, lens):
+    """gl_logp_grad with the surrogate builds each row's table inside the
+    gradient kernel's CTA (no table launch); the multi-system plan still
+    builds them in a launch of their own and reads them back. Both run the
+    same network arithmetic, so log p and gradients agree bit for bit, on rows
+    that use the tables, rows outside the training domain (the series) and
+    out-of-support rows."""
+    torch, g = gl
+    c = lens
+    s = c.gpu_system()
+    s.set_surrogate(trained)
+    th = np.concatenate([synth.jitter(c.truth, c.W.prior(), 8, 5, rel=0.01), c.theta(40, seed=9)])
+    th = th.astype(np.float32)
+    th[-3:-1, 2], th[-3:-1, 3] = 0.4, 0.0  # q = 0.43: outside the training domain (series)
+    th[-1, 0] = -1.0  # outside the support
+    tt = torch.tensor(th, device="cuda")
+    lpf, gf = s.logp_grad(tt, defl=g.GL_DEFL_SURROGATE)
+    plan = g.Multi([s], [len(th)])
+    (lpm,), (gm,) = plan.logp_grad([tt], defl=g.GL_DEFL_SURROGATE)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(lpf.cpu().numpy(), lpm.cpu().numpy())
+    np.testing.assert_array_equal(gf.cpu().numpy(), gm.cpu().numpy())
+    e = np.hypot(th[:, 2], th[:, 3])
+    q = (1 - e) / (1 + e)
+    assert (q >= 0.5).sum() > 8 and (q < 0.5).sum() > 0  # both kinds of rows were exercised
+    plan.close()

@@ -3,8 +3,10 @@ library's test hook (gl_debug_force_wait_timeout): the kernels act as if their
 first completion wait had run out, without waiting, so no wait really runs
 out and every issued MMA is still drained before the tensor memory is freed.
 
-Checked: the table build gives NaN log p and gradient on the rows it served,
-the next GL_DEFL_SURROGATE call on that surrogate returns GL_ETIMEOUT, the
+Checked: the table build (inside the fused gradient kernel, and the
+stand-alone one of the forward entry point) gives NaN log p and gradient on
+the rows it served, the next GL_DEFL_SURROGATE call on that surrogate returns
+GL_ETIMEOUT, the
 synchronous training entry points return GL_ETIMEOUT at once, and with the
 hook off the same calls succeed again with the results they had before (the
 context stays usable)."""
@@ -48,6 +50,13 @@ def test_table_build_timeout_is_reported(env):
         assert np.isnan(lp1.cpu().numpy()).all() and np.isnan(g1.cpu().numpy()).all()
         with pytest.raises(gl.GLError) as err:
             s.logp_grad(t, defl=gl.GL_DEFL_SURROGATE)
+        assert err.value.status == gl.GL_ETIMEOUT
+        # the stand-alone table build (the forward entry point uses it) as well
+        lpf = s.logp(t, defl=gl.GL_DEFL_SURROGATE)
+        torch.cuda.synchronize()
+        assert np.isnan(lpf.cpu().numpy()).all()
+        with pytest.raises(gl.GLError) as err:
+            s.logp(t, defl=gl.GL_DEFL_SURROGATE)
         assert err.value.status == gl.GL_ETIMEOUT
         # the exact series does not use the tensor cores and is unaffected
         lps, _ = s.logp_grad(t, defl=gl.GL_DEFL_SERIES)
