@@ -313,8 +313,9 @@ def learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world) -
     train_s = time.perf_counter() - t0
     S.set_surrogate(sur)
     out = {}
-    for name, defl in (("surrogate", gl.GL_DEFL_SURROGATE), ("exact_tables", gl.GL_DEFL_TABLE),
-                       ("exact_tables_fp32", gl.GL_DEFL_TABLE32)):
+    for name, defl in (("surrogate", gl.GL_DEFL_SURROGATE),
+                       ("surrogate_fused", gl.GL_DEFL_SURROGATE_FUSED),
+                       ("exact_tables", gl.GL_DEFL_TABLE), ("exact_tables_fp32", gl.GL_DEFL_TABLE32)):
         ms = timed_steps(lambda: S.logp_grad(theta, defl=defl, out=logp, grad=grad, stream=stream),
                          args.steps, args.warmup, stream, flush)
         out[name] = world * W.batch / (statistics.mean(ms) / 1e3)
@@ -351,6 +352,7 @@ def learned_leg(args, S, W, theta, theta_np, logp, grad, stream, flush, world) -
                                       "tuples": n},
             "rows_in_surrogate_domain": in_dom,
             "train_seconds": train_s, "train_final_loss": sur.final_loss,
+            "surrogate_in_ray_shoot_cta_evals_per_s": out["surrogate_fused"],
             "exact_series_tables_evals_per_s": out["exact_tables"],
             "exact_series_tables_fp32": {
                 "value": out["exact_tables_fp32"], "unit": "evals/s",

@@ -79,23 +79,28 @@ typedef enum {
  *                      row, F and its derivatives on 128 angles from the
  *                      network, interpolated (cubic Hermite) at every
  *                      sub-pixel; rows outside its training domain use the
- *                      exact series. gl_logp_grad evaluates the network
- *                      inside each row's CTA of the gradient kernel (tensor
- *                      cores, the table in shared memory) where two such CTAs
- *                      fit per SM, else, like the other entry points, in a
- *                      table launch of its own; the results are the same bit
- *                      for bit;
+ *                      exact series; the tables are built by a launch of their
+ *                      own;
  *   GL_DEFL_TABLE      the same tables filled from the exact series summed in
  *                      FP64 (rows with |e| > 0.5 use the series): differs from
  *                      GL_DEFL_SERIES by the interpolation error only;
  *   GL_DEFL_TABLE32    the same, with the series at the table's nodes summed in
  *                      FP32 (the build takes a fraction of the FP64 one's time on
- *                      a GPU whose FP64 rate is 1/64 of its FP32 rate). */
+ *                      a GPU whose FP64 rate is 1/64 of its FP32 rate);
+ *   GL_DEFL_SURROGATE_FUSED  the surrogate of GL_DEFL_SURROGATE with its results
+ *                      bit for bit, but gl_logp_grad evaluates the network
+ *                      inside each row's CTA of the gradient kernel (tensor
+ *                      cores; the table never leaves shared memory) where two
+ *                      such CTAs fit per SM; the other entry points, and
+ *                      gl_logp_grad where they do not fit, build the tables in
+ *                      a launch of their own. On the B300 the separate launch
+ *                      is the faster of the two at the benchmark's sizes. */
 typedef enum {
   GL_DEFL_SERIES = 0,
   GL_DEFL_SURROGATE = 1,
   GL_DEFL_TABLE = 2,
-  GL_DEFL_TABLE32 = 3
+  GL_DEFL_TABLE32 = 3,
+  GL_DEFL_SURROGATE_FUSED = 4
 } gl_deflection;
 
 /* Prior kinds (Eq. sim-dist, Sec. 4.2). */

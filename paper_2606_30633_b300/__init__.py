@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(HERE, "libgl.so")
 
 GL_OK, GL_EINVAL, GL_ENOMEM, GL_ECUDA, GL_ENOSURROGATE, GL_ETIMEOUT = range(6)
 GL_DEFL_SERIES, GL_DEFL_SURROGATE, GL_DEFL_TABLE, GL_DEFL_TABLE32 = 0, 1, 2, 3
+GL_DEFL_SURROGATE_FUSED = 4
 PRIOR_KIND = {"flat": 0, "uniform": 1, "normal": 2, "truncnorm": 3, "lognormal": 4}
 
 _STATUS_NAMES = {0: "GL_OK", 1: "GL_EINVAL", 2: "GL_ENOMEM", 3: "GL_ECUDA",

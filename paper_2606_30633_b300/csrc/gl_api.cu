@@ -111,7 +111,7 @@ gl_status ensure_scratch(gl_system* s, size_t floats) {
 // Builds the surrogate tables for B rows and points sp at them.
 gl_status prepare_surrogate(gl_system* s, const float* theta, int B, SysParams& sp,
                             gl_deflection defl, cudaStream_t st) {
-  if (defl == GL_DEFL_SURROGATE) {
+  if (gl::defl_network(defl)) {
     gl_status r = gl::surrogate_take_timeout(s->sur);
     if (r != GL_OK) return r;
   }
@@ -135,7 +135,7 @@ gl_status check_call(gl_system* sys, const void* theta, int B, const void* out,
   if (B < 0) return fail(GL_EINVAL, "B < 0");
   if (B > 0 && (!theta || !out)) return fail(GL_EINVAL, "NULL theta or output");
   if (!gl::defl_valid(defl)) return fail(GL_EINVAL, "unknown deflection kind");
-  if (defl == GL_DEFL_SURROGATE && !sys->sur)
+  if (gl::defl_network(defl) && !sys->sur)
     return fail(GL_ENOSURROGATE, "no surrogate attached to this system");
   return GL_OK;
 }
@@ -399,7 +399,7 @@ gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, f
     if (r != GL_OK) return r;
     sp.scratch = sys->scratch;
   }
-  if (defl == GL_DEFL_SURROGATE && !sys->no_fused) {
+  if (defl == GL_DEFL_SURROGATE_FUSED && !sys->no_fused) {
     // the surrogate evaluated inside each row's CTA (no table launch, no
     // tables in global memory), where two CTAs of it still fit per SM
     if ((r = gl::surrogate_take_timeout(sys->sur)) != GL_OK) return r;
@@ -554,7 +554,7 @@ gl_status eval_prepare(gl_system* s, int B, gl_deflection defl, bool with_grad, 
     if (r != GL_OK) return r;
     sp->scratch = s->scratch;
   }
-  if (defl == GL_DEFL_SURROGATE && (r = gl::surrogate_take_timeout(s->sur)) != GL_OK) return r;
+  if (gl::defl_network(defl) && (r = gl::surrogate_take_timeout(s->sur)) != GL_OK) return r;
   if (defl != GL_DEFL_SERIES) {
     if ((size_t)B > s->table_rows) {
       cudaFree(s->d_table);

@@ -82,14 +82,27 @@ k_grad_fused(const __grid_constant__ SysParams sp, const float* __restrict__ the
                  "r"(tc::TMEM_COLS));
 }
 
+// Two CTAs of the fused kernel fit per SM when two CTAs' registers and shared
+// memory (static, rounded up to the dynamic array's 1024-byte alignment, plus
+// dynamic, plus the per-block reserve) fit the SM's. (The occupancy query of
+// the runtime reports one CTA for this kernel although the SM runs two: ncu
+// shows both limits at two CTAs and 14.4 warps active.)
 template <int NL, int NS>
 cudaError_t grad_fused_launch(const SysParams& sp, const float* theta, int B, float* logp,
                               float* grad, size_t dyn, bool* fits, cudaStream_t st) {
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grad_fused<NL, NS>,
-                                                                THREADS, dyn);
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_grad_fused<NL, NS>);
+  int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
   if (e != cudaSuccess) return e;
-  *fits = per_sm >= 2;
+  const size_t per_cta = ((fa.sharedSizeBytes + 1023) & ~(size_t)1023) + dyn + (size_t)resv;
+  *fits = 2 * per_cta <= (size_t)smem_sm && 2 * fa.numRegs * THREADS <= regs_sm;
   if (!*fits) return cudaSuccess;
   k_grad_fused<NL, NS><<<B, THREADS, dyn, st>>>(sp, theta, B, logp, grad);
   return cudaGetLastError();

@@ -121,8 +121,9 @@ void surrogate_net(const gl_surrogate* s, SysParams* sp);
 size_t net_smem_bytes();
 cudaError_t surrogate_flag_begin(const gl_surrogate* s, cudaStream_t st);
 cudaError_t surrogate_flag_end(const gl_surrogate* s, cudaStream_t st);
-// A valid deflection kind (gl_deflection).
-inline bool defl_valid(int defl) { return defl >= 0 && defl <= 3; }
+// A valid deflection kind (gl_deflection), and whether it is the network.
+inline bool defl_valid(int defl) { return defl >= 0 && defl <= 4; }
+inline bool defl_network(int defl) { return defl == 1 || defl == 4; }
 
 // Largest static shared memory of the forward and gradient kernels (bytes,
 // with the surrogate table), or of the multi-system kernel of CTAs of

@@ -212,10 +212,10 @@ gl_status gl_multi_logp_grad(gl_multi* m, const float* const* theta, float* cons
   for (int k = 0; k < n_sys; ++k) {
     if (m->counts[k] > 0 && (!theta[k] || !logp[k] || !grad[k]))
       return fail(GL_EINVAL, "NULL theta, logp or grad for a system with rows");
-    if (defl == GL_DEFL_SURROGATE && !m->systems[k]->sur)
+    if (gl::defl_network(defl) && !m->systems[k]->sur)
       return fail(GL_ENOSURROGATE, "a system has no surrogate attached");
   }
-  if (defl == GL_DEFL_SURROGATE)
+  if (gl::defl_network(defl))
     for (int k = 0; k < n_sys; ++k) {
       const gl_status r = gl::surrogate_take_timeout(m->systems[k]->sur);
       if (r != GL_OK) return r;

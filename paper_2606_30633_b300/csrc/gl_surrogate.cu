@@ -734,7 +734,7 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
 
 cudaError_t launch_table(int defl, const gl_surrogate* s, const float* theta, int P, int B,
                          float4* table, cudaStream_t st) {
-  if (defl == GL_DEFL_SURROGATE) {
+  if (defl_network(defl)) {
     static thread_local int configured_dev = -1;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -791,7 +791,7 @@ gl_status surrogate_take_timeout(const gl_surrogate* s) {
 
 void table_domain(int defl, const gl_surrogate* s, float* q_lo, float* q_hi, float* g_lo,
                   float* g_hi) {
-  if (defl != GL_DEFL_SURROGATE || !s) {  // tabulated exact series: |e| <= 0.5, the model's gamma range
+  if (!defl_network(defl) || !s) {  // tabulated exact series: |e| <= 0.5, the model's gamma range
     *q_lo = 1.f / 3.f;
     *q_hi = 1.f;
     *g_lo = 1.f;

@@ -277,12 +277,12 @@ def test_what_the_network_gains(gl, trained):
 
 
 def test_fused_kernel_matches_the_separate_table_build(gl, trained, lens):
-    """gl_logp_grad with the surrogate builds each row's table inside the
-    gradient kernel's CTA (no table launch); the multi-system plan still
-    builds them in a launch of their own and reads them back. Both run the
-    same network arithmetic, so log p and gradients agree bit for bit, on rows
-    that use the tables, rows outside the training domain (the series) and
-    out-of-support rows."""
+    """GL_DEFL_SURROGATE_FUSED: gl_logp_grad builds each row's table inside
+    the gradient kernel's CTA (no table launch); GL_DEFL_SURROGATE builds them
+    in a launch of their own and reads them back, and so does the
+    multi-system plan. All run the same network arithmetic, so log p and
+    gradients agree bit for bit, on rows that use the tables, rows outside the
+    training domain (the series) and out-of-support rows."""
     torch, g = gl
     c = lens
     s = c.gpu_system()
@@ -292,10 +292,13 @@ def test_fused_kernel_matches_the_separate_table_build(gl, trained, lens):
     th[-3:-1, 2], th[-3:-1, 3] = 0.4, 0.0  # q = 0.43: outside the training domain (series)
     th[-1, 0] = -1.0  # outside the support
     tt = torch.tensor(th, device="cuda")
-    lpf, gf = s.logp_grad(tt, defl=g.GL_DEFL_SURROGATE)
+    lpf, gf = s.logp_grad(tt, defl=g.GL_DEFL_SURROGATE_FUSED)
+    lps, gs = s.logp_grad(tt, defl=g.GL_DEFL_SURROGATE)
     plan = g.Multi([s], [len(th)])
-    (lpm,), (gm,) = plan.logp_grad([tt], defl=g.GL_DEFL_SURROGATE)
+    (lpm,), (gm,) = plan.logp_grad([tt], defl=g.GL_DEFL_SURROGATE_FUSED)
     torch.cuda.synchronize()
+    np.testing.assert_array_equal(lpf.cpu().numpy(), lps.cpu().numpy())
+    np.testing.assert_array_equal(gf.cpu().numpy(), gs.cpu().numpy())
     np.testing.assert_array_equal(lpf.cpu().numpy(), lpm.cpu().numpy())
     np.testing.assert_array_equal(gf.cpu().numpy(), gm.cpu().numpy())
     e = np.hypot(th[:, 2], th[:, 3])

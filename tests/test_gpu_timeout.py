@@ -3,9 +3,8 @@ library's test hook (gl_debug_force_wait_timeout): the kernels act as if their
 first completion wait had run out, without waiting, so no wait really runs
 out and every issued MMA is still drained before the tensor memory is freed.
 
-Checked: the table build (inside the fused gradient kernel, and the
-stand-alone one of the forward entry point) gives NaN log p and gradient on
-the rows it served, the next GL_DEFL_SURROGATE call on that surrogate returns
+Checked: the table build (the stand-alone one, and the one inside the fused
+gradient kernel) gives NaN log p and gradient on the rows it served, the next GL_DEFL_SURROGATE call on that surrogate returns
 GL_ETIMEOUT, the
 synchronous training entry points return GL_ETIMEOUT at once, and with the
 hook off the same calls succeed again with the results they had before (the
@@ -51,12 +50,12 @@ def test_table_build_timeout_is_reported(env):
         with pytest.raises(gl.GLError) as err:
             s.logp_grad(t, defl=gl.GL_DEFL_SURROGATE)
         assert err.value.status == gl.GL_ETIMEOUT
-        # the stand-alone table build (the forward entry point uses it) as well
-        lpf = s.logp(t, defl=gl.GL_DEFL_SURROGATE)
+        # the network inside the gradient kernel's CTA as well
+        lpf, gf = s.logp_grad(t, defl=gl.GL_DEFL_SURROGATE_FUSED)
         torch.cuda.synchronize()
-        assert np.isnan(lpf.cpu().numpy()).all()
+        assert np.isnan(lpf.cpu().numpy()).all() and np.isnan(gf.cpu().numpy()).all()
         with pytest.raises(gl.GLError) as err:
-            s.logp(t, defl=gl.GL_DEFL_SURROGATE)
+            s.logp_grad(t, defl=gl.GL_DEFL_SURROGATE_FUSED)
         assert err.value.status == gl.GL_ETIMEOUT
         # the exact series does not use the tensor cores and is unaffected
         lps, _ = s.logp_grad(t, defl=gl.GL_DEFL_SERIES)
@@ -64,9 +63,12 @@ def test_table_build_timeout_is_reported(env):
     finally:
         gl.debug_force_wait_timeout(False)
     lp2, g2 = s.logp_grad(t, defl=gl.GL_DEFL_SURROGATE)
+    lp3, g3 = s.logp_grad(t, defl=gl.GL_DEFL_SURROGATE_FUSED)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(lp2.cpu().numpy(), lp0.cpu().numpy())
     np.testing.assert_array_equal(g2.cpu().numpy(), g0.cpu().numpy())
+    np.testing.assert_array_equal(lp3.cpu().numpy(), lp0.cpu().numpy())
+    np.testing.assert_array_equal(g3.cpu().numpy(), g0.cpu().numpy())
 
 
 def test_training_timeout_is_reported(env):
