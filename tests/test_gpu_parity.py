@@ -8,9 +8,11 @@ Tolerances (FP32 path vs FP64 oracle):
                per-pixel model tolerance, 1e-5 sum_p |d_p - m_p| |m_p| /
                sigma_p^2, whichever is larger (lenscase.logp_bound). On these
                small, bright images (m/sigma up to ~600) with compact sources
-               an FP32 lens equation misses the plain 1e-6 (the stated bounds
-               are asserted as they stand on the ground-based workloads near
-               the mode in test_gpu_tolerances.py);
+               FP32 misses the plain 1e-6 on some rows; how often, shape by
+               shape, is measured and bounded in
+               test_stated_bounds_on_every_shape (the stated bounds are
+               asserted as they stand on the ground-based workloads near the
+               mode in test_gpu_tolerances.py);
   gradient     |g_k - g_ref,k| <= 1e-3 |g_ref,k| + EPS_MODEL sum_p (|m_p| +
                |d_p - m_p|) |dm_p/dtheta_k| / sigma_p^2 (the gradient change
                that a per-pixel model error EPS_MODEL = 5e-6 causes, from the
@@ -103,6 +105,37 @@ def test_gradient_matches_oracle(torch, case):
     assert ok, worst
     ok, worst = grad_close_bound(g.cpu().numpy(), gref, grad_bound(case, th))
     assert ok, worst
+
+
+def test_stated_bounds_on_every_shape(torch, case):
+    """The stated bounds as the first criterion on each shape: every log p and
+    gradient entry is measured against them (and printed); at least 97 % of
+    the gradient entries meet the gradient bound near the mode and at prior
+    draws, and on the images of 20 px and more with s >= 2 at least 75 % of
+    the near-mode rows meet log p's 1e-6. The rest is the FP32 floor of small
+    bright images with few sub-pixels: a MUFU power carries ~2 ulp of
+    relative error, the Sersic exponent b_n p (up to ~20) multiplies it, and
+    with s^2 <= 4 samples per pixel little of it averages out; every row stays
+    within the error-propagation bounds of the other tests."""
+    th = np.concatenate([_near_mode(case, 8), case.theta(8)])
+    sysg = case.gpu_system()
+    lp, g = sysg.logp_grad(torch.tensor(th, dtype=torch.float32, device="cuda"))
+    lp, g = lp.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
+    lref, gref = case.oracle.logp_grad(th)
+    rel = np.abs(lp - lref) / np.abs(lref)
+    scale = np.maximum(np.abs(gref), 1e-2 * np.abs(gref).max(1, keepdims=True))
+    r14 = np.abs(g - gref) / (1e-3 * scale)
+    W = case.W
+    print(f"\n{W.ny}x{W.nx} s={W.supersample}: log p within 1e-6 on "
+          f"{(rel[:8] <= 1e-6).mean():.2f} of near-mode rows (max {rel[:8].max():.2e}), "
+          f"{(rel[8:] <= 1e-6).mean():.2f} of prior draws (max {rel[8:].max():.2e}); gradient "
+          f"entries within 1e-3: {(r14[:8] <= 1).mean():.3f} near the mode (max {r14[:8].max():.2f}), "
+          f"{(r14[8:] <= 1).mean():.3f} at prior draws (max {r14[8:].max():.2f})")
+    assert (r14[:8] <= 1).mean() >= 0.97 and (r14[8:] <= 1).mean() >= 0.97
+    if min(W.ny, W.nx) >= 20 and W.supersample >= 2:
+        assert (rel[:8] <= 1e-6).mean() >= 0.75
+    assert logp_close(case, th, lp)[0]
+    assert grad_close_bound(g, gref, grad_bound(case, th))[0]
 
 
 def test_gradient_matches_central_differences(torch):
