@@ -205,15 +205,15 @@ __device__ __forceinline__ void write_intervals(const float4 (*node)[2], float4*
 
 // The network at the 128 nodes of one row (EPL axis ratio q, slope gamma) with
 // three forward-mode tangents: node j's (F, dv dF/dvphi) and (dF/dq, dF/dt)
-// into node[j]. All NTH threads of the CTA call it (128: one thread per node
-// does the whole epilogue; 256: the second warpgroup reads the same TMEM lanes
-// and takes the d/dq and d/dgamma tangents while the first takes the primal
-// and d/dvphi; per value the arithmetic is the same). The weights are in
-// shared memory at sm (load_weights); tb is the CTA's 256-column TMEM
-// allocation, bar an initialised mbarrier whose parity is phase. Returns false
-// (the block's common decision) when a bounded wait ran out or forced is set:
-// the commit of parity phase is then still outstanding and the caller drains
-// it before freeing the tensor memory.
+// into node[j]. All NTH threads of the CTA call it; the first warpgroup (one
+// thread per node) does the layer epilogues, and a second one (NTH = 256, the
+// fused gradient kernel) only takes part in the barriers (splitting the
+// epilogues between two warpgroups measured slower in both kernels). The
+// weights are in shared memory at sm (load_weights); tb is the CTA's
+// 256-column TMEM allocation, bar an initialised mbarrier whose parity is
+// phase. Returns false (the block's common decision) when a bounded wait ran
+// out or forced is set: the commit of parity phase is then still outstanding
+// and the caller drains it before freeing the tensor memory.
 template <int NTH>
 __device__ __forceinline__ bool net_row(const __nv_bfloat16* __restrict__ wb,
                                         const float* __restrict__ params, float q, float gamma,
@@ -221,7 +221,8 @@ __device__ __forceinline__ bool net_row(const __nv_bfloat16* __restrict__ wb,
                                         uint64_t* bar, uint32_t& phase, bool forced) {
   using namespace tc;
   static_assert(NTH == 128 || NTH == 256, "one or two warpgroups");
-  const int t = threadIdx.x, wg = t >> 7, nd = t & 127;
+  const int t = threadIdx.x, nd = t & 127;
+  const bool worker = t < 128;  // the first warpgroup
   const uint32_t lane_addr = tb + ((uint32_t)(32 * ((t >> 5) & 3)) << 16);
   unsigned char* A0 = sm + TB_A0;
   unsigned char* A = sm + TB_A;
@@ -234,7 +235,7 @@ __device__ __forceinline__ bool net_row(const __nv_bfloat16* __restrict__ wb,
   float vp, dv, x[4];
   table_node(nd, vp, dv);
   features(q, gamma, 0.f, vp, x);
-  if (wg == 0) {
+  if (worker) {
     const float v[8] = {x[0], x[1], x[2], x[3], 0.f, 0.f, 0.f, 0.f};
     const float zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     put8(A0, nd, 0, 16, v);
@@ -256,38 +257,22 @@ __device__ __forceinline__ bool net_row(const __nv_bfloat16* __restrict__ wb,
     const float* bias = params + (layer == 1 ? OFF_B1 : layer == 2 ? OFF_B2
                                                       : layer == 3 ? OFF_B3 : OFF_B4);
 #pragma unroll 1
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-      // NTH 128: da, db, dc are the three tangents; NTH 256: the first
-      // warpgroup's da is d/dvphi, the second's da, db are d/dq, d/dgamma
-      float z[16], da[16], db[16], dc[16];
+    for (int c0 = 0; c0 < (worker ? 64 : 0); c0 += 16) {
+      float z[16], d1[16], d2[16], d3[16];
       ld16(lane_addr + c0, z);
       if (layer > 1) {
-        if (NTH == 128) {
-          ld16(lane_addr + 64 + c0, da);
-          ld16(lane_addr + 128 + c0, db);
-          ld16(lane_addr + 192 + c0, dc);
-        } else if (wg == 0) {
-          ld16(lane_addr + 64 + c0, da);
-        } else {
-          ld16(lane_addr + 128 + c0, da);
-          ld16(lane_addr + 192 + c0, db);
-        }
+        ld16(lane_addr + 64 + c0, d1);
+        ld16(lane_addr + 128 + c0, d2);
+        ld16(lane_addr + 192 + c0, d3);
       }
       wait_ld();
       if (layer == 1) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const __nv_bfloat16* wrow = wb + BOFF_P1 + (c0 + j) * 16;
-          if (NTH == 128) {
-            da[j] = __bfloat162float(wrow[seed_in[0]]) * seed[0];
-            db[j] = __bfloat162float(wrow[seed_in[1]]) * seed[1];
-            dc[j] = __bfloat162float(wrow[seed_in[2]]) * seed[2];
-          } else if (wg == 0) {
-            da[j] = __bfloat162float(wrow[seed_in[0]]) * seed[0];
-          } else {
-            da[j] = __bfloat162float(wrow[seed_in[1]]) * seed[1];
-            db[j] = __bfloat162float(wrow[seed_in[2]]) * seed[2];
-          }
+          d1[j] = __bfloat162float(wrow[seed_in[0]]) * seed[0];
+          d2[j] = __bfloat162float(wrow[seed_in[1]]) * seed[1];
+          d3[j] = __bfloat162float(wrow[seed_in[2]]) * seed[2];
         }
       }
 #pragma unroll
@@ -296,30 +281,18 @@ __device__ __forceinline__ bool net_row(const __nv_bfloat16* __restrict__ wb,
         const float sg = sigm(zz);
         const float dsl = sg * (1.f + zz * (1.f - sg));
         z[j] = zz * sg;
-        da[j] *= dsl;
-        if (NTH == 128 || wg == 1) db[j] *= dsl;
-        if (NTH == 128) dc[j] *= dsl;
+        d1[j] *= dsl;
+        d2[j] *= dsl;
+        d3[j] *= dsl;
       }
-      if (NTH == 128) {
-        put8(A, nd, c0, 64, z);
-        put8(A, nd, c0 + 8, 64, z + 8);
-        put8(A + A_BYTES, nd, c0, 64, da);
-        put8(A + A_BYTES, nd, c0 + 8, 64, da + 8);
-        put8(A + 2 * A_BYTES, nd, c0, 64, db);
-        put8(A + 2 * A_BYTES, nd, c0 + 8, 64, db + 8);
-        put8(A + 3 * A_BYTES, nd, c0, 64, dc);
-        put8(A + 3 * A_BYTES, nd, c0 + 8, 64, dc + 8);
-      } else if (wg == 0) {
-        put8(A, nd, c0, 64, z);
-        put8(A, nd, c0 + 8, 64, z + 8);
-        put8(A + A_BYTES, nd, c0, 64, da);
-        put8(A + A_BYTES, nd, c0 + 8, 64, da + 8);
-      } else {
-        put8(A + 2 * A_BYTES, nd, c0, 64, da);
-        put8(A + 2 * A_BYTES, nd, c0 + 8, 64, da + 8);
-        put8(A + 3 * A_BYTES, nd, c0, 64, db);
-        put8(A + 3 * A_BYTES, nd, c0 + 8, 64, db + 8);
-      }
+      put8(A, nd, c0, 64, z);
+      put8(A, nd, c0 + 8, 64, z + 8);
+      put8(A + A_BYTES, nd, c0, 64, d1);
+      put8(A + A_BYTES, nd, c0 + 8, 64, d1 + 8);
+      put8(A + 2 * A_BYTES, nd, c0, 64, d2);
+      put8(A + 2 * A_BYTES, nd, c0 + 8, 64, d2 + 8);
+      put8(A + 3 * A_BYTES, nd, c0, 64, d3);
+      put8(A + 3 * A_BYTES, nd, c0 + 8, 64, d3 + 8);
     }
     to_async();
     if (t == 0) {
@@ -334,7 +307,7 @@ __device__ __forceinline__ bool net_row(const __nv_bfloat16* __restrict__ wb,
     }
   }
   // output layer: y (primal) and the three tangents' dy, two columns each
-  if (wg == 0) {
+  if (worker) {
     float y[2], dy[3][2];
     ld2(lane_addr, y);
     ld2(lane_addr + 64, dy[0]);
