@@ -40,10 +40,11 @@ def env():
 
 
 @pytest.mark.parametrize("policy", [0, 1, 2])
-@pytest.mark.parametrize("defl", ["series", "table"])
+@pytest.mark.parametrize("defl", ["series", "table", "table32"])
 def test_multi_matches_per_system(env, policy, defl):
     torch, gl, cases, systems, thetas = env
-    d = gl.GL_DEFL_SERIES if defl == "series" else gl.GL_DEFL_TABLE
+    d = {"series": gl.GL_DEFL_SERIES, "table": gl.GL_DEFL_TABLE,
+         "table32": gl.GL_DEFL_TABLE32}[defl]
     plan = gl.Multi(systems, [t.shape[0] for t in thetas], policy)
     lps, gs = plan.logp_grad(thetas, defl=d)
     lps2, gs2 = plan.logp_grad(thetas, lps, gs, defl=d)  # second call reuses the work lists
