@@ -145,3 +145,47 @@ def test_no_cpu_fallback_without_a_device(lib):
     with pytest.raises(gl.GLError) as e:
         gl.System(*_ground_system_args())
     assert e.value.status == gl.GL_ECUDA
+
+
+def test_deflection_kinds_match_the_header():
+    """The binding's deflection constants are the header's enum values."""
+    text = open(os.path.join(ROOT, "include", "gl.h")).read()
+    body = re.search(r"typedef enum \{([^}]*)\} gl_deflection;", text).group(1)
+    values = dict((k, int(v)) for k, v in re.findall(r"(GL_DEFL_[A-Z0-9_]+)\s*=\s*(\d+)", body))
+    assert values == {"GL_DEFL_SERIES": gl.GL_DEFL_SERIES, "GL_DEFL_SURROGATE": gl.GL_DEFL_SURROGATE,
+                      "GL_DEFL_TABLE": gl.GL_DEFL_TABLE, "GL_DEFL_TABLE32": gl.GL_DEFL_TABLE32,
+                      "GL_DEFL_SURROGATE_FUSED": gl.GL_DEFL_SURROGATE_FUSED}
+
+
+def test_multi_plan_rejects_bad_arguments(lib):
+    """Host-side validation of gl_multi_create_ex and gl_multi_logp_grad: the
+    launch shapes are checked before any system is touched (the fake system
+    pointer below is never dereferenced)."""
+    h = ctypes.c_void_p()
+    one = (ctypes.c_int * 1)(8)
+    fake = (ctypes.c_void_p * 1)(ctypes.c_void_p(16))
+    assert lib.gl_multi_create_ex(None, 1, one, 1, None, None, ctypes.byref(h)) == gl.GL_EINVAL
+    assert lib.gl_multi_create_ex(fake, 0, one, 1, None, None, ctypes.byref(h)) == gl.GL_EINVAL
+    assert lib.gl_multi_create_ex(fake, 1, one, 3, None, None, ctypes.byref(h)) == gl.GL_EINVAL
+    assert "smem_policy" in gl.last_error()
+    bad_threads = (ctypes.c_int * 1)(192)
+    assert lib.gl_multi_create_ex(fake, 1, one, 1, bad_threads, None, ctypes.byref(h)) == gl.GL_EINVAL
+    assert "threads_per_cta" in gl.last_error()
+    bad_pairs = (ctypes.c_int * 1)(4)
+    assert lib.gl_multi_create_ex(fake, 1, one, 1, None, bad_pairs, ctypes.byref(h)) == gl.GL_EINVAL
+    assert "pixel_pairs" in gl.last_error()
+    assert lib.gl_multi_create_ex(fake, 1, one, 1, None, None, None) == gl.GL_EINVAL
+    assert h.value is None
+    assert lib.gl_multi_logp_grad(None, None, None, None, 0, None) == gl.GL_EINVAL
+    assert lib.gl_multi_destroy(None) == gl.GL_OK
+
+
+def test_autotuner_image_classes():
+    """The tuner groups systems by image size, supersampling and PSF size."""
+    from types import SimpleNamespace as NS
+    from paper_2606_30633_b300 import autotune
+    a = NS(ny=100, nx=100, s=3, psf_size=11)
+    b = NS(ny=100, nx=100, s=3, psf_size=11)
+    c = NS(ny=100, nx=100, s=4, psf_size=11)
+    assert autotune.image_class(a) == autotune.image_class(b) != autotune.image_class(c)
+    assert set(autotune.SHAPES) == {(256, 2), (256, 3), (128, 2), (128, 3)}
