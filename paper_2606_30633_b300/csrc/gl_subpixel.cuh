@@ -69,6 +69,7 @@ __device__ __forceinline__ Clen2 clenshaw(const float2* __restrict__ c, int n2, 
   const float4* c4 = reinterpret_cast<const float4*>(c);
   const float2 tw = add2(g.wr, g.wr);
   float2 b1 = f2(0.f), b2 = f2(0.f);
+#pragma unroll 2  // two chunks per trip: less loop overhead in the forward
   for (int k = n2 - 1; k >= 0; --k) {
     const float4 a = c4[k];  // a_{2k+1} in (z, w), a_{2k} in (x, y)
     const float2 bh = clen_step(tw, b1, b2, make_float2(a.z, a.w));
@@ -85,6 +86,7 @@ __device__ __forceinline__ void clenshaw2(const float2* __restrict__ c, int n2, 
   const float4* c4 = reinterpret_cast<const float4*>(c);
   const float2 tw0 = add2(g0.wr, g0.wr), tw1 = add2(g1.wr, g1.wr);
   float2 p1 = f2(0.f), p2 = f2(0.f), q1 = f2(0.f), q2 = f2(0.f);
+#pragma unroll 2  // two chunks per trip: less loop overhead in the forward
   for (int k = n2 - 1; k >= 0; --k) {
     const float4 a = c4[k];
     const float2 ah = make_float2(a.z, a.w), al = make_float2(a.x, a.y);
@@ -110,6 +112,7 @@ __device__ __forceinline__ void clenshaw3(const float2* __restrict__ c, int n2, 
     b1[m] = f2(0.f);
     b2[m] = f2(0.f);
   }
+#pragma unroll 2  // two chunks per trip: less loop overhead in the forward
   for (int k = n2 - 1; k >= 0; --k) {
     const float4 a = c4[k];
     const float2 ah = make_float2(a.z, a.w), al = make_float2(a.x, a.y);
