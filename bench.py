@@ -449,12 +449,16 @@ def run_ours(args) -> dict | None:
     value = job_rate(B * args.steps, world, t_ms)
     assert torch.isfinite(logp).all(), "non-finite log p in the benchmark batch"
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: theta in pinned host
+    # memory, log p and the gradient back into pinned host memory
+    h_theta = gl.pinned_array(theta_np.shape)
+    h_theta[:] = theta_np
+    h_out = (gl.pinned_array((B,)), gl.pinned_array(theta_np.shape))
     e2e_ms = []
     for k in range(args.warmup + max(3, args.steps // 5)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        S.logp_grad_host(theta_np)
+        S.logp_grad_host(h_theta, out=h_out)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             e2e_ms.append(dt * 1e3)

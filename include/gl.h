@@ -160,9 +160,13 @@ gl_status gl_logp(gl_system* sys, const float* theta, int B, float* logp, gl_def
 gl_status gl_logp_grad(gl_system* sys, const float* theta, int B, float* logp, float* grad,
                        gl_deflection defl, void* stream);
 
-/* The same with HOST buffers: copies theta in through the system's pinned
- * staging buffers, evaluates, copies logp and grad (grad may be NULL) back and
- * waits for the stream. Grows the system's staging buffers on first use. */
+/* The same with HOST buffers: copies theta in, evaluates, copies logp and grad
+ * (grad may be NULL) back and waits for the stream. When every buffer passed is
+ * page-locked host memory (cudaHostAlloc, cudaHostRegister, torch's
+ * pin_memory) from its first to its last byte, the copies go directly between
+ * those buffers and the device; otherwise they go through the system's own
+ * pinned staging buffers (one host memcpy each way). Grows the system's
+ * staging buffers on first use. */
 gl_status gl_logp_grad_host(gl_system* sys, const float* theta_host, int B, float* logp_host,
                             float* grad_host, gl_deflection defl, void* stream);
 

@@ -392,14 +392,26 @@ class System:
         return out, grad
 
     def logp_grad_host(self, theta: np.ndarray, defl: int = GL_DEFL_SERIES, want_grad=True,
-                       stream=None):
-        """Host arrays in and out (the copies happen inside the call)."""
+                       stream=None, out=None):
+        """Host arrays in and out (the copies happen inside the call). out:
+        optional (logp [B], grad [B, P] or None) float32 arrays to fill. Arrays
+        from pinned_array() are copied to and from the device directly."""
         th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
         if th.ndim != 2 or th.shape[1] != self.P:
             raise ValueError(f"theta must be [B, {self.P}]")
         B = th.shape[0]
-        lp = np.empty(B, dtype=np.float32)
-        g = np.empty_like(th) if want_grad else None
+        if out is None:
+            lp = np.empty(B, dtype=np.float32)
+            g = np.empty_like(th) if want_grad else None
+        else:
+            lp, g = out
+            for a, shape, name in ((lp, (B,), "logp"), (g, (B, self.P), "grad")):
+                if a is None and name == "grad":
+                    continue
+                if (not isinstance(a, np.ndarray) or a.dtype != np.float32 or a.shape != shape
+                        or not a.flags.c_contiguous or not a.flags.writeable):
+                    raise ValueError(f"out {name} must be a writable contiguous float32 "
+                                     f"array of shape {shape}")
         _check(self._lib.gl_logp_grad_host(self._h, th.ctypes.data, B, lp.ctypes.data,
                                            None if g is None else g.ctypes.data, defl,
                                            _stream_ptr(stream)))
@@ -623,6 +635,15 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+def pinned_array(shape, dtype=np.float32) -> np.ndarray:
+    """An uninitialised numpy array in page-locked host memory (a view of a
+    pinned torch tensor, which the array keeps alive)."""
+    torch = _torch()
+    tdt = {np.dtype(np.float32): torch.float32, np.dtype(np.float64): torch.float64}[
+        np.dtype(dtype)]
+    return torch.empty(shape, dtype=tdt, pin_memory=True).numpy()
 
 
 def debug_force_wait_timeout(on: bool) -> None:

@@ -98,6 +98,23 @@ void plan_buffers(size_t buf_floats, int nbufs, size_t smem_budget, size_t* dyn,
 
 namespace {
 
+// True when [p, p + bytes) starts and ends in page-locked host memory, which
+// the copy engines read and write directly. An unregistered pointer is not an
+// error for the query (its type is cudaMemoryTypeUnregistered); any error it
+// does return is cleared.
+bool page_locked(const void* p, size_t bytes) {
+  const char* c = static_cast<const char*>(p);
+  for (const char* q : {c, c + bytes - 1}) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (a.type != cudaMemoryTypeHost) return false;
+  }
+  return true;
+}
+
 gl_status ensure_scratch(gl_system* s, size_t floats) {
   if (floats <= s->scratch_floats) return GL_OK;
   if (s->scratch) cudaFree(s->scratch);
@@ -507,10 +524,14 @@ gl_status gl_logp_grad_host(gl_system* sys, const float* theta_host, int B, floa
   float* d_theta = sys->d_stage;
   float* d_grad = d_theta + (size_t)B * P;
   float* d_logp = d_grad + (size_t)B * P;
-  float* h_theta = sys->h_stage;
-  float* h_grad = h_theta + (size_t)B * P;
-  float* h_logp = h_grad + (size_t)B * P;
-  std::memcpy(h_theta, theta_host, (size_t)B * P * 4);
+  // page-locked caller buffers are copied directly, others through the staging
+  const bool direct = page_locked(theta_host, (size_t)B * P * 4) &&
+                      page_locked(logp_host, (size_t)B * 4) &&
+                      (!grad_host || page_locked(grad_host, (size_t)B * P * 4));
+  float* h_theta = direct ? const_cast<float*>(theta_host) : sys->h_stage;
+  float* h_grad = direct ? grad_host : h_theta + (size_t)B * P;
+  float* h_logp = direct ? logp_host : h_grad + (size_t)B * P;
+  if (!direct) std::memcpy(h_theta, theta_host, (size_t)B * P * 4);
   GL_CUDA(cudaMemcpyAsync(d_theta, h_theta, (size_t)B * P * 4, cudaMemcpyHostToDevice, st), "H2D");
   if (grad_host)
     r = gl_logp_grad(sys, d_theta, B, d_logp, d_grad, defl, stream);
@@ -521,8 +542,10 @@ gl_status gl_logp_grad_host(gl_system* sys, const float* theta_host, int B, floa
   if (grad_host)
     GL_CUDA(cudaMemcpyAsync(h_grad, d_grad, (size_t)B * P * 4, cudaMemcpyDeviceToHost, st), "D2H");
   GL_CUDA(cudaStreamSynchronize(st), "stream synchronize");
-  std::memcpy(logp_host, h_logp, (size_t)B * 4);
-  if (grad_host) std::memcpy(grad_host, h_grad, (size_t)B * P * 4);
+  if (!direct) {
+    std::memcpy(logp_host, h_logp, (size_t)B * 4);
+    if (grad_host) std::memcpy(grad_host, h_grad, (size_t)B * P * 4);
+  }
   return GL_OK;
 }
 

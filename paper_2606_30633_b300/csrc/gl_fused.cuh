@@ -55,8 +55,11 @@ k_grad_fused(const __grid_constant__ SysParams sp, const float* __restrict__ the
     const float q = (1.f - cc) / (1.f + cc), gamma = th[1];
     float4(*node)[2] = reinterpret_cast<float4(*)[2]>(net + tc::TB_A);
     uint32_t phase = 0;
+    float vp, dv;
+    table_node(t & 127, vp, dv);
     const bool ok = net_row<THREADS>(static_cast<const __nv_bfloat16*>(sp.net_wb), sp.net_params,
-                                     q, gamma, net, node, tb, &bar, phase, sp.net_forced != 0);
+                                     q, gamma, vp, dv, net, node, tb, &bar, phase,
+                                     sp.net_forced != 0);
     if (ok) {
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();

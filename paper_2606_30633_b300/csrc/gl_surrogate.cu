@@ -344,7 +344,7 @@ __global__ void k_table_exact(const float* __restrict__ theta, int P, int B, flo
 // complex numbers, from the network at R = theta_E with forward-mode
 // derivatives (net_row, gl_tc.cuh), and the row's intervals follow from the
 // nodes; rows outside the training domain are skipped (the lens kernels use
-// the exact series there). Persistent CTAs of 4 warps keep the weights in
+// the exact series there). Persistent CTAs of 8 warps keep the weights in
 // shared memory across rows.
 namespace tc {
 
@@ -361,11 +361,12 @@ __device__ __forceinline__ bool forced_timeout() {
   return *reinterpret_cast<volatile int*>(&g_force_wait_timeout) != 0;
 }
 
-constexpr int NT = 128;  // threads = nodes = MMA rows
+constexpr int NT = 128;      // training: threads = samples = MMA rows
+constexpr int NT_TAB = 256;  // table build: two warpgroups split each layer's columns
 
 }  // namespace tc
 
-__global__ void __launch_bounds__(tc::NT, 1)
+__global__ void __launch_bounds__(tc::NT_TAB, 2)
 k_table_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict__ wimg,
            const float* __restrict__ params,
            const float* __restrict__ theta, int P, int B, float q_lo, float q_hi, float g_lo,
@@ -378,7 +379,7 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
   // P1..P4 are the first bytes of the packed training image (same layout)
   static_assert(TB_W1 == 0 && TB_WH == 64 * 16 * 2 && TB_W5 == 64 * 16 * 2 + 3 * 64 * 64 * 2,
                 "the table kernel's P1..P4 must match the packed image");
-  load_weights<NT>(sm, wimg, wb);
+  load_weights<NT_TAB>(sm, wimg, wb);
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -395,13 +396,15 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
   uint32_t phase = 0;
   bool ok = true;
   const bool forced = forced_timeout();
+  float vp, dv;  // this thread's node, the same in every row
+  table_node(t & 127, vp, dv);
   for (int b = blockIdx.x; b < B && ok; b += gridDim.x) {
     const float* th = theta + (size_t)b * P;
     const float e1 = th[2], e2 = th[3];
     const float cc = sqrtf(e1 * e1 + e2 * e2);
     const float q = (1.f - cc) / (1.f + cc), gamma = th[1];
     if (!(q >= q_lo && q <= q_hi && gamma >= g_lo && gamma <= g_hi)) continue;
-    ok = net_row<NT>(wb, params, q, gamma, sm, node, tb, &bar, phase, forced);
+    ok = net_row<NT_TAB>(wb, params, q, gamma, vp, dv, sm, node, tb, &bar, phase, forced);
     if (!ok) break;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -418,7 +421,7 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
     if (t == 0) atomicExch(timeout, 1);
     const float nan = __int_as_float(0x7fc00000);
     for (int b = blockIdx.x; b < B; b += gridDim.x)
-      for (int k = t; k < TABLE_ROW; k += NT)
+      for (int k = t; k < TABLE_ROW; k += NT_TAB)
         table[(size_t)b * TABLE_ROW + k] = make_float4(nan, nan, nan, nan);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -748,7 +751,7 @@ cudaError_t launch_table(int defl, const gl_surrogate* s, const float* theta, in
     e = cudaMemsetAsync(s->d_timeout, 0, sizeof(int), st);  // this launch's flag only
     if (e != cudaSuccess) return e;
     const int grid = B < 2 * sms ? B : 2 * sms;
-    k_table_tc<<<grid, tc::NT, tc::SMEM_BYTES, st>>>(s->wb, s->wimg, s->params, theta, P, B, s->q_lo,
+    k_table_tc<<<grid, tc::NT_TAB, tc::SMEM_BYTES, st>>>(s->wb, s->wimg, s->params, theta, P, B, s->q_lo,
                                                      s->q_hi, s->g_lo, s->g_hi, table,
                                                      s->d_timeout);
     e = cudaGetLastError();

@@ -3,15 +3,16 @@
 // and TMEM access, bounded mbarrier waits) and net_row, which evaluates the
 // network at the 128 table nodes of one row with three forward-mode tangents
 // and leaves each node's (F, dF/dpa, dF/dq, dF/dt). Used by the stand-alone
-// table build (k_table_tc, 128 threads) and by the fused gradient kernel
-// (k_grad_fused, 256 threads), which therefore build bit-identical tables.
+// table build (k_table_tc) and by the fused gradient kernel (k_grad_fused),
+// which therefore build bit-identical tables.
 //
 // Per row, the 128 nodes are the M = 128 rows of every layer's MMA
 // (tcgen05.mma kind::f16, BF16 operands in shared memory, FP32 accumulators in
 // tensor memory), for the primal pass and the three tangents (d/dvphi, d/dq,
 // d/dgamma) as four accumulators of 64 columns. One thread per node reads its
 // accumulator row back (tcgen05.ld), applies bias and SiLU (and SiLU' to the
-// tangents) and writes the next layer's BF16 operand. Operands use the
+// tangents) and writes the next layer's BF16 operand (two warpgroups split
+// the columns). Operands use the
 // canonical K-major layout without swizzle: 8 x 16-byte core matrices,
 // K-adjacent ones 128 B apart (LBO), row-group-adjacent ones K/8 x 128 B apart
 // (SBO).
@@ -205,10 +206,12 @@ __device__ __forceinline__ void write_intervals(const float4 (*node)[2], float4*
 
 // The network at the 128 nodes of one row (EPL axis ratio q, slope gamma) with
 // three forward-mode tangents: node j's (F, dv dF/dvphi) and (dF/dq, dF/dt)
-// into node[j]. All NTH threads of the CTA call it; the first warpgroup (one
-// thread per node) does the layer epilogues, and a second one (NTH = 256, the
-// fused gradient kernel) only takes part in the barriers (splitting the
-// epilogues between two warpgroups measured slower in both kernels). The
+// into node[j]; (vp, dv) is table_node(t mod 128), the same for every row. All NTH threads of the CTA call it. Thread t serves node
+// t mod 128: with one warpgroup it does all 64 columns of the four streams in
+// each layer epilogue, with two (NTH = 256) the first warpgroup does columns
+// 0-31 and the second 32-63 (warps w and w + 4 reach the same TMEM lanes), so
+// no accumulator is read twice. The first warpgroup alone writes the inputs and
+// reads the output layer. The
 // weights are in shared memory at sm (load_weights); tb is the CTA's
 // 256-column TMEM allocation, bar an initialised mbarrier whose parity is
 // phase. Returns false (the block's common decision) when a bounded wait ran
@@ -217,7 +220,8 @@ __device__ __forceinline__ void write_intervals(const float4 (*node)[2], float4*
 template <int NTH>
 __device__ __forceinline__ bool net_row(const __nv_bfloat16* __restrict__ wb,
                                         const float* __restrict__ params, float q, float gamma,
-                                        unsigned char* sm, float4 (*node)[2], uint32_t tb,
+                                        float vp, float dv, unsigned char* sm,
+                                        float4 (*node)[2], uint32_t tb,
                                         uint64_t* bar, uint32_t& phase, bool forced) {
   using namespace tc;
   static_assert(NTH == 128 || NTH == 256, "one or two warpgroups");
@@ -232,8 +236,7 @@ __device__ __forceinline__ bool net_row(const __nv_bfloat16* __restrict__ wb,
   const float seed[3] = {__bfloat162float(__float2bfloat16(1.f / PI_F)), 4.f,
                          __bfloat162float(__float2bfloat16(1.f / 0.3f))};
   const int seed_in[3] = {3, 0, 1};
-  float vp, dv, x[4];
-  table_node(nd, vp, dv);
+  float x[4];
   features(q, gamma, 0.f, vp, x);
   if (worker) {
     const float v[8] = {x[0], x[1], x[2], x[3], 0.f, 0.f, 0.f, 0.f};
@@ -256,16 +259,15 @@ __device__ __forceinline__ bool net_row(const __nv_bfloat16* __restrict__ wb,
     // epilogue of layer `layer`: bias, SiLU, SiLU' on the tangents, BF16 operands
     const float* bias = params + (layer == 1 ? OFF_B1 : layer == 2 ? OFF_B2
                                                       : layer == 3 ? OFF_B3 : OFF_B4);
+    constexpr int CW = 64 / (NTH / 128);  // columns per thread
+    const int cb = (t >> 7) * CW;
 #pragma unroll 1
-    for (int c0 = 0; c0 < (worker ? 64 : 0); c0 += 16) {
-      float z[16], d1[16], d2[16], d3[16];
-      ld16(lane_addr + c0, z);
-      if (layer > 1) {
-        ld16(lane_addr + 64 + c0, d1);
-        ld16(lane_addr + 128 + c0, d2);
-        ld16(lane_addr + 192 + c0, d3);
-      }
-      wait_ld();
+    for (int c0 = cb; c0 < cb + CW; c0 += 16) {
+      // the global loads (biases, layer 1's tangent seeds) go out before the
+      // accumulator reads, whose wait would otherwise hold them back
+      float z[16], d1[16], d2[16], d3[16], bz[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) bz[j] = bias[c0 + j];
       if (layer == 1) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -275,9 +277,16 @@ __device__ __forceinline__ bool net_row(const __nv_bfloat16* __restrict__ wb,
           d3[j] = __bfloat162float(wrow[seed_in[2]]) * seed[2];
         }
       }
+      ld16(lane_addr + c0, z);
+      if (layer > 1) {
+        ld16(lane_addr + 64 + c0, d1);
+        ld16(lane_addr + 128 + c0, d2);
+        ld16(lane_addr + 192 + c0, d3);
+      }
+      wait_ld();
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const float zz = z[j] + bias[c0 + j];
+        const float zz = z[j] + bz[j];
         const float sg = sigm(zz);
         const float dsl = sg * (1.f + zz * (1.f - sg));
         z[j] = zz * sg;

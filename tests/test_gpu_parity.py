@@ -314,6 +314,24 @@ def test_host_buffer_entry_point(torch):
     lp_d, g_d = sysg.logp_grad(torch.tensor(th, device="cuda"))
     np.testing.assert_array_equal(lp_h, lp_d.cpu().numpy())
     np.testing.assert_array_equal(g_h, g_d.cpu().numpy())
+    # page-locked buffers are copied directly, pageable ones through the
+    # staging buffers: both give the device call's results
+    import paper_2606_30633_b300 as gl
+    h_th = gl.pinned_array(th.shape)
+    h_th[:] = th
+    out = (gl.pinned_array((9,)), gl.pinned_array(th.shape))
+    lp_p, g_p = sysg.logp_grad_host(h_th, out=out)
+    assert lp_p is out[0] and g_p is out[1]
+    np.testing.assert_array_equal(lp_p, lp_d.cpu().numpy())
+    np.testing.assert_array_equal(g_p, g_d.cpu().numpy())
+    lp_m, g_m = sysg.logp_grad_host(h_th)  # pinned theta, pageable outputs
+    np.testing.assert_array_equal(lp_m, lp_d.cpu().numpy())
+    np.testing.assert_array_equal(g_m, g_d.cpu().numpy())
+    lp_o, g_o = sysg.logp_grad_host(h_th, want_grad=False, out=(gl.pinned_array((9,)), None))
+    assert g_o is None
+    np.testing.assert_array_equal(lp_o, lp_d.cpu().numpy())
+    with pytest.raises(ValueError):
+        sysg.logp_grad_host(h_th, out=(np.empty(8, np.float32), None))
 
 
 def test_autograd_function(torch):
