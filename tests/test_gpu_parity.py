@@ -74,9 +74,15 @@ def test_model_image_matches_oracle(torch, case):
     sysg = case.gpu_system()
     img = sysg.model_image(torch.tensor(th, dtype=torch.float32, device="cuda")).cpu().numpy()
     ref = case.oracle.model_image(th)
+    frac = 0.0  # worst pixel error over the stated per-pixel bound
     for b in range(th.shape[0]):
         ok, worst = image_close(img[b].astype(np.float64), ref[b])
         assert ok, (b, worst)
+        bound = np.maximum(1e-5 * np.abs(ref[b]), 1e-4 * np.abs(ref[b]).max())
+        frac = max(frac, float(np.max(np.abs(img[b] - ref[b]) / bound)))
+    W = case.W
+    print(f"\n{W.ny}x{W.nx} s={W.supersample}: model image worst pixel error / stated bound "
+          f"{frac:.3f}")
 
 
 def test_logp_matches_oracle(torch, case):
@@ -371,3 +377,13 @@ def test_full_size_sampled_rows(torch, which):
     assert ok, worst
     lpf = sysg.logp(t).cpu().numpy()
     np.testing.assert_array_equal(lpf, lp)
+    # the model image of two rows (a prior draw, the near-mode row) per pixel
+    img = sysg.model_image(t[:2]).cpu().numpy().astype(np.float64)
+    iref = c.oracle.model_image(th_all[:2])
+    frac = 0.0
+    for b in range(2):
+        ok, worst = image_close(img[b], iref[b])
+        assert ok, (b, worst)
+        bound = np.maximum(1e-5 * np.abs(iref[b]), 1e-4 * np.abs(iref[b]).max())
+        frac = max(frac, float(np.max(np.abs(img[b] - iref[b]) / bound)))
+    print(f"\n{which} full size: model image worst pixel error / stated bound {frac:.3f}")
