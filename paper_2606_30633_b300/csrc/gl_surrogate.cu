@@ -361,7 +361,6 @@ __device__ __forceinline__ bool forced_timeout() {
   return *reinterpret_cast<volatile int*>(&g_force_wait_timeout) != 0;
 }
 
-constexpr int NT = 128;      // training: threads = samples = MMA rows
 constexpr int NT_TAB = 256;  // table build: two warpgroups split each layer's columns
 
 }  // namespace tc
@@ -432,9 +431,10 @@ k_table_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
 }
 
 // --------------------------------------- training step on tcgen05 ----
-// One training step for a 128-sample tile (thread t = sample t): forward,
-// MSE loss, backward, with every 64-wide contraction on tcgen05.mma and FP32
-// accumulators in tensor memory:
+// One training step for a 128-sample tile (threads t and t + 128 = sample t,
+// each with half of every layer's 64 columns): forward, MSE loss, backward,
+// with every 64-wide contraction on tcgen05.mma and FP32 accumulators in
+// tensor memory:
 //   forward   z_l = A_{l-1} W_l^T          (M = 128 samples, N = 64, K = 16 / 64)
 //   backward  dA_{l-1} = dZ_l W_l          (M = 128, N = 64, K = 64; B = W_l^T)
 //             dW_l = dZ_l^T A_{l-1}        (M = 64 outputs padded to 128 with zero
@@ -456,6 +456,8 @@ constexpr int TR_DZT = TR_SP + 3 * 128 * 64 * 2;  // dZ^T [128][128], rows 64.. 
 constexpr int TR_RED = TR_DZT + 128 * 128 * 2;  // column-sum scratch [4][128] float
 constexpr int TR_SMEM = TR_RED + 4 * 128 * 4;
 constexpr uint32_t TR_TMEM_COLS = 128;          // [0, 64) forward / dA, [64, 128) dW
+constexpr int TILE_S = 128;  // samples per tile (the MMAs' M)
+constexpr int NT_TR = 256;   // threads: two per sample, each half of its columns
 
 // Element (r, k) of an [R][128] operand in the core-matrix layout.
 __device__ __forceinline__ void put_t(unsigned char* base, int r, int k, float v) {
@@ -464,10 +466,12 @@ __device__ __forceinline__ void put_t(unsigned char* base, int r, int k, float v
 
 __device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
-// Sums of N per-thread values over the 128 threads: each warp's 32-value
-// chunks by reduce-scatter, then the four warps; dst[k] = sum (k < N).
-template <int N>
-__device__ void colsum(const float (&v)[N], float* red, float* __restrict__ dst) {
+// Sums over the tile's 128 samples of N per-thread values, separately for the
+// two warpgroups (each holds half of every sample's columns): each warp's
+// 32-value chunks by reduce-scatter, then the warpgroup's four warps.
+// put(g, k, sum) receives warpgroup g's sum k (k < n_out <= N).
+template <int N, class Put>
+__device__ void colsum(const float (&v)[N], float* red, int n_out, Put put) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < N / 32; ++c) {
@@ -487,13 +491,16 @@ __device__ void colsum(const float (&v)[N], float* red, float* __restrict__ dst)
     red[w * N + 32 * c + lane] = x[0];
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < N; k += NT) dst[k] = red[k] + red[N + k] + red[2 * N + k] + red[3 * N + k];
+  const int g = threadIdx.x >> 7;
+  const float* r = red + 4 * g * N;
+  for (int k = threadIdx.x & 127; k < n_out; k += 128)
+    put(g, k, r[k] + r[N + k] + r[2 * N + k] + r[3 * N + k]);
   __syncthreads();
 }
 
 }  // namespace tc
 
-__global__ void __launch_bounds__(tc::NT, 1)
+__global__ void __launch_bounds__(tc::NT_TR, 1)
 k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict__ wimg,
            const float* __restrict__ params,
            const float4* __restrict__ X, const float2* __restrict__ Y, long long n_data,
@@ -504,7 +511,10 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t bar;
   __shared__ float lsum_w[4];
+  __shared__ float2 ypart[2][TILE_S];  // the two halves' output-layer sums per sample
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  // sample smp of the tile; warpgroup g holds its columns [cb, cb + 32)
+  const int smp = t & (TILE_S - 1), g = t >> 7, cb = 32 * g;
   float* gp = gpart + (size_t)blockIdx.x * NPARAM;
   float* red = reinterpret_cast<float*>(sm + TR_RED);
   // weights in the operand layout; zero the transposed buffers (padding rows)
@@ -514,11 +524,11 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
     const uint4* src = reinterpret_cast<const uint4*>(wimg);
     uint4* dst = reinterpret_cast<uint4*>(sm + TR_W1);
 #pragma unroll 5
-    for (int k = t; k < TRAIN_IMG_BYTES / 16; k += NT) dst[k] = src[k];
+    for (int k = t; k < TRAIN_IMG_BYTES / 16; k += NT_TR) dst[k] = src[k];
   }
-  for (int k = t; k < (TR_AT - TR_XT) / 16; k += NT)
+  for (int k = t; k < (TR_AT - TR_XT) / 16; k += NT_TR)
     reinterpret_cast<uint4*>(sm + TR_XT)[k] = make_uint4(0u, 0u, 0u, 0u);
-  for (int k = t; k < (TR_RED - TR_DZT) / 16; k += NT)
+  for (int k = t; k < (TR_RED - TR_DZT) / 16; k += NT_TR)
     reinterpret_cast<uint4*>(sm + TR_DZT)[k] = make_uint4(0u, 0u, 0u, 0u);
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
@@ -532,7 +542,7 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
   }
   __syncthreads();
   // the sample
-  const long long tr = (long long)blockIdx.x * NT + t;
+  const long long tr = (long long)blockIdx.x * TILE_S + smp;
   const long long idx = (row0 + tr * stride) % n_data;
   float x[4];
   {
@@ -540,16 +550,17 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
     features(v.x, v.y, v.z, v.w, x);
   }
   const float2 tgt = Y[idx];
-  {
+  if (g == 0) {
     const float v8[8] = {x[0], x[1], x[2], x[3], 0.f, 0.f, 0.f, 0.f};
     const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    put8(sm + TR_X0, t, 0, 16, v8);
-    put8(sm + TR_X0, t, 8, 16, z8);
-    for (int f = 0; f < 4; ++f) put_t(sm + TR_XT, f, t, x[f]);
+    put8(sm + TR_X0, smp, 0, 16, v8);
+    put8(sm + TR_X0, smp, 8, 16, z8);
+    for (int f = 0; f < 4; ++f) put_t(sm + TR_XT, f, smp, x[f]);
   }
   to_async();
   const uint32_t tb = tmem_base;
-  const uint32_t lane_addr = tb + ((uint32_t)(32 * w) << 16);
+  // warps w and w + 4 reach the same TMEM lanes: the tile's samples 32 (w mod 4) ..
+  const uint32_t lane_addr = tb + ((uint32_t)(32 * (w & 3)) << 16);
   const uint32_t sA = smem_u32(sm + TR_A), sX0 = smem_u32(sm + TR_X0), sXT = smem_u32(sm + TR_XT);
   const uint32_t sAT = smem_u32(sm + TR_AT), sDZT = smem_u32(sm + TR_DZT);
   const uint32_t sW1 = smem_u32(sm + TR_W1), sWH = smem_u32(sm + TR_WH), sTH = smem_u32(sm + TR_TH);
@@ -570,13 +581,14 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
     mma(tb, sdesc(sX0, 256), sdesc(sW1, 256), idesc(128, 64), 0u);
     commit(&bar);
   }
-  float a4[64], s4[64];
+  float a4[32], s4[32];  // this half's columns of the last hidden layer and its SiLU'
   const int OFFB[4] = {mlp::OFF_B1, mlp::OFF_B2, mlp::OFF_B3, mlp::OFF_B4};
   for (int l = 1; l <= 4 && ok; ++l) {
     if (!wait()) { ok = false; break; }
     const float* bias = params + OFFB[l - 1];
 #pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 16) {
+    for (int h = 0; h < 32; h += 16) {
+      const int c0 = cb + h;
       float z[16];
       ld16(lane_addr + c0, z);
       wait_ld();
@@ -589,12 +601,12 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
         sp[j] = bfr(sg * (1.f + zz * (1.f - sg)));
       }
       if (l < 4) {
-        put8(sm + TR_A, t, c0, 64, a);
-        put8(sm + TR_A, t, c0 + 8, 64, a + 8);
+        put8(sm + TR_A, smp, c0, 64, a);
+        put8(sm + TR_A, smp, c0 + 8, 64, a + 8);
         unsigned char* at = sm + TR_AT + (l - 1) * 16384;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) put_t(at, c0 + j, t, a[j]);
-        uint4* spr = reinterpret_cast<uint4*>(sm + TR_SP + (l - 1) * 16384 + t * 128 + c0 * 2);
+        for (int j = 0; j < 16; ++j) put_t(at, c0 + j, smp, a[j]);
+        uint4* spr = reinterpret_cast<uint4*>(sm + TR_SP + (l - 1) * 16384 + smp * 128 + c0 * 2);
         spr[0] = make_uint4(pack_bf16(sp[0], sp[1]), pack_bf16(sp[2], sp[3]),
                             pack_bf16(sp[4], sp[5]), pack_bf16(sp[6], sp[7]));
         spr[1] = make_uint4(pack_bf16(sp[8], sp[9]), pack_bf16(sp[10], sp[11]),
@@ -602,8 +614,8 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
       } else {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          a4[c0 + j] = a[j];
-          s4[c0 + j] = sp[j];
+          a4[h + j] = a[j];
+          s4[h + j] = sp[j];
         }
       }
     }
@@ -620,58 +632,71 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
   }
   if (ok) {
     // ---- output layer, loss and its gradients (CUDA cores) ----
-    float y[2], dz5[2], dz5b[2];
-    for (int o = 0; o < 2; ++o) {
-      float acc = 0.f;
-      for (int i = 0; i < 64; ++i) acc = fmaf(__bfloat162float(wb[BOFF_P5 + o * 64 + i]), a4[i], acc);
-      y[o] = acc;
+    {
+      float yp[2];
+      for (int o = 0; o < 2; ++o) {
+        float acc = 0.f;
+        for (int i = 0; i < 32; ++i)
+          acc = fmaf(__bfloat162float(wb[BOFF_P5 + o * 64 + cb + i]), a4[i], acc);
+        yp[o] = acc;
+      }
+      ypart[g][smp] = make_float2(yp[0], yp[1]);
     }
-    const float e0 = y[0] + params[mlp::OFF_B5] - tgt.x, e1 = y[1] + params[mlp::OFF_B5 + 1] - tgt.y;
+    __syncthreads();
+    // both halves form the same y (the same two sums in the same order)
+    const float2 y0 = ypart[0][smp], y1 = ypart[1][smp];
+    const float e0 = (y0.x + y1.x) + params[mlp::OFF_B5] - tgt.x;
+    const float e1 = (y0.y + y1.y) + params[mlp::OFF_B5 + 1] - tgt.y;
     float ls = e0 * e0 + e1 * e1;
+    float dz5[2], dz5b[2];
     dz5[0] = 2.f * e0 * inv_batch;
     dz5[1] = 2.f * e1 * inv_batch;
     dz5b[0] = bfr(dz5[0]);
     dz5b[1] = bfr(dz5[1]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
-    if (lane == 0) lsum_w[w] = ls;
+    if (lane == 0 && g == 0) lsum_w[w] = ls;
     {
+      // db5 from the first half only (the second's values are zero)
       float db5[32];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) db5[k] = k < 2 ? dz5[k] : 0.f;
-      float tmp[2];
-      colsum<32>(db5, red, red + 512 - 32);  // scratch tail, read back below
-      if (t < 2) tmp[0] = red[512 - 32 + t];
-      __syncthreads();
-      if (t < 2) gp[mlp::OFF_B5 + t] = tmp[0];
+      for (int k = 0; k < 32; ++k) db5[k] = (k < 2 && g == 0) ? dz5[k] : 0.f;
+      colsum<32>(db5, red, 2, [&](int gg, int k, float v) {
+        if (gg == 0) gp[mlp::OFF_B5 + k] = v;
+      });
       if (t == 0) lpart[blockIdx.x] = lsum_w[0] + lsum_w[1] + lsum_w[2] + lsum_w[3];
     }
     {
-      float dw5[128];
+      // dW5[o][cb + i], o = k / 32, i = k mod 32
+      float dw5[64];
 #pragma unroll
-      for (int k = 0; k < 128; ++k) dw5[k] = dz5b[k >> 6] * a4[k & 63];
-      colsum<128>(dw5, red, gp + mlp::OFF_W5);
+      for (int k = 0; k < 64; ++k) dw5[k] = dz5b[k >> 5] * a4[k & 31];
+      colsum<64>(dw5, red, 64, [&](int gg, int k, float v) {
+        gp[mlp::OFF_W5 + (k >> 5) * 64 + 32 * gg + (k & 31)] = v;
+      });
     }
-    // dA4 = dZ5 W5, dZ4 = dA4 * SiLU'(z4)
-    float dz[64];
+    // dA4 = dZ5 W5, dZ4 = dA4 * SiLU'(z4), this half's columns
+    float dz[32];
 #pragma unroll
-    for (int i = 0; i < 64; ++i) {
-      const float da = dz5b[0] * __bfloat162float(wb[BOFF_P5 + i]) +
-                       dz5b[1] * __bfloat162float(wb[BOFF_P5 + 64 + i]);
+    for (int i = 0; i < 32; ++i) {
+      const float da = dz5b[0] * __bfloat162float(wb[BOFF_P5 + cb + i]) +
+                       dz5b[1] * __bfloat162float(wb[BOFF_P5 + 64 + cb + i]);
       dz[i] = da * s4[i];
     }
     // ---- backward through the hidden layers ----
     const int OFFW[4] = {mlp::OFF_W1, mlp::OFF_W2, mlp::OFF_W3, mlp::OFF_W4};
     for (int l = 4; l >= 1 && ok; --l) {
-      colsum<64>(dz, red, gp + OFFB[l - 1]);  // db_l
+      colsum<32>(dz, red, 32, [&](int gg, int k, float v) {  // db_l
+        gp[OFFB[l - 1] + 32 * gg + k] = v;
+      });
 #pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 8) {
+      for (int h = 0; h < 32; h += 8) {
         float v8[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v8[j] = dz[c0 + j];
-        put8(sm + TR_A, t, c0, 64, v8);
+        for (int j = 0; j < 8; ++j) v8[j] = dz[h + j];
+        put8(sm + TR_A, smp, cb + h, 64, v8);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) put_t(sm + TR_DZT, c0 + j, t, v8[j]);
+        for (int j = 0; j < 8; ++j) put_t(sm + TR_DZT, cb + h + j, smp, v8[j]);
       }
       to_async();
       if (t == 0) {
@@ -690,28 +715,30 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
         commit(&bar);
       }
       if (!wait()) { ok = false; break; }
-      // dW_l rows (outputs) live in TMEM lanes 0..63: warps 0 and 1
+      // dW_l rows (outputs) live in TMEM lanes 0..63: warps 0, 1 and 4, 5; the
+      // halves split its columns (layer 1's 16 stay with the first)
       const int in_dim = l > 1 ? 64 : NIN;
-      if (w < 2) {
-        for (int c0 = 0; c0 < (l > 1 ? 64 : 16); c0 += 16) {
+      if ((w & 3) < 2 && (l > 1 || g == 0)) {
+        const int row = t & 63, c_lo = l > 1 ? cb : 0, c_hi = l > 1 ? cb + 32 : 16;
+        for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
           float v[16];
           ld16(lane_addr + 64 + c0, v);
           wait_ld();
           for (int j = 0; j < 16; ++j)
-            if (c0 + j < in_dim) gp[OFFW[l - 1] + t * in_dim + c0 + j] = v[j];
+            if (c0 + j < in_dim) gp[OFFW[l - 1] + row * in_dim + c0 + j] = v[j];
         }
       }
       if (l > 1) {
-        const unsigned char* spl = sm + TR_SP + (l - 2) * 16384 + t * 128;
+        const unsigned char* spl = sm + TR_SP + (l - 2) * 16384 + smp * 128;
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int h = 0; h < 32; h += 16) {
           float v[16];
-          ld16(lane_addr + c0, v);
+          ld16(lane_addr + cb + h, v);
           wait_ld();
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            dz[c0 + j] = v[j] * __bfloat162float(
-                                    reinterpret_cast<const __nv_bfloat16*>(spl)[c0 + j]);
+            dz[h + j] = v[j] * __bfloat162float(
+                                   reinterpret_cast<const __nv_bfloat16*>(spl)[cb + h + j]);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -726,7 +753,7 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
       atomicExch(timeout, 1);
       lpart[blockIdx.x] = __int_as_float(0x7fc00000);
     }
-    for (int k = t; k < NPARAM; k += NT) gp[k] = __int_as_float(0x7fc00000);
+    for (int k = t; k < NPARAM; k += NT_TR) gp[k] = __int_as_float(0x7fc00000);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -935,7 +962,7 @@ gl_status gl_surrogate_loss_grad(const gl_surrogate* s, const float* x, const fl
            "smem limit");
   SUR_CUDA(cudaMalloc(&tb.timeout, sizeof(int)), "alloc");
   SUR_CUDA(cudaMemset(tb.timeout, 0, sizeof(int)), "flag reset");
-  gl::k_train_tc<<<ntiles, gl::tc::NT, gl::tc::TR_SMEM>>>(
+  gl::k_train_tc<<<ntiles, gl::tc::NT_TR, gl::tc::TR_SMEM>>>(
       s->wb, s->wimg, s->params, reinterpret_cast<const float4*>(x),
       reinterpret_cast<const float2*>(target), N, 0, 1, 1.f / N, tb.gpart, tb.lpart, tb.timeout);
   k_adam<<<(NPARAM + 255) / 256, 256>>>(nullptr, nullptr, nullptr, tb.gpart, ntiles, 0.f, 0.f, 0.f,
@@ -1012,7 +1039,7 @@ gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** ou
     bc2 *= b2;
     k_pack<<<(NBF16 + 255) / 256, 256>>>(s->params, s->wb, s->wimg);
     const long long row0 = (it * (long long)d->batch) % n;
-    gl::k_train_tc<<<ntiles, gl::tc::NT, gl::tc::TR_SMEM>>>(s->wb, s->wimg, s->params, tb.X, tb.Y,
+    gl::k_train_tc<<<ntiles, gl::tc::NT_TR, gl::tc::TR_SMEM>>>(s->wb, s->wimg, s->params, tb.X, tb.Y,
                                                             n, row0,
                                                             stride, 1.f / d->batch, tb.gpart,
                                                             tb.lpart, tb.timeout);
