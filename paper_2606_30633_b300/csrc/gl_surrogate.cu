@@ -458,6 +458,8 @@ constexpr int TR_SMEM = TR_RED + 4 * 128 * 4;
 constexpr uint32_t TR_TMEM_COLS = 128;          // [0, 64) forward / dA, [64, 128) dW
 constexpr int TILE_S = 128;  // samples per tile (the MMAs' M)
 constexpr int NT_TR = 256;   // threads: two per sample, each half of its columns
+constexpr int DWS = 65;      // row stride (floats) of a dW block staged in shared memory
+static_assert(64 * DWS * 4 <= TR_XT - TR_A, "the staged dW block fits over A and X0");
 
 // Element (r, k) of an [R][128] operand in the core-matrix layout.
 __device__ __forceinline__ void put_t(unsigned char* base, int r, int k, float v) {
@@ -716,8 +718,12 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
       }
       if (!wait()) { ok = false; break; }
       // dW_l rows (outputs) live in TMEM lanes 0..63: warps 0, 1 and 4, 5; the
-      // halves split its columns (layer 1's 16 stay with the first)
+      // halves split its columns (layer 1's 16 stay with the first). They go to
+      // shared memory first (rows DWS floats apart, over the operand A, whose
+      // MMAs are complete, and X0, unused in the backward pass), so that the
+      // global stores below are coalesced.
       const int in_dim = l > 1 ? 64 : NIN;
+      float* dws = reinterpret_cast<float*>(sm + TR_A);
       if ((w & 3) < 2 && (l > 1 || g == 0)) {
         const int row = t & 63, c_lo = l > 1 ? cb : 0, c_hi = l > 1 ? cb + 32 : 16;
         for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
@@ -725,7 +731,7 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
           ld16(lane_addr + 64 + c0, v);
           wait_ld();
           for (int j = 0; j < 16; ++j)
-            if (c0 + j < in_dim) gp[OFFW[l - 1] + row * in_dim + c0 + j] = v[j];
+            if (c0 + j < in_dim) dws[row * DWS + c0 + j] = v[j];
         }
       }
       if (l > 1) {
@@ -743,6 +749,11 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
+      static_assert(NIN == 4, "layer 1's dW rows are 4 wide");
+      const int sh = l > 1 ? 6 : 2;  // log2 in_dim
+      for (int k = t; k < 64 * in_dim; k += NT_TR)
+        gp[OFFW[l - 1] + k] = dws[(k >> sh) * DWS + (k & (in_dim - 1))];
+      // (the next layer's column sums synchronise before operand A is rewritten)
     }
   }
   if (!ok) {
