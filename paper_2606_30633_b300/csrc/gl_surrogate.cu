@@ -185,13 +185,29 @@ __global__ void k_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ 
 // Sum of the tiles' gradients and Adam (FP32 master weights); writes the
 // gradient itself when out_grad is non-null (tests) and skips the update when
 // lr == 0.
-__global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                       const float* __restrict__ gpart, int ntiles, float lr, float b1, float b2,
-                       float eps, float bc1, float bc2, float* __restrict__ out_grad) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= NPARAM) return;
+// The gradient of parameter k is the sum of the tiles' partial gradients:
+// a CTA of ADAM_THREADS takes ADAM_PAR consecutive parameters, each warp the
+// tiles t = warp, warp + 8, ... of them (coalesced rows), and the eight
+// partial sums are added in a fixed order (deterministic).
+constexpr int ADAM_PAR = 32, ADAM_THREADS = 256;
+__global__ void __launch_bounds__(ADAM_THREADS)
+k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+       const float* __restrict__ gpart, int ntiles, float lr, float b1, float b2, float eps,
+       float bc1, float bc2, float* __restrict__ out_grad) {
+  constexpr int NG = ADAM_THREADS / ADAM_PAR;
+  __shared__ float part[NG][ADAM_PAR];
+  const int pl = threadIdx.x % ADAM_PAR, grp = threadIdx.x / ADAM_PAR;
+  const int k = blockIdx.x * ADAM_PAR + pl;
+  float s = 0.f;
+  if (k < NPARAM) {
+#pragma unroll 16
+    for (int t = grp; t < ntiles; t += NG) s += gpart[(size_t)t * NPARAM + k];
+  }
+  part[grp][pl] = s;
+  __syncthreads();
+  if (grp != 0 || k >= NPARAM) return;
   float gsum = 0.f;
-  for (int t = 0; t < ntiles; ++t) gsum += gpart[(size_t)t * NPARAM + k];
+  for (int g = 0; g < NG; ++g) gsum += part[g][pl];
   if (out_grad) out_grad[k] = gsum;
   if (lr == 0.f) return;
   const float mk = b1 * m[k] + (1.f - b1) * gsum;
@@ -591,13 +607,15 @@ k_train_tc(const __nv_bfloat16* __restrict__ wb, const unsigned char* __restrict
 #pragma unroll
     for (int h = 0; h < 32; h += 16) {
       const int c0 = cb + h;
-      float z[16];
+      float z[16], bz[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) bz[j] = bias[c0 + j];  // before the accumulator wait
       ld16(lane_addr + c0, z);
       wait_ld();
       float a[16], sp[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const float zz = z[j] + bias[c0 + j];
+        const float zz = z[j] + bz[j];
         const float sg = sigm(zz);
         a[j] = bfr(zz * sg);
         sp[j] = bfr(sg * (1.f + zz * (1.f - sg)));
@@ -976,8 +994,8 @@ gl_status gl_surrogate_loss_grad(const gl_surrogate* s, const float* x, const fl
   gl::k_train_tc<<<ntiles, gl::tc::NT_TR, gl::tc::TR_SMEM>>>(
       s->wb, s->wimg, s->params, reinterpret_cast<const float4*>(x),
       reinterpret_cast<const float2*>(target), N, 0, 1, 1.f / N, tb.gpart, tb.lpart, tb.timeout);
-  k_adam<<<(NPARAM + 255) / 256, 256>>>(nullptr, nullptr, nullptr, tb.gpart, ntiles, 0.f, 0.f, 0.f,
-                                       0.f, 1.f, 1.f, tb.loss);
+  k_adam<<<(NPARAM + ADAM_PAR - 1) / ADAM_PAR, ADAM_THREADS>>>(
+      nullptr, nullptr, nullptr, tb.gpart, ntiles, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, tb.loss);
   k_sum<<<1, 256>>>(tb.lpart, ntiles, tb.loss + NPARAM);
   SUR_CUDA(cudaGetLastError(), "loss/gradient launch");
   SUR_CUDA(cudaMemcpy(grad_host, tb.loss, NPARAM * sizeof(float), cudaMemcpyDeviceToHost), "copy");
@@ -1054,8 +1072,9 @@ gl_status gl_surrogate_train(const gl_surrogate_train_desc* d, gl_surrogate** ou
                                                             n, row0,
                                                             stride, 1.f / d->batch, tb.gpart,
                                                             tb.lpart, tb.timeout);
-    k_adam<<<(NPARAM + 255) / 256, 256>>>(s->params, tb.m, tb.v, tb.gpart, ntiles, lr, b1, b2,
-                                         1e-8f, (float)(1.0 - bc1), (float)(1.0 - bc2), nullptr);
+    k_adam<<<(NPARAM + ADAM_PAR - 1) / ADAM_PAR, ADAM_THREADS>>>(
+        s->params, tb.m, tb.v, tb.gpart, ntiles, lr, b1, b2, 1e-8f, (float)(1.0 - bc1),
+        (float)(1.0 - bc2), nullptr);
     if ((it & 255) == 0) {
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return bail(fail(GL_ECUDA, std::string("training: ") + cudaGetErrorString(e)));
