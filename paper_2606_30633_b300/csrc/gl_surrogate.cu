@@ -184,11 +184,9 @@ __global__ void k_pack(const float* __restrict__ p, __nv_bfloat16* __restrict__ 
 
 // Sum of the tiles' gradients and Adam (FP32 master weights); writes the
 // gradient itself when out_grad is non-null (tests) and skips the update when
-// lr == 0.
-// The gradient of parameter k is the sum of the tiles' partial gradients:
-// a CTA of ADAM_THREADS takes ADAM_PAR consecutive parameters, each warp the
-// tiles t = warp, warp + 8, ... of them (coalesced rows), and the eight
-// partial sums are added in a fixed order (deterministic).
+// lr == 0. A CTA of ADAM_THREADS takes ADAM_PAR consecutive parameters; each
+// warp sums the tiles t = warp, warp + 8, ... of them (coalesced rows), and
+// the eight partial sums are added in a fixed order (deterministic).
 constexpr int ADAM_PAR = 32, ADAM_THREADS = 256;
 __global__ void __launch_bounds__(ADAM_THREADS)
 k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
